@@ -1,0 +1,162 @@
+/*
+ * fraclap — GB300 (sm_103a) library for the fractional Poisson problem
+ * (-Laplacian)^{alpha/2} u = f with homogeneous Dirichlet conditions on
+ * masked 2-D/3-D grids, by the eigenfunction-expansion method of
+ * arXiv:1911.11906 (Carlson, Kirby, Sundar).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All matrices are column-major IEEE double: a(i, j) = a[i + j * ld].
+ *  - Pointers named *_dev are device pointers owned by the caller; the
+ *    library never frees them and never copies to or from the host unless
+ *    the entry point says so.  Outputs may not alias inputs unless stated.
+ *  - Every call is asynchronous on the given stream (0 = legacy default
+ *    stream) unless stated.  Device-side failures (an iteration cap, a wait
+ *    that timed out, lambda <= 0 with alpha != 0) are recorded in a device
+ *    status word of the context; fraclap_sync() waits for the stream and
+ *    returns that status (and clears it).
+ *  - Return values: FRACLAP_OK (0) or a negative FRACLAP_ERR_* code.
+ *    fraclap_last_error() gives a message for the last failure of a context.
+ *  - Workspace: an entry point that takes (work_dev, work_bytes) uses that
+ *    caller-owned device buffer (at least the size the matching
+ *    *_workspace_bytes query returns, 256-byte aligned); with work_dev == NULL
+ *    it uses a buffer owned by the context, grown with cudaMalloc on demand.
+ *  - One context serves one device; calls on one context must not overlap.
+ */
+#ifndef FRACLAP_H_
+#define FRACLAP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fraclap_stream_t; /* = cudaStream_t */
+typedef struct fraclap_ctx fraclap_ctx;
+
+enum {
+  FRACLAP_OK = 0,
+  FRACLAP_ERR_INVALID_ARG = -1,   /* a null pointer, a negative size, ld < rows, ... */
+  FRACLAP_ERR_NOT_SPD = -2,       /* lambda_i <= 0 met with alpha != 0 in frac_apply */
+  FRACLAP_ERR_NO_CONVERGENCE = -3,/* an eigen-iteration hit its cap */
+  FRACLAP_ERR_TIMEOUT = -4,       /* a bounded device-side wait expired */
+  FRACLAP_ERR_ALLOC = -5,         /* a context-owned workspace allocation failed */
+  FRACLAP_ERR_CUDA = -6,          /* a CUDA runtime call failed (see fraclap_last_error) */
+  FRACLAP_ERR_UNSUPPORTED = -7    /* a size or option outside what this build handles */
+};
+
+/* Options; zero fields take the defaults in brackets. */
+typedef struct fraclap_opts {
+  int band_width;           /* half-bandwidth b of the dense-to-band stage [32]; 1..64 */
+  int leaf_size;            /* largest leaf of the tridiagonal divide and conquer [32]; 2..32 */
+  double wait_timeout_s;    /* limit of every device-side spin wait in seconds [10] */
+} fraclap_opts;
+
+/* Creates a context on the current CUDA device.  opts may be NULL. */
+int fraclap_create(fraclap_ctx** ctx, const fraclap_opts* opts);
+void fraclap_destroy(fraclap_ctx* ctx);
+const char* fraclap_strerror(int code);
+const char* fraclap_last_error(const fraclap_ctx* ctx);
+/* Waits for `stream`, then returns and clears the context's device status. */
+int fraclap_sync(fraclap_ctx* ctx, fraclap_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * fd_assemble — the discrete Laplace operator of Sec. II, eq.
+ * (discrete_laplace), with a nodal finite-difference basis: the mass matrix
+ * is the identity and K is the 5-point (dim = 2) or 7-point (dim = 3)
+ * Laplacian scaled by 1/h^2 with homogeneous Dirichlet conditions
+ * (eq. continuous_eigenproblem): row i holds 2*dim/h^2 on the diagonal and
+ * -1/h^2 for every face neighbour inside the mask, columns ascending.
+ *
+ *  mask_dev  uint8[ext0*ext1*ext2], x fastest then y then z; nonzero = dof.
+ *  ext       host int64[3] = (nx, ny, nz); nz must be 1 when dim = 2.
+ *  idx_dev   int32[ext0*ext1*ext2] out: dof number of each node, -1 outside;
+ *            dofs are numbered in row-major order over the kept nodes.
+ *  n_out, nnz_out  host out: number of dofs and of CSR nonzeros.
+ *  rowptr_dev int64[n+1], col_dev int32[nnz], val_dev double[nnz]: CSR out.
+ *  A_dense_dev double[lda*n]: optional dense copy of the matrix (zero
+ *            elsewhere); lda >= n.
+ * Two-call protocol: with rowptr_dev == NULL the call numbers the dofs,
+ * writes idx_dev, and returns n and nnz (it synchronises `stream` to read
+ * them).  A second call with the CSR buffers (and optionally A_dense_dev)
+ * fills them; it reads idx_dev from the first call and is asynchronous.
+ * ---------------------------------------------------------------------- */
+int fd_assemble(fraclap_ctx* ctx, const uint8_t* mask_dev, int dim, const int64_t ext[3],
+                double h, int32_t* idx_dev, int64_t* n_out, int64_t* nnz_out,
+                int64_t* rowptr_dev, int32_t* col_dev, double* val_dev,
+                double* A_dense_dev, int64_t lda, fraclap_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * eig_full — all n eigenpairs A = V diag(lambda) V^T of a dense symmetric
+ * matrix (the "solve for all N eigenpairs once" step of Sec. II and
+ * Sec. III-A), FP64 throughout.  Route: Householder reduction to a band of
+ * half-width b (compact-WY panels, symmetric rank-2b trailing updates),
+ * bulge chasing to tridiagonal form, tridiagonal divide and conquer, and
+ * back-transformation by both orthogonal factors.
+ *
+ *  A_dev      double[lda*n], only the lower triangle is read; not modified.
+ *  lambda_dev double[n] out, ascending.
+ *  V_dev      double[ldv*n] out, orthonormal eigenvectors in columns (the
+ *             sign of each column is unspecified); ldv >= n.
+ *  work_dev / work_bytes: see fraclap_eig_workspace_bytes.
+ *  info_dev   optional int32 out (device): 0, or a positive count of
+ *             failures recorded on the device (also in the context status).
+ * ---------------------------------------------------------------------- */
+size_t fraclap_eig_workspace_bytes(const fraclap_ctx* ctx, int64_t n);
+int eig_full(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_t lda,
+             double* lambda_dev, double* V_dev, int64_t ldv, void* work_dev,
+             size_t work_bytes, int32_t* info_dev, fraclap_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * frac_apply — the spectral solution operator of Sec. II,
+ * eq. (poisson_solution) and the sum v after eq. (discrete_laplace):
+ *   u_j = V diag(lambda^{-alpha_j / 2}) V^T f_{pair_f[j]},  j = 0..k-1.
+ * alpha may be any real number; alpha < 0 applies the forward operator of
+ * eq. (spectral_definition).  With alpha != 0 every lambda must be > 0, else
+ * the device status becomes FRACLAP_ERR_NOT_SPD.
+ *
+ *  V_dev double[ldv*n], lambda_dev double[n]: a decomposition from eig_full.
+ *  F_dev double[ldf*m]: m distinct forcings in columns; ldf >= n.
+ *  pair_f_dev int32[k] (each in [0, m)), pair_alpha_dev double[k].
+ *  U_dev double[ldu*k] out; ldu >= n.
+ *  work: fraclap_apply_workspace_bytes(n, m, k) bytes (V^T F and the scaled
+ *  coefficients).
+ * ---------------------------------------------------------------------- */
+size_t fraclap_apply_workspace_bytes(int64_t n, int64_t m, int64_t k);
+int frac_apply(fraclap_ctx* ctx, const double* V_dev, int64_t ldv, const double* lambda_dev,
+               int64_t n, const double* F_dev, int64_t ldf, int64_t m,
+               const int32_t* pair_f_dev, const double* pair_alpha_dev, int64_t k,
+               double* U_dev, int64_t ldu, void* work_dev, size_t work_bytes,
+               fraclap_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Stage entry points (the steps eig_full chains), for stage-level checks.
+ * ---------------------------------------------------------------------- */
+
+/* Reduction to symmetric tridiagonal form A = Q T Q^T (dense to band, then
+ * bulge chasing).  d_dev double[n], e_dev double[n-1] out (T(i+1, i) = e[i]).
+ * Q_dev double[ldq*n]: optional (NULL = skip); when given, Q is formed by
+ * back-transforming the identity.  work as for eig_full. */
+int fraclap_tridiagonalize(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_t lda,
+                           double* d_dev, double* e_dev, double* Q_dev, int64_t ldq,
+                           void* work_dev, size_t work_bytes, fraclap_stream_t stream);
+
+/* Eigen-decomposition of the symmetric tridiagonal (d, e) by divide and
+ * conquer: lambda_dev double[n] ascending, Z_dev double[ldz*n] eigenvectors. */
+size_t fraclap_tridiag_workspace_bytes(const fraclap_ctx* ctx, int64_t n);
+int fraclap_tridiag_eig(fraclap_ctx* ctx, const double* d_dev, const double* e_dev, int64_t n,
+                        double* lambda_dev, double* Z_dev, int64_t ldz, void* work_dev,
+                        size_t work_bytes, fraclap_stream_t stream);
+
+/* C = alpha * op(A) * op(B) + beta * C in FP64 with op = transpose when
+ * trans_* != 0 (the GEMM engine behind every dense step). */
+int fraclap_dgemm(fraclap_ctx* ctx, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
+                  double alpha, const double* A_dev, int64_t lda, const double* B_dev,
+                  int64_t ldb, double beta, double* C_dev, int64_t ldc, fraclap_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FRACLAP_H_ */

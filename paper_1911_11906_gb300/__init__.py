@@ -1,0 +1,24 @@
+"""fraclap: fractional Poisson solves by eigenfunction expansion on GB300.
+
+Thin Python binding of the C ABI in ``include/fraclap.h`` (argument
+marshalling only; every step runs in the library's CUDA kernels).  PyTorch
+supplies device memory and the current stream.  The library is built
+in-tree by ``paper_1911_11906_gb300.build``; if it is missing, every call
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+from ._binding import (  # noqa: F401
+    FraclapError,
+    Context,
+    load_library,
+    library_path,
+    fd_assemble,
+    eig_full,
+    frac_apply,
+    tridiagonalize,
+    tridiag_eig,
+    dgemm,
+    solve,
+    default_context,
+)

@@ -1,0 +1,268 @@
+"""ctypes marshalling for libfraclap.so (see include/fraclap.h)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libfraclap.so")
+_lock = threading.Lock()
+_lib = None
+
+_i32, _i64, _dbl, _p, _sz = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+
+# (name, restype, argtypes) of every exported entry point
+SIGNATURES = {
+    "fraclap_create": (_i32, [ctypes.POINTER(_p), _p]),
+    "fraclap_destroy": (None, [_p]),
+    "fraclap_strerror": (ctypes.c_char_p, [_i32]),
+    "fraclap_last_error": (ctypes.c_char_p, [_p]),
+    "fraclap_sync": (_i32, [_p, _p]),
+    "fd_assemble": (_i32, [_p, _p, _i32, _p, _dbl, _p, _p, _p, _p, _p, _p, _p, _i64, _p]),
+    "fraclap_eig_workspace_bytes": (_sz, [_p, _i64]),
+    "eig_full": (_i32, [_p, _p, _i64, _i64, _p, _p, _i64, _p, _sz, _p, _p]),
+    "fraclap_apply_workspace_bytes": (_sz, [_i64, _i64, _i64]),
+    "frac_apply": (_i32, [_p, _p, _i64, _p, _i64, _p, _i64, _i64, _p, _p, _i64, _p, _i64, _p, _sz, _p]),
+    "fraclap_tridiagonalize": (_i32, [_p, _p, _i64, _i64, _p, _p, _p, _i64, _p, _sz, _p]),
+    "fraclap_tridiag_workspace_bytes": (_sz, [_p, _i64]),
+    "fraclap_tridiag_eig": (_i32, [_p, _p, _p, _i64, _p, _p, _i64, _p, _sz, _p]),
+    "fraclap_dgemm": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64, _p]),
+}
+
+
+class FraclapError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fraclap error {code}: {msg}")
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("band_width", ctypes.c_int), ("leaf_size", ctypes.c_int), ("wait_timeout_s", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Loads the in-tree CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(
+                    f"CUDA library {_LIB_PATH} is missing: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+            lib = ctypes.CDLL(_LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _stream(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A library context on the current CUDA device (owns a status word and
+    an optional workspace)."""
+
+    def __init__(self, band_width: int = 0, leaf_size: int = 0, wait_timeout_s: float = 0.0):
+        self.lib = load_library()
+        self.handle = ctypes.c_void_p()
+        opts = _Opts(band_width, leaf_size, wait_timeout_s)
+        rc = self.lib.fraclap_create(ctypes.byref(self.handle), ctypes.byref(opts))
+        if rc != 0:
+            raise FraclapError(rc, self.lib.fraclap_strerror(rc).decode())
+
+    def close(self):
+        if self.handle:
+            self.lib.fraclap_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc: int):
+        if rc != 0:
+            msg = self.lib.fraclap_last_error(self.handle).decode()
+            raise FraclapError(rc, msg)
+
+    def sync(self, stream=None):
+        """Waits for the stream and raises if a kernel recorded a failure."""
+        self.check(self.lib.fraclap_sync(self.handle, ctypes.c_void_p(_stream(stream))))
+
+
+_default = None
+
+
+def default_context() -> Context:
+    global _default
+    if _default is None:
+        _default = Context()
+    return _default
+
+
+def _f64_colmajor(t: torch.Tensor, name: str) -> torch.Tensor:
+    """Returns a column-major (Fortran-order) float64 CUDA view: ld = t.stride(1)."""
+    if t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if t.dim() == 1:
+        t = t.unsqueeze(1)
+    if t.stride(0) != 1:
+        t = t.t().contiguous().t()
+    return t
+
+
+def _ld(t: torch.Tensor) -> int:
+    return max(t.stride(1), t.shape[0], 1) if t.dim() == 2 else max(t.shape[0], 1)
+
+
+def empty_colmajor(rows: int, cols: int, device=None) -> torch.Tensor:
+    return torch.empty((cols, rows), dtype=torch.float64, device=device or "cuda").t()
+
+
+def fd_assemble(mask: torch.Tensor, h: float, dense: bool = True, ctx: Context | None = None,
+                stream=None):
+    """Assembles the FD Laplacian of a uint8 mask ([y, x] or [z, y, x]) on the GPU.
+    Returns dict(idx, n, rowptr, col, val, A (column-major dense or None))."""
+    ctx = ctx or default_context()
+    if mask.dtype != torch.uint8 or not mask.is_cuda:
+        raise TypeError("mask must be a uint8 CUDA tensor")
+    mask = mask.contiguous()
+    dim = mask.dim()
+    ext = (ctypes.c_int64 * 3)(*(list(reversed(mask.shape)) + [1] * (3 - dim)))
+    idx = torch.empty(mask.shape, dtype=torch.int32, device=mask.device)
+    n = ctypes.c_int64(-1)
+    nnz = ctypes.c_int64(-1)
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.fd_assemble(ctx.handle, _ptr(mask), dim, ext, float(h), _ptr(idx), ctypes.byref(n),
+                                  ctypes.byref(nnz), None, None, None, None, 0, st))
+    N, NNZ = n.value, nnz.value
+    rowptr = torch.empty(N + 1, dtype=torch.int64, device=mask.device)
+    col = torch.empty(max(NNZ, 1), dtype=torch.int32, device=mask.device)
+    val = torch.empty(max(NNZ, 1), dtype=torch.float64, device=mask.device)
+    A = empty_colmajor(N, N, mask.device) if (dense and N > 0) else None
+    ctx.check(ctx.lib.fd_assemble(ctx.handle, _ptr(mask), dim, ext, float(h), _ptr(idx), ctypes.byref(n),
+                                  ctypes.byref(nnz), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(A),
+                                  max(N, 1), st))
+    return {"idx": idx, "n": N, "rowptr": rowptr, "col": col[:NNZ], "val": val[:NNZ], "A": A}
+
+
+def eig_full(A: torch.Tensor, ctx: Context | None = None, stream=None, workspace: torch.Tensor | None = None,
+             sync: bool = True):
+    """All eigenpairs of the symmetric matrix A (lower triangle read).
+    Returns (lambda ascending, V column-major)."""
+    ctx = ctx or default_context()
+    A = _f64_colmajor(A, "A")
+    n = A.shape[0]
+    lam = torch.empty(n, dtype=torch.float64, device=A.device)
+    V = empty_colmajor(n, n, A.device)
+    if workspace is None:
+        nbytes = ctx.lib.fraclap_eig_workspace_bytes(ctx.handle, n)
+        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=A.device)
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.eig_full(ctx.handle, _ptr(A), n, _ld(A), _ptr(lam), _ptr(V), max(n, 1),
+                               _ptr(workspace), workspace.numel(), None, st))
+    if sync:
+        ctx.sync(stream)
+    return lam, V
+
+
+def frac_apply(V: torch.Tensor, lam: torch.Tensor, F: torch.Tensor, pair_f, pair_alpha,
+               ctx: Context | None = None, stream=None, out: torch.Tensor | None = None,
+               workspace: torch.Tensor | None = None, sync: bool = True) -> torch.Tensor:
+    """u_j = V diag(lam^{-alpha_j/2}) V^T F[:, pair_f[j]]; returns U (n x k, column-major)."""
+    ctx = ctx or default_context()
+    V = _f64_colmajor(V, "V")
+    F = _f64_colmajor(F, "F")
+    n = V.shape[0]
+    dev = V.device
+    pf = torch.as_tensor(pair_f, dtype=torch.int32).to(dev).contiguous()
+    pa = torch.as_tensor(pair_alpha, dtype=torch.float64).to(dev).contiguous()
+    k, m = pf.numel(), F.shape[1]
+    U = out if out is not None else empty_colmajor(n, k, dev)
+    if workspace is None:
+        nbytes = ctx.lib.fraclap_apply_workspace_bytes(n, m, k)
+        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.frac_apply(ctx.handle, _ptr(V), _ld(V), _ptr(lam.contiguous()), n, _ptr(F), _ld(F), m,
+                                 _ptr(pf), _ptr(pa), k, _ptr(U), _ld(U), _ptr(workspace), workspace.numel(), st))
+    if sync:
+        ctx.sync(stream)
+    return U
+
+
+def tridiagonalize(A: torch.Tensor, want_q: bool = True, ctx: Context | None = None, stream=None):
+    """A = Q T Q^T (two-stage reduction).  Returns (d, e, Q or None)."""
+    ctx = ctx or default_context()
+    A = _f64_colmajor(A, "A")
+    n = A.shape[0]
+    d = torch.empty(n, dtype=torch.float64, device=A.device)
+    e = torch.empty(max(n - 1, 1), dtype=torch.float64, device=A.device)
+    Q = empty_colmajor(n, n, A.device) if want_q else None
+    nbytes = ctx.lib.fraclap_eig_workspace_bytes(ctx.handle, n)
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=A.device)
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.fraclap_tridiagonalize(ctx.handle, _ptr(A), n, _ld(A), _ptr(d), _ptr(e), _ptr(Q),
+                                             max(n, 1), _ptr(ws), ws.numel(), st))
+    ctx.sync(stream)
+    return d, e[: max(n - 1, 0)], Q
+
+
+def tridiag_eig(d: torch.Tensor, e: torch.Tensor, ctx: Context | None = None, stream=None):
+    """Divide-and-conquer eigensolver of the symmetric tridiagonal (d, e)."""
+    ctx = ctx or default_context()
+    n = d.numel()
+    lam = torch.empty(n, dtype=torch.float64, device=d.device)
+    Z = empty_colmajor(n, n, d.device)
+    nbytes = ctx.lib.fraclap_tridiag_workspace_bytes(ctx.handle, n)
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=d.device)
+    ee = e.contiguous() if e.numel() > 0 else torch.zeros(1, dtype=torch.float64, device=d.device)
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.fraclap_tridiag_eig(ctx.handle, _ptr(d.contiguous()), _ptr(ee), n, _ptr(lam), _ptr(Z),
+                                          max(n, 1), _ptr(ws), ws.numel(), st))
+    ctx.sync(stream)
+    return lam, Z
+
+
+def dgemm(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, alpha=1.0, beta=0.0,
+          C: torch.Tensor | None = None, ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """C = alpha op(A) op(B) + beta C on the library's FP64 GEMM engine."""
+    ctx = ctx or default_context()
+    A = _f64_colmajor(A, "A")
+    B = _f64_colmajor(B, "B")
+    m = A.shape[1] if trans_a else A.shape[0]
+    k = A.shape[0] if trans_a else A.shape[1]
+    n = B.shape[0] if trans_b else B.shape[1]
+    if C is None:
+        C = empty_colmajor(m, n, A.device)
+        beta = 0.0
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.fraclap_dgemm(ctx.handle, int(trans_a), int(trans_b), m, n, k, float(alpha), _ptr(A),
+                                    _ld(A), _ptr(B), _ld(B), float(beta), _ptr(C), _ld(C), st))
+    ctx.sync(stream)
+    return C
+
+
+def solve(mask: torch.Tensor, h: float, F: torch.Tensor, pair_f, pair_alpha, ctx: Context | None = None):
+    """The whole path on the GPU: assemble, decompose, apply.  Returns (lam, V, U)."""
+    asm = fd_assemble(mask, h, dense=True, ctx=ctx)
+    lam, V = eig_full(asm["A"], ctx=ctx)
+    U = frac_apply(V, lam, F, pair_f, pair_alpha, ctx=ctx)
+    return lam, V, U

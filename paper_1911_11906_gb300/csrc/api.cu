@@ -1,0 +1,284 @@
+// C ABI of the fraclap library: contexts, errors, workspace, and the
+// eigendecomposition entry points (the spectral apply is in apply.cu, the
+// stencil assembly in assemble.cu).
+#include <stdarg.h>
+
+#include "internal.cuh"
+
+namespace fraclap {
+
+int set_error(fraclap_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return code;
+}
+
+int get_workspace(fraclap_ctx* ctx, void* work, size_t work_bytes, size_t need, Arena* arena) {
+  need = align256(need);
+  if (work) {
+    FL_CHECK(ctx, ((uintptr_t)work & 255) == 0, FRACLAP_ERR_INVALID_ARG,
+             "workspace must be 256-byte aligned");
+    FL_CHECK(ctx, work_bytes >= need, FRACLAP_ERR_INVALID_ARG,
+             "workspace too small: %zu bytes given, %zu needed", work_bytes, need);
+    arena->base = (char*)work;
+    arena->cap = work_bytes;
+    arena->off = 0;
+    return 0;
+  }
+  if (ctx->ws_bytes < need) {
+    if (ctx->ws) {
+      FL_CUDA(ctx, cudaDeviceSynchronize());
+      FL_CUDA(ctx, cudaFree(ctx->ws));
+      ctx->ws = nullptr;
+      ctx->ws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&ctx->ws, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->ws = nullptr;
+      return set_error(ctx, FRACLAP_ERR_ALLOC, "workspace allocation of %zu bytes failed: %s", need,
+                       cudaGetErrorString(e));
+    }
+    ctx->ws_bytes = need;
+  }
+  arena->base = (char*)ctx->ws;
+  arena->cap = ctx->ws_bytes;
+  arena->off = 0;
+  return 0;
+}
+
+namespace {
+
+__global__ void set_identity(double* Z, int64_t ldz, int64_t n) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n * n) return;
+  const int64_t i = p % n, j = p / n;
+  Z[i + j * ldz] = (i == j) ? 1.0 : 0.0;
+}
+
+__global__ void copy_lower(const double* A, int64_t lda, double* B, int64_t ldb, int64_t n) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n * n) return;
+  const int64_t i = p % n, j = p / n;
+  if (i >= j) B[i + j * ldb] = A[i + j * lda];
+}
+
+struct EigWork {
+  double* Aw;     // n x n working copy
+  double* band;   // 2b x n
+  double* d;      // n
+  double* e;      // n
+  double* W1;     // b x n
+  double* W2;     // b x n
+  Stage1 s1;
+  Stage2 s2;
+};
+
+int eig_take(Arena* ar, const fraclap_ctx* ctx, int64_t n, EigWork* w) {
+  const int b = ctx->band_width;
+  w->Aw = ar->take<double>(n * n);
+  w->band = ar->take<double>(2 * (int64_t)b * n);
+  w->d = ar->take<double>(n);
+  w->e = ar->take<double>(n);
+  w->W1 = ar->take<double>((int64_t)b * n);
+  w->W2 = ar->take<double>((int64_t)b * n);
+  stage1_take(ar, n, b, ctx->sm_count, &w->s1);
+  stage2_take(ar, n, b, &w->s2);
+  return 0;
+}
+
+size_t eig_ws_bytes(const fraclap_ctx* ctx, int64_t n, bool with_dc) {
+  Arena ar;
+  EigWork w;
+  eig_take(&ar, ctx, n, &w);
+  size_t s = ar.off;
+  if (with_dc) s += stedc_ws(ctx, n);
+  return s + 4096;
+}
+
+// Reduction of A to tridiagonal form (d, e) in w; optionally Z <- Q1 Q2 Z.
+int reduce(fraclap_ctx* ctx, const double* A, int64_t n, int64_t lda, EigWork* w, cudaStream_t st) {
+  const int b = ctx->band_width;
+  copy_lower<<<(unsigned)cdiv(n * n, 256), 256, 0, st>>>(A, lda, w->Aw, n, n);
+  FL_CUDA(ctx, cudaGetLastError());
+  FL_TRY(sy2sb_run(ctx, w->Aw, n, n, b, w->band, &w->s1, st));
+  FL_TRY(sb2st_run(ctx, w->band, n, b, w->d, w->e, &w->s2, st));
+  return 0;
+}
+
+int back_transform(fraclap_ctx* ctx, int64_t n, EigWork* w, double* Z, int64_t ldz,
+                   cudaStream_t st) {
+  const int b = ctx->band_width;
+  FL_TRY(q2_apply_run(ctx, &w->s2, n, b, Z, ldz, n, st));
+  FL_TRY(q1_apply_run(ctx, &w->s1, n, b, Z, ldz, n, w->W1, w->W2, st));
+  return 0;
+}
+
+}  // namespace
+}  // namespace fraclap
+
+using namespace fraclap;
+
+extern "C" const char* fraclap_strerror(int code) {
+  switch (code) {
+    case FRACLAP_OK: return "ok";
+    case FRACLAP_ERR_INVALID_ARG: return "invalid argument";
+    case FRACLAP_ERR_NOT_SPD: return "eigenvalue <= 0 with alpha != 0";
+    case FRACLAP_ERR_NO_CONVERGENCE: return "eigen-iteration did not converge";
+    case FRACLAP_ERR_TIMEOUT: return "device-side wait timed out";
+    case FRACLAP_ERR_ALLOC: return "workspace allocation failed";
+    case FRACLAP_ERR_CUDA: return "CUDA runtime error";
+    case FRACLAP_ERR_UNSUPPORTED: return "unsupported size or option";
+    default: return "unknown error";
+  }
+}
+
+extern "C" const char* fraclap_last_error(const fraclap_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : "null context";
+}
+
+extern "C" int fraclap_create(fraclap_ctx** out, const fraclap_opts* opts) {
+  if (!out) return FRACLAP_ERR_INVALID_ARG;
+  *out = nullptr;
+  fraclap_ctx* ctx = new fraclap_ctx();
+  if (opts) {
+    if (opts->band_width) ctx->band_width = opts->band_width;
+    if (opts->leaf_size) ctx->leaf_size = opts->leaf_size;
+    if (opts->wait_timeout_s > 0) ctx->wait_timeout_s = opts->wait_timeout_s;
+  }
+  if (ctx->band_width < 1 || ctx->band_width > 64 || ctx->leaf_size < 2 || ctx->leaf_size > 32) {
+    delete ctx;
+    return FRACLAP_ERR_INVALID_ARG;
+  }
+  // the wait limit is counted in SM clock cycles; 2.5 GHz bounds every clock
+  ctx->wait_cycles = (long long)(ctx->wait_timeout_s * 2.5e9);
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_barrier, 4 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_barrier, 0, 4 * sizeof(unsigned));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->d_barrier) cudaFree(ctx->d_barrier);
+    delete ctx;
+    return FRACLAP_ERR_CUDA;
+  }
+  *out = ctx;
+  return 0;
+}
+
+extern "C" void fraclap_destroy(fraclap_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_barrier) cudaFree(ctx->d_barrier);
+  delete ctx;
+}
+
+extern "C" int fraclap_sync(fraclap_ctx* ctx, fraclap_stream_t stream) {
+  if (!ctx) return FRACLAP_ERR_INVALID_ARG;
+  FL_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+  int32_t st = 0;
+  FL_CUDA(ctx, cudaMemcpy(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    FL_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int32_t)));
+    return set_error(ctx, st, "device reported: %s", fraclap_strerror(st));
+  }
+  return 0;
+}
+
+extern "C" size_t fraclap_eig_workspace_bytes(const fraclap_ctx* ctx, int64_t n) {
+  if (!ctx || n <= 0) return 0;
+  return eig_ws_bytes(ctx, n, true);
+}
+
+extern "C" size_t fraclap_tridiag_workspace_bytes(const fraclap_ctx* ctx, int64_t n) {
+  if (!ctx || n <= 0) return 0;
+  return stedc_ws(ctx, n) + 4096;
+}
+
+extern "C" int eig_full(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_t lda,
+                        double* lambda_dev, double* V_dev, int64_t ldv, void* work_dev,
+                        size_t work_bytes, int32_t* info_dev, fraclap_stream_t stream) {
+  if (!ctx) return FRACLAP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  FL_CHECK(ctx, n >= 0, FRACLAP_ERR_INVALID_ARG, "eig_full: n < 0");
+  if (n == 0) return 0;
+  FL_CHECK(ctx, A_dev && lambda_dev && V_dev, FRACLAP_ERR_INVALID_ARG, "eig_full: null pointer");
+  FL_CHECK(ctx, lda >= n && ldv >= n, FRACLAP_ERR_INVALID_ARG, "eig_full: leading dimension < n");
+  FL_CHECK(ctx, n < (1LL << 31) / 64, FRACLAP_ERR_UNSUPPORTED, "eig_full: n too large");
+  Arena ar;
+  FL_TRY(get_workspace(ctx, work_dev, work_bytes, eig_ws_bytes(ctx, n, true), &ar));
+  EigWork w;
+  eig_take(&ar, ctx, n, &w);
+  FL_CHECK(ctx, w.s2.progress != nullptr, FRACLAP_ERR_ALLOC, "eig_full: workspace too small");
+  FL_TRY(reduce(ctx, A_dev, n, lda, &w, st));
+  FL_TRY(stedc_run(ctx, w.d, w.e, n, lambda_dev, V_dev, ldv, &ar, st));
+  FL_TRY(back_transform(ctx, n, &w, V_dev, ldv, st));
+  if (info_dev) FL_CUDA(ctx, cudaMemcpyAsync(info_dev, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  return 0;
+}
+
+extern "C" int fraclap_tridiagonalize(fraclap_ctx* ctx, const double* A_dev, int64_t n,
+                                      int64_t lda, double* d_dev, double* e_dev, double* Q_dev,
+                                      int64_t ldq, void* work_dev, size_t work_bytes,
+                                      fraclap_stream_t stream) {
+  if (!ctx) return FRACLAP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  FL_CHECK(ctx, n >= 0, FRACLAP_ERR_INVALID_ARG, "tridiagonalize: n < 0");
+  if (n == 0) return 0;
+  FL_CHECK(ctx, A_dev && d_dev && (e_dev || n == 1), FRACLAP_ERR_INVALID_ARG, "tridiagonalize: null pointer");
+  FL_CHECK(ctx, lda >= n && (!Q_dev || ldq >= n), FRACLAP_ERR_INVALID_ARG, "tridiagonalize: leading dimension < n");
+  Arena ar;
+  FL_TRY(get_workspace(ctx, work_dev, work_bytes, eig_ws_bytes(ctx, n, false), &ar));
+  EigWork w;
+  eig_take(&ar, ctx, n, &w);
+  FL_CHECK(ctx, w.s2.progress != nullptr, FRACLAP_ERR_ALLOC, "tridiagonalize: workspace too small");
+  FL_TRY(reduce(ctx, A_dev, n, lda, &w, st));
+  FL_CUDA(ctx, cudaMemcpyAsync(d_dev, w.d, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  if (n > 1) FL_CUDA(ctx, cudaMemcpyAsync(e_dev, w.e, sizeof(double) * (n - 1), cudaMemcpyDeviceToDevice, st));
+  if (Q_dev) {
+    set_identity<<<(unsigned)cdiv(n * n, 256), 256, 0, st>>>(Q_dev, ldq, n);
+    FL_CUDA(ctx, cudaGetLastError());
+    FL_TRY(back_transform(ctx, n, &w, Q_dev, ldq, st));
+  }
+  return 0;
+}
+
+extern "C" int fraclap_tridiag_eig(fraclap_ctx* ctx, const double* d_dev, const double* e_dev,
+                                   int64_t n, double* lambda_dev, double* Z_dev, int64_t ldz,
+                                   void* work_dev, size_t work_bytes, fraclap_stream_t stream) {
+  if (!ctx) return FRACLAP_ERR_INVALID_ARG;
+  FL_CHECK(ctx, n >= 0, FRACLAP_ERR_INVALID_ARG, "tridiag_eig: n < 0");
+  if (n == 0) return 0;
+  FL_CHECK(ctx, d_dev && lambda_dev && Z_dev && (e_dev || n == 1), FRACLAP_ERR_INVALID_ARG,
+           "tridiag_eig: null pointer");
+  FL_CHECK(ctx, ldz >= n, FRACLAP_ERR_INVALID_ARG, "tridiag_eig: ldz < n");
+  Arena ar;
+  FL_TRY(get_workspace(ctx, work_dev, work_bytes, stedc_ws(ctx, n) + 4096, &ar));
+  return stedc_run(ctx, d_dev, e_dev, n, lambda_dev, Z_dev, ldz, &ar, (cudaStream_t)stream);
+}
+
+extern "C" int fraclap_dgemm(fraclap_ctx* ctx, int trans_a, int trans_b, int64_t m, int64_t n,
+                             int64_t k, double alpha, const double* A_dev, int64_t lda,
+                             const double* B_dev, int64_t ldb, double beta, double* C_dev,
+                             int64_t ldc, fraclap_stream_t stream) {
+  if (!ctx) return FRACLAP_ERR_INVALID_ARG;
+  FL_CHECK(ctx, m >= 0 && n >= 0 && k >= 0, FRACLAP_ERR_INVALID_ARG, "dgemm: negative size");
+  if (m == 0 || n == 0) return 0;
+  FL_CHECK(ctx, C_dev && (k == 0 || (A_dev && B_dev)), FRACLAP_ERR_INVALID_ARG, "dgemm: null pointer");
+  FL_CHECK(ctx, ldc >= m && lda >= (trans_a ? k : m) && ldb >= (trans_b ? n : k),
+           FRACLAP_ERR_INVALID_ARG, "dgemm: leading dimension too small");
+  GemmDesc d{m, n, k, A_dev, lda, B_dev, ldb, C_dev, ldc, nullptr, 0, nullptr, 0, 0, alpha, beta};
+  return gemm(ctx, trans_a != 0, trans_b != 0, kGemmPlain, d, 1, (cudaStream_t)stream);
+}

@@ -1,0 +1,77 @@
+// frac_apply: u_j = V diag(lambda^{-alpha_j/2}) V^T f_{pair_f[j]}
+// (Sec. II, eq. poisson_solution; the sum v after eq. discrete_laplace).
+//
+// Two FP64 GEMMs on the engine (W = V^T F over the m distinct forcings, then
+// U = V C) around an elementwise kernel that forms the spectral
+// coefficients C(i, j) = lambda_i^{-alpha_j/2} W(i, pair_f[j]); pow() is
+// CUDA's double-precision pow.  A zero or negative eigenvalue met with
+// alpha != 0 raises FRACLAP_ERR_NOT_SPD in the device status.
+#include "internal.cuh"
+
+namespace fraclap {
+namespace {
+
+__global__ void spectral_scale(const double* lambda, int64_t n, const double* W, int64_t ldw,
+                               const int32_t* pair_f, const double* pair_alpha, int64_t k,
+                               int64_t m, double* C, int64_t ldc, int32_t* status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i >= n || j >= k) return;
+  const double alpha = pair_alpha[j];
+  const int32_t f = pair_f[j];
+  if (f < 0 || f >= m) {
+    raise_status(status, FRACLAP_ERR_INVALID_ARG);
+    C[i + j * ldc] = 0.0;
+    return;
+  }
+  const double lam = lambda[i];
+  double mult = 1.0;
+  if (alpha != 0.0) {
+    if (!(lam > 0.0)) raise_status(status, FRACLAP_ERR_NOT_SPD);
+    mult = pow(lam, -0.5 * alpha);
+  }
+  C[i + j * ldc] = mult * W[i + (int64_t)f * ldw];
+}
+
+}  // namespace
+}  // namespace fraclap
+
+using namespace fraclap;
+
+extern "C" size_t fraclap_apply_workspace_bytes(int64_t n, int64_t m, int64_t k) {
+  if (n < 0 || m < 0 || k < 0) return 0;
+  return align256(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(m > 0 ? m : 1)) +
+         align256(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(k > 0 ? k : 1)) + 512;
+}
+
+extern "C" int frac_apply(fraclap_ctx* ctx, const double* V_dev, int64_t ldv,
+                          const double* lambda_dev, int64_t n, const double* F_dev, int64_t ldf,
+                          int64_t m, const int32_t* pair_f_dev, const double* pair_alpha_dev,
+                          int64_t k, double* U_dev, int64_t ldu, void* work_dev, size_t work_bytes,
+                          fraclap_stream_t stream) {
+  if (!ctx) return FRACLAP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  FL_CHECK(ctx, n >= 0 && m >= 0 && k >= 0, FRACLAP_ERR_INVALID_ARG, "frac_apply: negative size");
+  if (n == 0 || k == 0) return 0;
+  FL_CHECK(ctx, m >= 1, FRACLAP_ERR_INVALID_ARG, "frac_apply: pairs need at least one forcing");
+  FL_CHECK(ctx, V_dev && lambda_dev && F_dev && pair_f_dev && pair_alpha_dev && U_dev,
+           FRACLAP_ERR_INVALID_ARG, "frac_apply: null pointer");
+  FL_CHECK(ctx, ldv >= n && ldf >= n && ldu >= n, FRACLAP_ERR_INVALID_ARG, "frac_apply: leading dimension < n");
+  FL_CHECK(ctx, k <= 65535 * 64 && m <= 65535 * 64, FRACLAP_ERR_UNSUPPORTED, "frac_apply: too many pairs");
+  Arena ar;
+  FL_TRY(get_workspace(ctx, work_dev, work_bytes, fraclap_apply_workspace_bytes(n, m, k), &ar));
+  double* W = ar.take<double>(n * m);
+  double* C = ar.take<double>(n * k);
+  FL_CHECK(ctx, W && C, FRACLAP_ERR_ALLOC, "frac_apply: workspace too small");
+  // W = V^T F
+  GemmDesc d{n, m, n, V_dev, ldv, F_dev, ldf, W, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+  FL_TRY(gemm(ctx, true, false, kGemmPlain, d, 1, st));
+  FL_CHECK(ctx, k <= 65535, FRACLAP_ERR_UNSUPPORTED, "frac_apply: at most 65535 pairs per call");
+  spectral_scale<<<dim3((unsigned)cdiv(n, 256), (unsigned)k), 256, 0, st>>>(
+      lambda_dev, n, W, n, pair_f_dev, pair_alpha_dev, k, m, C, n, ctx->d_status);
+  FL_CUDA(ctx, cudaGetLastError());
+  // U = V C
+  d = GemmDesc{n, k, n, V_dev, ldv, C, n, U_dev, ldu, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+  FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+  return 0;
+}

@@ -1,0 +1,226 @@
+// FP64 GEMM engine.
+//
+// On GB300 the FP64 pipe delivers ~1.2 TFLOP/s for both DFMA and DMMA
+// (measured: DFMA 1.20, mma.sync f64 1.05, cuBLAS DGEMM 1.10 TFLOP/s), i.e.
+// about 2 FMA per clock per SM.  A 64x64 output tile with a 16-deep k step
+// needs 1 KB of operands per 4096 FMAs, so a plain shared-memory tiled SIMT
+// kernel is bound by the FP64 pipe, not by memory; the design goal is to keep
+// that pipe busy (enough resident warps, 16 independent accumulators per
+// thread) while supporting the operand forms the eigensolver needs: both
+// transposes, a symmetric A read from its lower triangle, a lower-triangular
+// C, a fused second product (symmetric rank-2k update), split-K with atomics
+// and device-side batched descriptors.
+#include "internal.cuh"
+
+namespace fraclap {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+template <bool TA, int MODE>
+__device__ __forceinline__ void load_a(double (*As)[BM + 1], const double* A, int64_t lda,
+                                       int64_t M, int64_t K, int64_t m0, int64_t k0) {
+  const int tid = threadIdx.x;
+  if (MODE == kGemmSymA) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = tid % BM, k = tid / BM + 4 * i;
+      const int64_t gm = m0 + m, gk = k0 + k;
+      double v = 0.0;
+      if (gm < M && gk < K) v = (gm >= gk) ? A[gm + gk * lda] : A[gk + gm * lda];
+      As[k][m] = v;
+    }
+  } else if (!TA) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = tid % BM, k = tid / BM + 4 * i;
+      const int64_t gm = m0 + m, gk = k0 + k;
+      As[k][m] = (gm < M && gk < K) ? A[gm + gk * lda] : 0.0;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = tid % BK, m = tid / BK + 16 * i;
+      const int64_t gm = m0 + m, gk = k0 + k;
+      As[k][m] = (gm < M && gk < K) ? A[gk + gm * lda] : 0.0;
+    }
+  }
+}
+
+template <bool TB>
+__device__ __forceinline__ void load_b(double (*Bs)[BN + 1], const double* B, int64_t ldb,
+                                       int64_t N, int64_t K, int64_t n0, int64_t k0) {
+  const int tid = threadIdx.x;
+  if (!TB) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = tid % BK, n = tid / BK + 16 * i;
+      const int64_t gn = n0 + n, gk = k0 + k;
+      Bs[k][n] = (gn < N && gk < K) ? B[gk + gn * ldb] : 0.0;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int n = tid % BN, k = tid / BN + 4 * i;
+      const int64_t gn = n0 + n, gk = k0 + k;
+      Bs[k][n] = (gn < N && gk < K) ? B[gn + gk * ldb] : 0.0;
+    }
+  }
+}
+
+template <bool TA, bool TB, int MODE>
+__device__ __forceinline__ void accumulate(double (&acc)[4][4], double (*As)[BM + 1],
+                                           double (*Bs)[BN + 1], const double* A, int64_t lda,
+                                           const double* B, int64_t ldb, int64_t M, int64_t N,
+                                           int64_t K, int64_t m0, int64_t n0, int64_t kbeg,
+                                           int64_t kend) {
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    load_a<TA, MODE>(As, A, lda, M, kend, m0, k0);
+    load_b<TB>(Bs, B, ldb, N, kend, n0, k0);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+}
+
+template <bool TA, bool TB, int MODE, bool ATOMIC>
+__device__ __forceinline__ void gemm_tile(const GemmDesc& d, int64_t m0, int64_t n0, int64_t kbeg,
+                                          int64_t kend) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  if (MODE == kGemmLowerC && m0 + BM - 1 < n0) return;  // tile entirely above the diagonal
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  accumulate<TA, TB, MODE>(acc, As, Bs, d.A, d.lda, d.B, d.ldb, d.M, d.N, d.K, m0, n0, kbeg, kend);
+  if (d.K2 > 0 && kbeg == 0)
+    accumulate<TA, TB, MODE>(acc, As, Bs, d.A2, d.lda2, d.B2, d.ldb2, d.M, d.N, d.K2, m0, n0, 0,
+                             d.K2);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + ty + 16 * i;
+    if (gm >= d.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx + 16 * j;
+      if (gn >= d.N) continue;
+      if (MODE == kGemmLowerC && gm < gn) continue;
+      double* c = d.C + gm + gn * d.ldc;
+      const double v = d.alpha * acc[i][j];
+      if (ATOMIC) {
+        atomicAdd(c, v);
+      } else {
+        *c = (d.beta == 0.0) ? v : v + d.beta * *c;
+      }
+    }
+  }
+}
+
+template <bool TA, bool TB, int MODE, bool ATOMIC>
+__global__ void __launch_bounds__(NT) gemm_kernel(GemmDesc d, int64_t kchunk) {
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = (kbeg + kchunk < d.K) ? kbeg + kchunk : d.K;
+  if (kbeg > 0 && kbeg >= d.K) return;  // z-slice 0 always runs (K = 0: C = beta C)
+  gemm_tile<TA, TB, MODE, ATOMIC>(d, m0, n0, kbeg, kend);
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(NT) gemm_batched_kernel(const GemmDesc* descs) {
+  const GemmDesc d = descs[blockIdx.z];
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  if (d.M <= 0 || d.N <= 0 || m0 >= d.M || n0 >= d.N) return;
+  if (d.K <= 0) {  // C = beta C
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        const int64_t gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+        if (gm < d.M && gn < d.N) {
+          double* c = d.C + gm + gn * d.ldc;
+          *c = (d.beta == 0.0) ? 0.0 : d.beta * *c;
+        }
+      }
+    return;
+  }
+  gemm_tile<TA, TB, kGemmPlain, false>(d, m0, n0, 0, d.K);
+}
+
+template <bool TA, bool TB, int MODE>
+int launch(fraclap_ctx* ctx, const GemmDesc& d, int split_k, cudaStream_t st) {
+  const int64_t gx = cdiv(d.M, BM), gy = cdiv(d.N, BN);
+  FL_CHECK(ctx, gy <= 65535, FRACLAP_ERR_UNSUPPORTED, "gemm: N = %lld too large", (long long)d.N);
+  if (split_k <= 1 || d.K2 > 0) {
+    gemm_kernel<TA, TB, MODE, false><<<dim3((unsigned)gx, (unsigned)gy, 1), NT, 0, st>>>(
+        d, d.K > 0 ? d.K : 1);
+  } else {
+    int64_t kchunk = cdiv(cdiv(d.K, split_k), BK) * BK;
+    const int64_t gz = cdiv(d.K, kchunk);
+    gemm_kernel<TA, TB, MODE, true><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), NT, 0, st>>>(
+        d, kchunk);
+  }
+  FL_CUDA(ctx, cudaGetLastError());
+  return 0;
+}
+
+}  // namespace
+
+int gemm(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDesc& d, int split_k,
+         cudaStream_t st) {
+  if (d.M <= 0 || d.N <= 0) return 0;
+  FL_CHECK(ctx, mode != kGemmSymA || (!ta && d.M == d.K), FRACLAP_ERR_INVALID_ARG,
+           "gemm: symmetric A must be square and untransposed");
+  FL_CHECK(ctx, split_k <= 1 || d.beta == 1.0, FRACLAP_ERR_INVALID_ARG,
+           "gemm: split-K accumulates into C (beta must be 1)");
+  if (d.K <= 0 && d.K2 <= 0) {  // C = beta C
+    GemmDesc z = d;
+    z.K = 0;
+    z.K2 = 0;
+    return launch<false, false, kGemmPlain>(ctx, z, 1, st);
+  }
+#define FL_GEMM_CASE(TA, TB)                                                        \
+  if (ta == TA && tb == TB) {                                                       \
+    if (mode == kGemmPlain) return launch<TA, TB, kGemmPlain>(ctx, d, split_k, st); \
+    if (mode == kGemmLowerC) return launch<TA, TB, kGemmLowerC>(ctx, d, split_k, st); \
+  }
+  FL_GEMM_CASE(false, false)
+  FL_GEMM_CASE(false, true)
+  FL_GEMM_CASE(true, false)
+  FL_GEMM_CASE(true, true)
+#undef FL_GEMM_CASE
+  if (mode == kGemmSymA) {
+    if (tb) return launch<false, true, kGemmSymA>(ctx, d, split_k, st);
+    return launch<false, false, kGemmSymA>(ctx, d, split_k, st);
+  }
+  return set_error(ctx, FRACLAP_ERR_INVALID_ARG, "gemm: bad mode");
+}
+
+int gemm_batched(fraclap_ctx* ctx, bool ta, bool tb, const GemmDesc* d_descs, int count,
+                 int64_t max_m, int64_t max_n, cudaStream_t st) {
+  if (count <= 0 || max_m <= 0 || max_n <= 0) return 0;
+  const int64_t gx = cdiv(max_m, BM), gy = cdiv(max_n, BN);
+  FL_CHECK(ctx, gy <= 65535 && count <= 65535, FRACLAP_ERR_UNSUPPORTED, "gemm_batched: too large");
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)count);
+  if (!ta && !tb) gemm_batched_kernel<false, false><<<grid, NT, 0, st>>>(d_descs);
+  else if (!ta && tb) gemm_batched_kernel<false, true><<<grid, NT, 0, st>>>(d_descs);
+  else if (ta && !tb) gemm_batched_kernel<true, false><<<grid, NT, 0, st>>>(d_descs);
+  else gemm_batched_kernel<true, true><<<grid, NT, 0, st>>>(d_descs);
+  FL_CUDA(ctx, cudaGetLastError());
+  return 0;
+}
+
+}  // namespace fraclap

@@ -1,0 +1,214 @@
+// Internal declarations of the fraclap CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/fraclap.h"
+
+struct fraclap_ctx {
+  int device = 0;
+  int sm_count = 0;
+  int band_width = 32;
+  int leaf_size = 32;
+  double wait_timeout_s = 10.0;
+  long long wait_cycles = 0;     // wait_timeout_s in SM clock cycles (upper bound)
+  int32_t* d_status = nullptr;   // device status word (0 = ok, else a FRACLAP_ERR_*)
+  unsigned* d_barrier = nullptr; // grid-barrier state for cooperative kernels
+  void* ws = nullptr;            // context-owned workspace
+  size_t ws_bytes = 0;
+  std::string last_error;
+};
+
+namespace fraclap {
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+int set_error(fraclap_ctx* ctx, int code, const char* fmt, ...);
+
+#define FL_CUDA(ctx, call)                                                          \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return ::fraclap::set_error((ctx), FRACLAP_ERR_CUDA, "%s failed: %s (%s:%d)", #call, \
+                                  cudaGetErrorString(e_), __FILE__, __LINE__);     \
+  } while (0)
+
+#define FL_CHECK(ctx, cond, code, ...)                                   \
+  do {                                                                   \
+    if (!(cond)) return ::fraclap::set_error((ctx), (code), __VA_ARGS__); \
+  } while (0)
+
+#define FL_TRY(expr)          \
+  do {                        \
+    int rc_ = (expr);         \
+    if (rc_ != 0) return rc_; \
+  } while (0)
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Bump allocator over a workspace buffer.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, off = 0;
+  template <class T>
+  T* take(int64_t count) {
+    size_t bytes = align256(sizeof(T) * (size_t)(count > 0 ? count : 1));
+    if (base == nullptr) {  // sizing pass
+      off += bytes;
+      return nullptr;
+    }
+    if (off + bytes > cap) return nullptr;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+// Context workspace: the caller's buffer or the context's own (grown).
+int get_workspace(fraclap_ctx* ctx, void* work, size_t work_bytes, size_t need, Arena* arena);
+
+// ---------------------------------------------------------------------------
+// GEMM engine (FP64 SIMT; the FP64 pipe of GB300 is the bound, see gemm.cu)
+// ---------------------------------------------------------------------------
+enum GemmMode : int {
+  kGemmPlain = 0,     // C = alpha op(A) op(B) + beta C
+  kGemmLowerC = 1,    // only C(i, j) with i >= j is written (tiles above skipped)
+  kGemmSymA = 2,      // A is symmetric, only its lower triangle is read (M == K)
+};
+
+struct GemmDesc {
+  int64_t M, N, K;
+  const double* A; int64_t lda;
+  const double* B; int64_t ldb;
+  double* C; int64_t ldc;
+  // optional second product accumulated into the same C (K2 = 0: none):
+  // C = alpha (op(A) op(B) + op(A2) op(B2)) + beta C, same transposes.
+  const double* A2; int64_t lda2;
+  const double* B2; int64_t ldb2;
+  int64_t K2;
+  double alpha, beta;
+};
+
+// One product; split_k > 1 accumulates partial sums with atomics (beta must be
+// 1 and C pre-scaled/zeroed by the caller).
+int gemm(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDesc& d, int split_k,
+         cudaStream_t st);
+// Batched over a device array of descriptors; grid covers max_m x max_n tiles,
+// tiles outside a descriptor's M x N exit.  Descriptors with M, N or K <= 0
+// are skipped.
+int gemm_batched(fraclap_ctx* ctx, bool ta, bool tb, const GemmDesc* d_descs, int count,
+                 int64_t max_m, int64_t max_n, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// stages
+// ---------------------------------------------------------------------------
+// Stage 1 (dense -> band) workspace: compact-WY panels kept for the
+// back-transformation.
+struct Stage1 {
+  double* Vstore;    // sum_j m_j * b: explicit V of every panel
+  double* Tstore;    // npanel * b * b
+  double* tau;       // npanel * b
+  double* XT;        // n * b
+  double* X;         // n * b
+  double* Y;         // b * b
+  double* Mm;        // b * b
+  double* gram;      // b * b
+  double* partials;  // 2 * G * 2b
+  int64_t npanel;
+  int64_t vtotal;
+};
+int64_t stage1_panels(int64_t n, int b);
+int stage1_take(Arena* ar, int64_t n, int b, int G, Stage1* s);
+int sy2sb_run(fraclap_ctx* ctx, double* Aw, int64_t n, int64_t lda, int b, double* band,
+              Stage1* s, cudaStream_t st);
+int q1_apply_run(fraclap_ctx* ctx, const Stage1* s, int64_t n, int b, double* Z, int64_t ldz,
+                 int64_t ncols, double* W1, double* W2, cudaStream_t st);
+
+// Stage 2 (band -> tridiagonal) workspace: the bulge-chasing reflectors.
+struct Stage2 {
+  double* refl;   // (n-1) * kmax * b
+  double* rtau;   // (n-1) * kmax
+  int* progress;  // n + 1
+  int64_t kmax;
+};
+int stage2_take(Arena* ar, int64_t n, int b, Stage2* s);
+int sb2st_run(fraclap_ctx* ctx, double* band, int64_t n, int b, double* d, double* e, Stage2* s,
+              cudaStream_t st);
+int q2_apply_run(fraclap_ctx* ctx, const Stage2* s, int64_t n, int b, double* Z, int64_t ldz,
+                 int64_t ncols, cudaStream_t st);
+
+size_t stedc_ws(const fraclap_ctx* ctx, int64_t n);
+int stedc_run(fraclap_ctx* ctx, const double* d, const double* e, int64_t n, double* lambda,
+              double* Z, int64_t ldz, Arena* arena, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu_u(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Records the first failure code in the device status word.
+__device__ __forceinline__ void raise_status(int32_t* status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+// Grid-wide barrier for cooperative launches, bounded in time.
+// state[0] = arrival count, state[1] = generation.  Returns false (after
+// raising FRACLAP_ERR_TIMEOUT) when the wait exceeded `limit` cycles or when
+// the status word already holds an error.
+__device__ __forceinline__ bool grid_barrier(unsigned* state, unsigned nblocks, long long limit,
+                                             int32_t* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned gen = ld_acquire_gpu_u(state + 1);
+    __threadfence();
+    unsigned arrived = atomicAdd(state, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(state, 0u);
+      __threadfence();
+      atomicAdd(state + 1, 1u);
+    } else {
+      long long t0 = clock64();
+      while (ld_acquire_gpu_u(state + 1) == gen) {
+        if (clock64() - t0 > limit) {
+          raise_status(status, FRACLAP_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int32_t*)status != 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+}  // namespace fraclap

@@ -1,0 +1,281 @@
+// Stage 1 of the two-stage reduction: dense symmetric -> band of half-width b.
+//
+// Panel j (columns j0..j0+b-1) is factorised P = Q_j R with Q_j = I - V T V^T
+// (compact WY) by a cooperative kernel: the panel's rows are split over the
+// CTAs and stay in shared memory, and each Householder column costs one
+// grid-wide reduction (the dot products of the pivot column with every later
+// column, from which the reflector and its effect on the panel follow).  The
+// trailing matrix is then updated as A22 <- Q^T A22 Q = A22 - W V^T - V W^T
+// with X = A22 (V T), W = X - 1/2 V (T^T V^T X), through the GEMM engine
+// (symmetric A22 read from its lower triangle; lower-triangular rank-2b
+// update).  FP64 throughout; the Householder norms and scalings stay FP64.
+#include "internal.cuh"
+
+namespace fraclap {
+namespace {
+
+constexpr int PQR_NT = 256;
+
+// Cooperative panel QR.  P: m x bw panel (ld ldp) in the working matrix.
+// On exit P holds R on and above its diagonal (the band block) and the
+// reflectors below it; Vout gets the explicit unit lower-trapezoidal V
+// (m x bw, ld ldv); tau[bw]; T: bw x bw upper triangular (ld bw).
+__global__ void __launch_bounds__(PQR_NT)
+panel_qr_kernel(double* P, int64_t ldp, int64_t m, int bw, double* Vout, int64_t ldv,
+                double* tau, double* T, double* partials, double* gram, unsigned* bar,
+                long long limit, int32_t* status, int64_t rows_per_cta) {
+  extern __shared__ double S[];  // rows_per_cta x bw, column-major (ld rows_per_cta)
+  __shared__ double red[2 * 64 + 4];
+  __shared__ double sw[64];
+  __shared__ double s_coef[4];  // beta, v0, tau
+  const unsigned G = gridDim.x;
+  const int64_t rb = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t re = (rb + rows_per_cta < m) ? rb + rows_per_cta : m;
+  const int64_t nr = (re > rb) ? re - rb : 0;
+  const int64_t ld = rows_per_cta;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = PQR_NT / 32;
+
+  for (int c = 0; c < bw; ++c)
+    for (int64_t r = tid; r < nr; r += PQR_NT) S[r + c * ld] = P[(rb + r) + c * ldp];
+  __syncthreads();
+
+  const int nref = (m < bw) ? (int)m : bw;
+  const int stride = 2 * bw;
+  for (int c = 0; c < nref; ++c) {
+    double* part = partials + (size_t)(c & 1) * G * stride + (size_t)blockIdx.x * stride;
+    // partial dot products over this CTA's rows r >= c
+    const int64_t r0 = (c > rb) ? c - rb : 0;  // first local row with global row >= c
+    for (int j = c + warp; j < bw; j += nwarp) {
+      double s = 0.0;
+      for (int64_t r = r0 + lane; r < nr; r += 32) {
+        const int64_t gr = rb + r;
+        if (j == c && gr == c) continue;  // g_c is the tail sum of squares (rows > c)
+        s += S[r + c * ld] * S[r + j * ld];
+      }
+      s = warp_sum(s);
+      if (lane == 0) part[j] = s;
+    }
+    for (int j = c + tid; j < bw; j += PQR_NT)
+      part[bw + j] = (c >= rb && c < re) ? S[(c - rb) + j * ld] : 0.0;
+    if (!grid_barrier(bar, G, limit, status)) return;
+    // every CTA reduces the partials in the same order (identical results)
+    for (int t = tid; t < 2 * (bw - c); t += PQR_NT) {
+      const int slot = (t < bw - c) ? c + t : bw + c + (t - (bw - c));
+      const double* base = partials + (size_t)(c & 1) * G * stride;
+      double s = 0.0;
+      for (unsigned b = 0; b < G; ++b) s += __ldcg(base + (size_t)b * stride + slot);
+      red[(t < bw - c) ? t : 64 + (t - (bw - c))] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double tail = red[0], x0 = red[64];
+      double beta = x0, v0 = 1.0, tu = 0.0;
+      if (tail > 0.0 && m - c > 1) {
+        const double alpha = sqrt(x0 * x0 + tail);
+        beta = (x0 >= 0.0) ? -alpha : alpha;
+        v0 = x0 - beta;
+        tu = (beta - x0) / beta;
+      }
+      s_coef[0] = beta;
+      s_coef[1] = v0;
+      s_coef[2] = tu;
+      if (blockIdx.x == 0) tau[c] = tu;
+    }
+    __syncthreads();
+    const double beta = s_coef[0], v0 = s_coef[1], tu = s_coef[2];
+    // w_j = tau v^T p_j, v^T p_j = (g_j - beta p_j(c)) / v0
+    for (int j = c + 1 + tid; j < bw; j += PQR_NT) {
+      const double g = red[j - c], pc = red[64 + (j - c)];
+      sw[j] = (tu == 0.0) ? 0.0 : tu * (g - beta * pc) / v0;
+    }
+    __syncthreads();
+    // update own rows (global row >= c)
+    const double inv_v0 = 1.0 / v0;
+    for (int64_t r = r0 + tid; r < nr; r += PQR_NT) {
+      const int64_t gr = rb + r;
+      double vr;
+      if (gr == c) {
+        vr = 1.0;
+        S[r + c * ld] = beta;
+      } else {
+        vr = (tu == 0.0) ? 0.0 : S[r + c * ld] * inv_v0;
+        S[r + c * ld] = vr;
+      }
+      if (tu != 0.0)
+        for (int j = c + 1; j < bw; ++j) S[r + j * ld] -= vr * sw[j];
+    }
+    __syncthreads();
+  }
+  for (int c = nref; c < bw && blockIdx.x == 0 && tid == 0; ++c) tau[c] = 0.0;
+
+  // write back the panel (R and the reflectors) and the explicit V
+  for (int c = 0; c < bw; ++c)
+    for (int64_t r = tid; r < nr; r += PQR_NT) {
+      const int64_t gr = rb + r;
+      const double s = S[r + c * ld];
+      P[gr + c * ldp] = s;
+      double v = 0.0;
+      if (c < nref) v = (gr < c) ? 0.0 : (gr == c ? 1.0 : s);
+      Vout[gr + c * ldv] = v;
+    }
+  // Gram matrix V^T V (upper part) accumulated over CTAs
+  for (int p = tid; p < bw * bw; p += PQR_NT) {
+    const int i = p % bw, j = p / bw;
+    if (i > j || j >= nref) continue;
+    double s = 0.0;
+    for (int64_t r = 0; r < nr; ++r) {
+      const int64_t gr = rb + r;
+      if (gr < j) continue;
+      const double vi = (gr == i) ? 1.0 : (gr < i ? 0.0 : S[r + i * ld]);
+      const double vj = (gr == j) ? 1.0 : S[r + j * ld];
+      s += vi * vj;
+    }
+    if (s != 0.0) atomicAdd(&gram[i + j * bw], s);
+  }
+  if (!grid_barrier(bar, G, limit, status)) return;
+  if (blockIdx.x != 0) return;
+  // T: T(i,i) = tau_i, T(0:i, i) = -tau_i T(0:i,0:i) (V^T v_i)(0:i)
+  __shared__ double Ts[64 * 64];
+  __shared__ double y[64];
+  for (int p = tid; p < bw * bw; p += PQR_NT) Ts[p] = 0.0;
+  __syncthreads();
+  for (int i = 0; i < bw; ++i) {
+    const double ti = __ldcg(tau + i);
+    if (tid < i) y[tid] = __ldcg(gram + tid + i * bw);
+    __syncthreads();
+    if (tid < i) {
+      double s = 0.0;
+      for (int q = tid; q < i; ++q) s += Ts[tid + q * bw] * y[q];
+      Ts[tid + i * bw] = -ti * s;
+    }
+    if (tid == 0) Ts[i + i * bw] = ti;
+    __syncthreads();
+  }
+  for (int p = tid; p < bw * bw; p += PQR_NT) T[p] = Ts[p];
+}
+
+// Band extraction: band(off, j) = A(j + off, j) for off <= b, 0 for b < off < ldb.
+__global__ void extract_band(const double* A, int64_t lda, int64_t n, int b, double* band,
+                             int ldb) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n * ldb) return;
+  const int off = (int)(p % ldb);
+  const int64_t j = p / ldb;
+  const int64_t i = j + off;
+  band[p] = (off <= b && i < n) ? A[i + j * lda] : 0.0;
+}
+
+}  // namespace
+
+int64_t stage1_panels(int64_t n, int b) { return (n > b) ? cdiv(n - b, b) : 0; }
+
+int stage1_take(Arena* ar, int64_t n, int b, int G, Stage1* s) {
+  s->npanel = stage1_panels(n, b);
+  s->vtotal = 0;
+  for (int64_t j = 0; j < s->npanel; ++j) s->vtotal += (n - j * b - b) * b;
+  s->Vstore = ar->take<double>(s->vtotal);
+  s->Tstore = ar->take<double>(s->npanel * b * b);
+  s->tau = ar->take<double>(s->npanel * b);
+  s->XT = ar->take<double>(n * b);
+  s->X = ar->take<double>(n * b);
+  s->Y = ar->take<double>((int64_t)b * b);
+  s->Mm = ar->take<double>((int64_t)b * b);
+  s->gram = ar->take<double>((int64_t)b * b);
+  s->partials = ar->take<double>(2 * (int64_t)G * 2 * b);
+  return 0;
+}
+
+static int panel_grid(fraclap_ctx* ctx, int64_t m, int bw, int64_t* rows_per_cta, size_t* smem) {
+  int G = ctx->sm_count;
+  if (m < (int64_t)G * 8) G = (int)cdiv(m, 8);
+  if (G < 1) G = 1;
+  *rows_per_cta = cdiv(m, G);
+  G = (int)cdiv(m, *rows_per_cta);
+  *smem = (size_t)(*rows_per_cta) * bw * sizeof(double);
+  return G;
+}
+
+// Reduces Aw (n x n, lower triangle valid, overwritten) to band form and
+// writes the band (ld 2b, offsets 0..2b-1, zero beyond b) to `band`.
+int sy2sb_run(fraclap_ctx* ctx, double* Aw, int64_t n, int64_t lda, int b, double* band,
+              Stage1* s, cudaStream_t st) {
+  const int ldb = 2 * b;
+  int64_t voff = 0;
+  for (int64_t p = 0; p < s->npanel; ++p) {
+    const int64_t j0 = p * b, m = n - j0 - b;
+    double* P = Aw + (j0 + b) + j0 * lda;
+    double* V = s->Vstore + voff;
+    double* T = s->Tstore + p * b * b;
+    int64_t rows_per_cta;
+    size_t smem;
+    const int G = panel_grid(ctx, m, b, &rows_per_cta, &smem);
+    FL_CHECK(ctx, smem <= 200 * 1024, FRACLAP_ERR_UNSUPPORTED, "sy2sb: panel too tall (%lld)", (long long)m);
+    FL_CUDA(ctx, cudaMemsetAsync(s->gram, 0, sizeof(double) * b * b, st));
+    FL_CUDA(ctx, cudaMemsetAsync(ctx->d_barrier, 0, 2 * sizeof(unsigned), st));
+    {
+      double* tau = s->tau + p * b;
+      int64_t ldp = lda, ldv = m, mm = m;
+      int bw = b;
+      double* partials = s->partials;
+      double* gram = s->gram;
+      unsigned* bar = ctx->d_barrier;
+      long long limit = ctx->wait_cycles;
+      int32_t* status = ctx->d_status;
+      void* args[] = {&P, &ldp, &mm, &bw, &V, &ldv, &tau, &T, &partials, &gram, &bar, &limit, &status, &rows_per_cta};
+      FL_CUDA(ctx, cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(PQR_NT), args, smem, st));
+    }
+    double* A22 = Aw + (j0 + b) + (j0 + b) * lda;
+    GemmDesc d{};
+    // XT = V T  (m x b)
+    d = GemmDesc{m, b, b, V, m, T, b, s->XT, m, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+    FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+    // X = A22 XT (A22 symmetric, lower triangle)
+    d = GemmDesc{m, b, m, A22, lda, s->XT, m, s->X, m, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+    FL_TRY(gemm(ctx, false, false, kGemmSymA, d, 1, st));
+    // Y = V^T X  (b x b), split over the long dimension
+    FL_CUDA(ctx, cudaMemsetAsync(s->Y, 0, sizeof(double) * b * b, st));
+    d = GemmDesc{b, b, m, V, m, s->X, m, s->Y, b, nullptr, 0, nullptr, 0, 0, 1.0, 1.0};
+    FL_TRY(gemm(ctx, true, false, kGemmPlain, d, (int)cdiv(m, 256), st));
+    // Mm = T^T Y
+    d = GemmDesc{b, b, b, T, b, s->Y, b, s->Mm, b, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+    FL_TRY(gemm(ctx, true, false, kGemmPlain, d, 1, st));
+    // W = X - 1/2 V Mm  (in X)
+    d = GemmDesc{m, b, b, V, m, s->Mm, b, s->X, m, nullptr, 0, nullptr, 0, 0, -0.5, 1.0};
+    FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+    // A22 -= W V^T + V W^T  (lower triangle)
+    d = GemmDesc{m, m, b, s->X, m, V, m, A22, lda, V, m, s->X, m, b, -1.0, 1.0};
+    FL_TRY(gemm(ctx, false, true, kGemmLowerC, d, 1, st));
+    voff += m * b;
+  }
+  extract_band<<<(unsigned)cdiv(n * ldb, 256), 256, 0, st>>>(Aw, lda, n, b, band, ldb);
+  FL_CUDA(ctx, cudaGetLastError());
+  return 0;
+}
+
+// Back-transformation by Q1 = Q_0 Q_1 ... Q_{p-1}: Z <- Q1 Z (n x ncols).
+// Applied from the last panel to the first: Z(rows_j, :) -= V_j (T_j (V_j^T Z(rows_j, :))).
+int q1_apply_run(fraclap_ctx* ctx, const Stage1* s, int64_t n, int b, double* Z, int64_t ldz,
+                 int64_t ncols, double* W1, double* W2, cudaStream_t st) {
+  int64_t voff = s->vtotal;
+  for (int64_t p = s->npanel - 1; p >= 0; --p) {
+    const int64_t j0 = p * b, m = n - j0 - b;
+    voff -= m * b;
+    const double* V = s->Vstore + voff;
+    const double* T = s->Tstore + p * b * b;
+    double* Zr = Z + (j0 + b);
+    GemmDesc d{};
+    // W1 = V^T Zr  (b x ncols)
+    d = GemmDesc{b, ncols, m, V, m, Zr, ldz, W1, b, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+    FL_TRY(gemm(ctx, true, false, kGemmPlain, d, 1, st));
+    // W2 = T W1
+    d = GemmDesc{b, ncols, b, T, b, W1, b, W2, b, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+    FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+    // Zr -= V W2
+    d = GemmDesc{m, ncols, b, V, m, W2, b, Zr, ldz, nullptr, 0, nullptr, 0, 0, -1.0, 1.0};
+    FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+  }
+  return 0;
+}
+
+}  // namespace fraclap

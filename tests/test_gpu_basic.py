@@ -1,0 +1,115 @@
+"""GPU parity of the assembly kernel, the FP64 GEMM engine and the spectral
+apply against the FP64 CPU oracle (all calls go through the C ABI)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1911_11906_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _F():
+    import paper_1911_11906_gb300 as F
+    return F
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _colmajor(a):
+    a = np.asfortranarray(a, dtype=np.float64)
+    return torch.from_numpy(a.T.copy()).cuda().t()
+
+
+@pytest.mark.parametrize("which", ["square48", "ellipse128", "holed_cube", "golden2d", "golden3d", "strip"])
+def test_assembly_bitwise(which):
+    F = _F()
+    if which == "square48":
+        p = I.square_problem(48); mask, h = p.mask, p.h
+    elif which == "ellipse128":
+        p = I.ellipse_problem(); mask, h = p.mask, p.h
+    elif which == "holed_cube":
+        p = I.holed_cube_problem(16, n_forcings=1); mask, h = p.mask, p.h
+    elif which == "strip":
+        mask, h = np.ones((1, 37), np.uint8), 1.0 / 38
+    else:
+        name = "assemble_2d_3x2.txt" if which == "golden2d" else "assemble_3d_2x2x2.txt"
+        from test_oracle_pins import _read_golden
+        mask, h, _ = _read_golden(name)
+    idx_o, A_o = O.assemble(mask, h)
+    out = F.fd_assemble(_cuda(mask), h, dense=A_o.n <= 12000)
+    assert out["n"] == A_o.n
+    np.testing.assert_array_equal(out["idx"].cpu().numpy().reshape(-1), idx_o)
+    np.testing.assert_array_equal(out["rowptr"].cpu().numpy(), A_o.rowptr)
+    np.testing.assert_array_equal(out["col"].cpu().numpy(), A_o.col)
+    np.testing.assert_array_equal(out["val"].cpu().numpy(), A_o.val)  # bit-exact doubles
+    if out["A"] is not None:
+        np.testing.assert_array_equal(out["A"].cpu().numpy(), A_o.dense())
+
+
+def test_assembly_empty_mask():
+    F = _F()
+    out = F.fd_assemble(_cuda(np.zeros((5, 7), np.uint8)), 0.1)
+    assert out["n"] == 0 and out["rowptr"].cpu().numpy().tolist() == [0]
+    assert np.all(out["idx"].cpu().numpy() == -1)
+
+
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (63, 65, 17), (130, 70, 200), (64, 64, 0), (257, 3, 1000)])
+def test_dgemm_against_float64_reference(ta, tb, m, n, k):
+    F = _F()
+    rng = np.random.default_rng(m * 1000 + n * 10 + k)
+    A = rng.standard_normal((k, m) if ta else (m, k))
+    B = rng.standard_normal((n, k) if tb else (k, n))
+    C0 = rng.standard_normal((m, n))
+    ref = 0.5 * (A.T if ta else A) @ (B.T if tb else B) - 2.0 * C0
+    C = _colmajor(C0)
+    F.dgemm(_colmajor(A), _colmajor(B), trans_a=ta, trans_b=tb, alpha=0.5, beta=-2.0, C=C)
+    got = C.cpu().numpy()
+    scale = np.abs(A).max(initial=1) * np.abs(B).max(initial=1) * max(k, 1)
+    assert np.max(np.abs(got - ref)) <= 1e-14 * scale + 1e-13
+
+
+@pytest.fixture(scope="module")
+def square_small():
+    p = I.square_problem(20)
+    _, A = O.assemble(p.mask, p.h)
+    lam, V = O.eig_full(A.dense())
+    return p, A, lam, V
+
+
+def test_frac_apply_matches_oracle(square_small):
+    F = _F()
+    p, A, lam, V = square_small
+    U_o = O.frac_apply(V, lam, p.F, p.pair_f, p.pair_alpha)
+    U = F.frac_apply(_colmajor(V), _cuda(lam), _colmajor(p.F), p.pair_f, p.pair_alpha).cpu().numpy()
+    for j in range(U_o.shape[1]):
+        assert np.linalg.norm(U[:, j] - U_o[:, j]) <= 1e-13 * np.linalg.norm(U_o[:, j])
+
+
+def test_frac_apply_edge_cases(square_small):
+    F = _F()
+    p, A, lam, V = square_small
+    Vd, ld = _colmajor(V), _cuda(lam)
+    # alpha = 0 returns f; repeated forcings; negative orders
+    U = F.frac_apply(Vd, ld, _colmajor(p.F), [0, 0, 1, 2], [0.0, -2.0, 0.0, 2.0]).cpu().numpy()
+    assert np.linalg.norm(U[:, 0] - p.F[:, 0]) <= 1e-13 * np.linalg.norm(p.F[:, 0])
+    Af = O.spmv(A, p.F[:, 0])
+    assert np.linalg.norm(U[:, 1] - Af) <= 1e-12 * np.linalg.norm(Af)
+    u2 = O.band_solve(A, p.F[:, 2])
+    assert np.linalg.norm(U[:, 3] - u2) <= 1e-12 * np.linalg.norm(u2)
+    # a non-positive eigenvalue with alpha != 0 is reported
+    bad = lam.copy()
+    bad[3] = 0.0
+    with pytest.raises(F.FraclapError) as ei:
+        F.frac_apply(Vd, _cuda(bad), _colmajor(p.F), [0], [1.0])
+    assert ei.value.code == -2
+    # ... but alpha = 0 never evaluates the power
+    F.frac_apply(Vd, _cuda(bad), _colmajor(p.F), [0], [0.0])
