@@ -156,6 +156,28 @@ int fraclap_dgemm(fraclap_ctx* ctx, int trans_a, int trans_b, int64_t m, int64_t
                   double alpha, const double* A_dev, int64_t lda, const double* B_dev,
                   int64_t ldb, double beta, double* C_dev, int64_t ldc, fraclap_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper; it reports per-phase wall
+ * times, Table I, and these give the same view of this library).
+ * ---------------------------------------------------------------------- */
+enum {
+  FRACLAP_STAGE_ASSEMBLE = 0,       /* fd_assemble */
+  FRACLAP_STAGE_BAND_REDUCTION = 1, /* dense -> band (panels + trailing updates) */
+  FRACLAP_STAGE_BULGE_CHASING = 2,  /* band -> tridiagonal */
+  FRACLAP_STAGE_TRIDIAG_DC = 3,     /* tridiagonal divide and conquer */
+  FRACLAP_STAGE_BACK_Q2 = 4,        /* back-transformation by the bulge-chasing reflectors */
+  FRACLAP_STAGE_BACK_Q1 = 5,        /* back-transformation by the panel reflectors */
+  FRACLAP_STAGE_APPLY = 6,          /* frac_apply */
+  FRACLAP_STAGE_COUNT = 7
+};
+/* With enable != 0, every later stage records a CUDA event pair on its stream. */
+int fraclap_set_profiling(fraclap_ctx* ctx, int enable);
+/* Waits for the recorded events, writes the summed milliseconds (and the
+ * number of records, count_out may be NULL) per stage id, and forgets them. */
+int fraclap_stage_times(fraclap_ctx* ctx, double* ms_out, int64_t* count_out, int nstages);
+/* Number of kernels the context has launched so far. */
+long long fraclap_launch_count(const fraclap_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

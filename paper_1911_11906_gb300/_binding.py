@@ -30,6 +30,9 @@ SIGNATURES = {
     "fraclap_tridiagonalize": (_i32, [_p, _p, _i64, _i64, _p, _p, _p, _i64, _p, _sz, _p]),
     "fraclap_tridiag_workspace_bytes": (_sz, [_p, _i64]),
     "fraclap_tridiag_eig": (_i32, [_p, _p, _p, _i64, _p, _p, _i64, _p, _sz, _p]),
+    "fraclap_set_profiling": (_i32, [_p, _i32]),
+    "fraclap_stage_times": (_i32, [_p, _p, _p, _i32]),
+    "fraclap_launch_count": (ctypes.c_longlong, [_p]),
     "fraclap_dgemm": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64, _p]),
 }
 
@@ -102,6 +105,22 @@ class Context:
         if rc != 0:
             msg = self.lib.fraclap_last_error(self.handle).decode()
             raise FraclapError(rc, msg)
+
+    STAGES = ("assemble", "band_reduction", "bulge_chasing", "tridiag_dc", "back_q2", "back_q1", "apply")
+
+    def set_profiling(self, enable: bool = True):
+        self.check(self.lib.fraclap_set_profiling(self.handle, int(enable)))
+
+    def stage_times(self) -> dict:
+        """{stage: (milliseconds, records)} summed since the last call."""
+        n = len(self.STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        self.check(self.lib.fraclap_stage_times(self.handle, ms, cnt, n))
+        return {s: (ms[i], cnt[i]) for i, s in enumerate(self.STAGES)}
+
+    def launch_count(self) -> int:
+        return int(self.lib.fraclap_launch_count(self.handle))
 
     def sync(self, stream=None):
         """Waits for the stream and raises if a kernel recorded a failure."""

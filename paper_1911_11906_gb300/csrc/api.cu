@@ -106,17 +106,30 @@ size_t eig_ws_bytes(const fraclap_ctx* ctx, int64_t n, bool with_dc) {
 int reduce(fraclap_ctx* ctx, const double* A, int64_t n, int64_t lda, EigWork* w, cudaStream_t st) {
   const int b = ctx->band_width;
   copy_lower<<<(unsigned)cdiv(n * n, 256), 256, 0, st>>>(A, lda, w->Aw, n, n);
+  count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
-  FL_TRY(sy2sb_run(ctx, w->Aw, n, n, b, w->band, &w->s1, st));
-  FL_TRY(sb2st_run(ctx, w->band, n, b, w->d, w->e, &w->s2, st));
+  {
+    StageTimer t(ctx, kStageBandReduction, st);
+    FL_TRY(sy2sb_run(ctx, w->Aw, n, n, b, w->band, &w->s1, st));
+  }
+  {
+    StageTimer t(ctx, kStageBulgeChasing, st);
+    FL_TRY(sb2st_run(ctx, w->band, n, b, w->d, w->e, &w->s2, st));
+  }
   return 0;
 }
 
 int back_transform(fraclap_ctx* ctx, int64_t n, EigWork* w, double* Z, int64_t ldz,
                    cudaStream_t st) {
   const int b = ctx->band_width;
-  FL_TRY(q2_apply_run(ctx, &w->s2, n, b, Z, ldz, n, st));
-  FL_TRY(q1_apply_run(ctx, &w->s1, n, b, Z, ldz, n, w->W1, w->W2, st));
+  {
+    StageTimer t(ctx, kStageBackQ2, st);
+    FL_TRY(q2_apply_run(ctx, &w->s2, n, b, Z, ldz, n, st));
+  }
+  {
+    StageTimer t(ctx, kStageBackQ1, st);
+    FL_TRY(q1_apply_run(ctx, &w->s1, n, b, Z, ldz, n, w->W1, w->W2, st));
+  }
   return 0;
 }
 
@@ -223,7 +236,10 @@ extern "C" int eig_full(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_
   eig_take(&ar, ctx, n, &w);
   FL_CHECK(ctx, w.s2.progress != nullptr, FRACLAP_ERR_ALLOC, "eig_full: workspace too small");
   FL_TRY(reduce(ctx, A_dev, n, lda, &w, st));
-  FL_TRY(stedc_run(ctx, w.d, w.e, n, lambda_dev, V_dev, ldv, &ar, st));
+  {
+    StageTimer t(ctx, kStageTridiagDC, st);
+    FL_TRY(stedc_run(ctx, w.d, w.e, n, lambda_dev, V_dev, ldv, &ar, st));
+  }
   FL_TRY(back_transform(ctx, n, &w, V_dev, ldv, st));
   if (info_dev) FL_CUDA(ctx, cudaMemcpyAsync(info_dev, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   return 0;
@@ -249,6 +265,7 @@ extern "C" int fraclap_tridiagonalize(fraclap_ctx* ctx, const double* A_dev, int
   if (n > 1) FL_CUDA(ctx, cudaMemcpyAsync(e_dev, w.e, sizeof(double) * (n - 1), cudaMemcpyDeviceToDevice, st));
   if (Q_dev) {
     set_identity<<<(unsigned)cdiv(n * n, 256), 256, 0, st>>>(Q_dev, ldq, n);
+    count_launch(ctx);
     FL_CUDA(ctx, cudaGetLastError());
     FL_TRY(back_transform(ctx, n, &w, Q_dev, ldq, st));
   }
@@ -266,6 +283,7 @@ extern "C" int fraclap_tridiag_eig(fraclap_ctx* ctx, const double* d_dev, const 
   FL_CHECK(ctx, ldz >= n, FRACLAP_ERR_INVALID_ARG, "tridiag_eig: ldz < n");
   Arena ar;
   FL_TRY(get_workspace(ctx, work_dev, work_bytes, stedc_ws(ctx, n) + 4096, &ar));
+  StageTimer t(ctx, kStageTridiagDC, (cudaStream_t)stream);
   return stedc_run(ctx, d_dev, e_dev, n, lambda_dev, Z_dev, ldz, &ar, (cudaStream_t)stream);
 }
 
@@ -282,3 +300,35 @@ extern "C" int fraclap_dgemm(fraclap_ctx* ctx, int trans_a, int trans_b, int64_t
   GemmDesc d{m, n, k, A_dev, lda, B_dev, ldb, C_dev, ldc, nullptr, 0, nullptr, 0, 0, alpha, beta};
   return gemm(ctx, trans_a != 0, trans_b != 0, kGemmPlain, d, 1, (cudaStream_t)stream);
 }
+
+extern "C" int fraclap_set_profiling(fraclap_ctx* ctx, int enable) {
+  if (!ctx) return FRACLAP_ERR_INVALID_ARG;
+  ctx->profiling = enable != 0;
+  return 0;
+}
+
+extern "C" int fraclap_stage_times(fraclap_ctx* ctx, double* ms_out, int64_t* count_out, int nstages) {
+  if (!ctx || nstages < 0 || (nstages > 0 && !ms_out)) return FRACLAP_ERR_INVALID_ARG;
+  for (int i = 0; i < nstages; ++i) {
+    ms_out[i] = 0.0;
+    if (count_out) count_out[i] = 0;
+  }
+  int rc = 0;
+  for (auto& ev : ctx->stage_events) {
+    float ms = 0.0f;
+    cudaError_t e = cudaEventSynchronize(ev.stop);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.start, ev.stop);
+    if (e != cudaSuccess && rc == 0)
+      rc = set_error(ctx, FRACLAP_ERR_CUDA, "stage timing: %s", cudaGetErrorString(e));
+    if (ev.stage >= 0 && ev.stage < nstages) {
+      ms_out[ev.stage] += ms;
+      if (count_out) count_out[ev.stage] += 1;
+    }
+    cudaEventDestroy(ev.start);
+    cudaEventDestroy(ev.stop);
+  }
+  ctx->stage_events.clear();
+  return rc;
+}
+
+extern "C" long long fraclap_launch_count(const fraclap_ctx* ctx) { return ctx ? ctx->launches : -1; }

@@ -58,6 +58,7 @@ extern "C" int frac_apply(fraclap_ctx* ctx, const double* V_dev, int64_t ldv,
            FRACLAP_ERR_INVALID_ARG, "frac_apply: null pointer");
   FL_CHECK(ctx, ldv >= n && ldf >= n && ldu >= n, FRACLAP_ERR_INVALID_ARG, "frac_apply: leading dimension < n");
   FL_CHECK(ctx, k <= 65535 * 64 && m <= 65535 * 64, FRACLAP_ERR_UNSUPPORTED, "frac_apply: too many pairs");
+  StageTimer timer(ctx, kStageApply, st);
   Arena ar;
   FL_TRY(get_workspace(ctx, work_dev, work_bytes, fraclap_apply_workspace_bytes(n, m, k), &ar));
   double* W = ar.take<double>(n * m);
@@ -69,6 +70,7 @@ extern "C" int frac_apply(fraclap_ctx* ctx, const double* V_dev, int64_t ldv,
   FL_CHECK(ctx, k <= 65535, FRACLAP_ERR_UNSUPPORTED, "frac_apply: at most 65535 pairs per call");
   spectral_scale<<<dim3((unsigned)cdiv(n, 256), (unsigned)k), 256, 0, st>>>(
       lambda_dev, n, W, n, pair_f_dev, pair_alpha_dev, k, m, C, n, ctx->d_status);
+  count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   // U = V C
   d = GemmDesc{n, k, n, V_dev, ldv, C, n, U_dev, ldu, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};

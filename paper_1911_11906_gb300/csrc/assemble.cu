@@ -186,6 +186,7 @@ extern "C" int fd_assemble(fraclap_ctx* ctx, const uint8_t* mask_dev, int dim, c
                            double* A_dense_dev, int64_t lda, fraclap_stream_t stream) {
   if (!ctx) return FRACLAP_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  StageTimer timer(ctx, kStageAssemble, st);
   FL_CHECK(ctx, ext && (dim == 2 || dim == 3), FRACLAP_ERR_INVALID_ARG, "fd_assemble: dim must be 2 or 3");
   FL_CHECK(ctx, ext[0] >= 0 && ext[1] >= 0 && ext[2] >= 1 && (dim == 3 || ext[2] == 1),
            FRACLAP_ERR_INVALID_ARG, "fd_assemble: bad extents");
@@ -207,10 +208,15 @@ extern "C" int fd_assemble(fraclap_ctx* ctx, const uint8_t* mask_dev, int dim, c
     FL_CHECK(ctx, n_out && nnz_out, FRACLAP_ERR_INVALID_ARG, "fd_assemble: null n_out/nnz_out");
     if (len == 0) { *n_out = 0; *nnz_out = 0; return 0; }
     scan_tile_sums<<<(unsigned)ntiles, SCAN_NT, 0, st>>>(MaskCount{mask_dev}, len, tile);
+    count_launch(ctx);
     scan_tile_offsets<<<1, SCAN_NT, 0, st>>>(tile, ntiles, total);
+    count_launch(ctx);
     number_dofs<<<(unsigned)ntiles, SCAN_NT, 0, st>>>(mask_dev, len, tile, idx_dev);
+    count_launch(ctx);
     scan_tile_sums<<<(unsigned)ntiles, SCAN_NT, 0, st>>>(RowCount{mask_dev, G}, len, tile);
+    count_launch(ctx);
     scan_tile_offsets<<<1, SCAN_NT, 0, st>>>(tile, ntiles, total + 1);
+    count_launch(ctx);
     FL_CUDA(ctx, cudaGetLastError());
     int64_t host[2];
     FL_CUDA(ctx, cudaMemcpyAsync(host, total, sizeof(host), cudaMemcpyDeviceToHost, st));
@@ -229,9 +235,13 @@ extern "C" int fd_assemble(fraclap_ctx* ctx, const uint8_t* mask_dev, int dim, c
     return 0;
   }
   scan_tile_sums<<<(unsigned)ntiles, SCAN_NT, 0, st>>>(RowCount{mask_dev, G}, len, tile);
+  count_launch(ctx);
   scan_tile_offsets<<<1, SCAN_NT, 0, st>>>(tile, ntiles, total + 1);
+  count_launch(ctx);
   write_rowptr<<<(unsigned)ntiles, SCAN_NT, 0, st>>>(mask_dev, G, len, tile, idx_dev, rowptr_dev, n);
+  count_launch(ctx);
   set_last<<<1, 1, 0, st>>>(rowptr_dev, n, total + 1);
+  count_launch(ctx);
   if (A_dense_dev && n > 0)
     FL_CUDA(ctx, cudaMemset2DAsync(A_dense_dev, (size_t)lda * sizeof(double), 0,
                                    (size_t)n * sizeof(double), (size_t)n, st));
@@ -239,6 +249,7 @@ extern "C" int fd_assemble(fraclap_ctx* ctx, const uint8_t* mask_dev, int dim, c
   const double diag = (2.0 * dim) / h2, off = -1.0 / h2;
   fill_csr<<<(unsigned)cdiv(len, 256), 256, 0, st>>>(mask_dev, G, len, idx_dev, rowptr_dev, col_dev,
                                                     val_dev, diag, off, A_dense_dev, lda);
+  count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   return 0;
 }

@@ -167,11 +167,13 @@ int launch(fraclap_ctx* ctx, const GemmDesc& d, int split_k, cudaStream_t st) {
   if (split_k <= 1 || d.K2 > 0) {
     gemm_kernel<TA, TB, MODE, false><<<dim3((unsigned)gx, (unsigned)gy, 1), NT, 0, st>>>(
         d, d.K > 0 ? d.K : 1);
+    count_launch(ctx);
   } else {
     int64_t kchunk = cdiv(cdiv(d.K, split_k), BK) * BK;
     const int64_t gz = cdiv(d.K, kchunk);
     gemm_kernel<TA, TB, MODE, true><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), NT, 0, st>>>(
         d, kchunk);
+    count_launch(ctx);
   }
   FL_CUDA(ctx, cudaGetLastError());
   return 0;
@@ -219,6 +221,7 @@ int gemm_batched(fraclap_ctx* ctx, bool ta, bool tb, const GemmDesc* d_descs, in
   else if (!ta && tb) gemm_batched_kernel<false, true><<<grid, NT, 0, st>>>(d_descs);
   else if (ta && !tb) gemm_batched_kernel<true, false><<<grid, NT, 0, st>>>(d_descs);
   else gemm_batched_kernel<true, true><<<grid, NT, 0, st>>>(d_descs);
+  count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   return 0;
 }

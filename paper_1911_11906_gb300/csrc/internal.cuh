@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fraclap.h"
 
@@ -21,6 +22,10 @@ struct fraclap_ctx {
   void* ws = nullptr;            // context-owned workspace
   size_t ws_bytes = 0;
   std::string last_error;
+  long long launches = 0;        // kernels launched through this context
+  bool profiling = false;        // record CUDA events around every stage
+  struct StageEvent { int stage; cudaEvent_t start, stop; };
+  std::vector<StageEvent> stage_events;
 };
 
 namespace fraclap {
@@ -48,6 +53,41 @@ int set_error(fraclap_ctx* ctx, int code, const char* fmt, ...);
     int rc_ = (expr);         \
     if (rc_ != 0) return rc_; \
   } while (0)
+
+inline void count_launch(fraclap_ctx* c) { c->launches++; }
+
+// Stages timed by fraclap_stage_times (ids are part of the C ABI).
+enum Stage : int {
+  kStageAssemble = 0,
+  kStageBandReduction = 1,
+  kStageBulgeChasing = 2,
+  kStageTridiagDC = 3,
+  kStageBackQ2 = 4,
+  kStageBackQ1 = 5,
+  kStageApply = 6,
+  kStageCount = 7
+};
+
+// Records CUDA events around a stage on `st` when profiling is on.
+struct StageTimer {
+  fraclap_ctx* ctx;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t e0 = nullptr;
+  StageTimer(fraclap_ctx* c, int s, cudaStream_t stream) : ctx(c), stage(s), st(stream) {
+    if (ctx->profiling && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, st);
+  }
+  ~StageTimer() {
+    if (!e0) return;
+    cudaEvent_t e1;
+    if (cudaEventCreate(&e1) == cudaSuccess) {
+      cudaEventRecord(e1, st);
+      ctx->stage_events.push_back({stage, e0, e1});
+    } else {
+      cudaEventDestroy(e0);
+    }
+  }
+};
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }

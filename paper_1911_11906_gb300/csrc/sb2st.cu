@@ -294,10 +294,12 @@ int sb2st_run(fraclap_ctx* ctx, double* band, int64_t n, int b, double* d, doubl
     int64_t G = (int64_t)ctx->sm_count * per_sm;
     if (G > n - 1) G = n - 1;
     void* args[] = {&a};
-    FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)sb2st_kernel, dim3((unsigned)G), dim3(SB_NT), args, smem, st));
+    count_launch(ctx);
+      FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)sb2st_kernel, dim3((unsigned)G), dim3(SB_NT), args, smem, st));
   }
   if (n >= 1) {
     band_diagonals<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(band, 2 * b, n, d, e);
+    count_launch(ctx);
     FL_CUDA(ctx, cudaGetLastError());
   }
   return 0;
@@ -311,6 +313,7 @@ int q2_apply_run(fraclap_ctx* ctx, const Stage2* s, int64_t n, int b, double* Z,
   const int64_t grid = cdiv(ncols, 32 * Q2_WARPS);
   q2_apply_kernel<<<(unsigned)grid, Q2_WARPS * 32, smem, st>>>(s->refl, s->rtau, n, b, s->kmax, Z, ldz,
                                                                ncols);
+  count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   return 0;
 }

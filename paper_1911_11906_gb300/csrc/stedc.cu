@@ -572,24 +572,34 @@ int stedc_run(fraclap_ctx* ctx, const double* d, const double* e, int64_t n, dou
   FL_CHECK(ctx, B.G != nullptr, FRACLAP_ERR_ALLOC, "stedc: workspace too small");
   FL_CUDA(ctx, cudaMemset2DAsync(Z, ldz * sizeof(double), 0, n * sizeof(double), n, st));
   dc_setup<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(d, e, n, L, B.D);
+  count_launch(ctx);
   const int64_t nleaf = (int64_t)1 << L;
   dc_leaf<<<(unsigned)cdiv(nleaf, 4), 128, 0, st>>>(B.D, e, n, L, lambda, Z, ldz, ctx->d_status);
+  count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   for (int level = 1; level <= L; ++level) {
     const int64_t nmerge = (int64_t)1 << (L - level);
     const int64_t nmax = level_nmax(n, L, level);
     FL_CHECK(ctx, nmerge <= 65535 && nmax < (1LL << 31), FRACLAP_ERR_UNSUPPORTED, "stedc: too large");
     dc_merge_prep<<<(unsigned)nmerge, 128, 0, st>>>(B, e, lambda, Z, ldz, n, L, level, nmax);
+    count_launch(ctx);
     const dim3 rows((unsigned)cdiv(nmax, 128), (unsigned)nmerge);
     dc_gather<<<rows, 128, 0, st>>>(B, Z, ldz, nmax);
+    count_launch(ctx);
     dc_secular<<<rows, 128, 0, st>>>(B, ctx->d_status);
+    count_launch(ctx);
     dc_zhat<<<rows, 128, 0, st>>>(B);
+    count_launch(ctx);
     dc_vectors<<<dim3((unsigned)nmax, (unsigned)nmerge), 128, 0, st>>>(B, nmax);
+    count_launch(ctx);
     dc_gather_kept<<<rows, 128, 0, st>>>(B, nmax);
+    count_launch(ctx);
     FL_CUDA(ctx, cudaGetLastError());
     FL_TRY(gemm_batched(ctx, false, false, B.desc, (int)nmerge, nmax, nmax, st));
     dc_order<<<(unsigned)nmerge, 32, 0, st>>>(B);
+    count_launch(ctx);
     dc_scatter<<<dim3((unsigned)nmax, (unsigned)nmerge), 128, 0, st>>>(B, lambda, Z, ldz, nmax);
+    count_launch(ctx);
     FL_CUDA(ctx, cudaGetLastError());
   }
   return 0;

@@ -223,6 +223,7 @@ int sy2sb_run(fraclap_ctx* ctx, double* Aw, int64_t n, int64_t lda, int b, doubl
       int32_t* status = ctx->d_status;
       void* args[] = {&P, &ldp, &mm, &bw, &V, &ldv, &tau, &T, &partials, &gram, &bar, &limit, &status, &rows_per_cta};
       FL_CUDA(ctx, cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      count_launch(ctx);
       FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(PQR_NT), args, smem, st));
     }
     double* A22 = Aw + (j0 + b) + (j0 + b) * lda;
@@ -249,6 +250,7 @@ int sy2sb_run(fraclap_ctx* ctx, double* Aw, int64_t n, int64_t lda, int b, doubl
     voff += m * b;
   }
   extract_band<<<(unsigned)cdiv(n * ldb, 256), 256, 0, st>>>(Aw, lda, n, b, band, ldb);
+  count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   return 0;
 }
