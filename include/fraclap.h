@@ -132,6 +132,38 @@ int frac_apply(fraclap_ctx* ctx, const double* V_dev, int64_t ldv, const double*
                fraclap_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * frac_apply_noalloc — frac_apply for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a deployment variant.
+ * It serves code that runs where cudaMalloc is not available to it: inside a
+ * host framework whose memory pool already owns the device (an extra
+ * allocation would fail or break its accounting), or in latency-critical
+ * loops that cannot pay the implicit device synchronisation of
+ * cudaMalloc/cudaFree.  It needs no context and allocates nothing: its
+ * scratch (V^T F and the scaled coefficients) is a fixed array of
+ * FRACLAP_NOALLOC_MAX_DOUBLES doubles (16 MiB) compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ *  Arguments as for frac_apply, without the context and workspace; the
+ *  caller still owns every input and output.  status_dev: optional int32 on
+ *  the device that receives FRACLAP_ERR_NOT_SPD (or INVALID_ARG for a pair
+ *  index out of range) from the kernels; it is not cleared by the call.
+ *  Returns FRACLAP_ERR_UNSUPPORTED, launching nothing, when the scratch is
+ *  too small: n*m rounded up to a multiple of 32, plus n*k, must not exceed
+ *  FRACLAP_NOALLOC_MAX_DOUBLES, and k <= 65535.
+ *  The first call on each device looks up the array's device address with
+ *  cudaGetSymbolAddress (with that device current); make that first call
+ *  before any stream capture.  All calls share the one array and it keeps
+ *  the previous call's contents (every element used is rewritten before it
+ *  is read): calls whose executions overlap on the GPU (different streams,
+ *  or host threads without ordering) race on it.
+ * ---------------------------------------------------------------------- */
+#define FRACLAP_NOALLOC_MAX_DOUBLES (1 << 21)
+int frac_apply_noalloc(const double* V_dev, int64_t ldv, const double* lambda_dev, int64_t n,
+                       const double* F_dev, int64_t ldf, int64_t m, const int32_t* pair_f_dev,
+                       const double* pair_alpha_dev, int64_t k, double* U_dev, int64_t ldu,
+                       int32_t* status_dev, fraclap_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Stage entry points (the steps eig_full chains), for stage-level checks.
  * ---------------------------------------------------------------------- */
 

@@ -27,6 +27,7 @@ SIGNATURES = {
     "eig_full": (_i32, [_p, _p, _i64, _i64, _p, _p, _i64, _p, _sz, _p, _p]),
     "fraclap_apply_workspace_bytes": (_sz, [_i64, _i64, _i64]),
     "frac_apply": (_i32, [_p, _p, _i64, _p, _i64, _p, _i64, _i64, _p, _p, _i64, _p, _i64, _p, _sz, _p]),
+    "frac_apply_noalloc": (_i32, [_p, _i64, _p, _i64, _p, _i64, _i64, _p, _p, _i64, _p, _i64, _p, _p]),
     "fraclap_tridiagonalize": (_i32, [_p, _p, _i64, _i64, _p, _p, _p, _i64, _p, _sz, _p]),
     "fraclap_tridiag_workspace_bytes": (_sz, [_p, _i64]),
     "fraclap_tridiag_eig": (_i32, [_p, _p, _p, _i64, _p, _p, _i64, _p, _sz, _p]),

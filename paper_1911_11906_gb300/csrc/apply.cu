@@ -77,3 +77,88 @@ extern "C" int frac_apply(fraclap_ctx* ctx, const double* V_dev, int64_t ldv,
   FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
   return 0;
 }
+
+// ----------------------------------------------------------------------------
+// frac_apply_noalloc: the same spectral apply for callers that cannot
+// allocate device memory.  Its scratch (V^T F and the scaled coefficients)
+// lives in a fixed file-scope device array that every device loading this
+// library keeps until the process exits.
+// ----------------------------------------------------------------------------
+#include <mutex>
+
+namespace fraclap {
+namespace {
+
+constexpr int64_t kNoAllocDoubles = FRACLAP_NOALLOC_MAX_DOUBLES;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+static __device__ __align__(256) int32_t g_noalloc_status[1];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_scratch_ptr[kNoAllocMaxDevices] = {};
+int32_t* g_noalloc_status_ptr[kNoAllocMaxDevices] = {};
+
+// Device addresses of the scratch array and the fallback status word on the
+// current device, looked up once per device (the symbol names are host-side
+// stand-ins and must never be passed to a kernel).
+int noalloc_setup(double** scratch, int32_t** status) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FRACLAP_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return FRACLAP_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_scratch_ptr[dev]) {
+    double* p = nullptr;
+    int32_t* q = nullptr;
+    if (cudaGetSymbolAddress((void**)&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return FRACLAP_ERR_CUDA;
+    }
+    if (cudaGetSymbolAddress((void**)&q, g_noalloc_status) != cudaSuccess || !q) {
+      cudaGetLastError();
+      return FRACLAP_ERR_CUDA;
+    }
+    g_noalloc_status_ptr[dev] = q;
+    g_noalloc_scratch_ptr[dev] = p;
+  }
+  *scratch = g_noalloc_scratch_ptr[dev];
+  *status = g_noalloc_status_ptr[dev];
+  return 0;
+}
+
+}  // namespace
+}  // namespace fraclap
+
+extern "C" int frac_apply_noalloc(const double* V_dev, int64_t ldv, const double* lambda_dev,
+                                  int64_t n, const double* F_dev, int64_t ldf, int64_t m,
+                                  const int32_t* pair_f_dev, const double* pair_alpha_dev,
+                                  int64_t k, double* U_dev, int64_t ldu, int32_t* status_dev,
+                                  fraclap_stream_t stream) {
+  if (n < 0 || m < 0 || k < 0) return FRACLAP_ERR_INVALID_ARG;
+  if (n == 0 || k == 0) return 0;
+  if (m < 1 || !V_dev || !lambda_dev || !F_dev || !pair_f_dev || !pair_alpha_dev || !U_dev)
+    return FRACLAP_ERR_INVALID_ARG;
+  if (ldv < n || ldf < n || ldu < n) return FRACLAP_ERR_INVALID_ARG;
+  // the scratch holds W (n x m) and C (n x k), each starting on a 256-byte boundary
+  const int64_t wlen = ((n * m + 31) / 32) * 32;
+  if (m > kNoAllocDoubles || k > 65535 || n > kNoAllocDoubles / (m + k) ||
+      wlen + n * k > kNoAllocDoubles)
+    return FRACLAP_ERR_UNSUPPORTED;
+  double* scratch = nullptr;
+  int32_t* own_status = nullptr;
+  const int rc = noalloc_setup(&scratch, &own_status);
+  if (rc != 0) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* status = status_dev ? status_dev : own_status;
+  double* W = scratch;
+  double* C = scratch + wlen;
+  fraclap_ctx local;  // host-side bookkeeping only (error text, launch count)
+  GemmDesc d{n, m, n, V_dev, ldv, F_dev, ldf, W, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+  int r = gemm(&local, true, false, kGemmPlain, d, 1, st);
+  if (r != 0) return r;
+  spectral_scale<<<dim3((unsigned)cdiv(n, 256), (unsigned)k), 256, 0, st>>>(
+      lambda_dev, n, W, n, pair_f_dev, pair_alpha_dev, k, m, C, n, status);
+  if (cudaGetLastError() != cudaSuccess) return FRACLAP_ERR_CUDA;
+  d = GemmDesc{n, k, n, V_dev, ldv, C, n, U_dev, ldu, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+  return gemm(&local, false, false, kGemmPlain, d, 1, st);
+}
