@@ -49,7 +49,7 @@ enum {
 
 /* Options; zero fields take the defaults in brackets. */
 typedef struct fraclap_opts {
-  int band_width;           /* half-bandwidth b of the dense-to-band stage [32]; 1..64 */
+  int band_width;           /* half-bandwidth b of the dense-to-band stage [32]: 4, 8, 16, 32 or 64 */
   int leaf_size;            /* largest leaf of the tridiagonal divide and conquer [32]; 2..32 */
   double wait_timeout_s;    /* limit of every device-side spin wait in seconds [10] */
 } fraclap_opts;

@@ -124,7 +124,7 @@ int back_transform(fraclap_ctx* ctx, int64_t n, EigWork* w, double* Z, int64_t l
   const int b = ctx->band_width;
   {
     StageTimer t(ctx, kStageBackQ2, st);
-    FL_TRY(q2_apply_run(ctx, &w->s2, n, b, Z, ldz, n, st));
+    FL_TRY(q2_apply_run(ctx, &w->s2, n, b, Z, ldz, n, w->Aw, n, st));
   }
   {
     StageTimer t(ctx, kStageBackQ1, st);
@@ -165,7 +165,9 @@ extern "C" int fraclap_create(fraclap_ctx** out, const fraclap_opts* opts) {
     if (opts->leaf_size) ctx->leaf_size = opts->leaf_size;
     if (opts->wait_timeout_s > 0) ctx->wait_timeout_s = opts->wait_timeout_s;
   }
-  if (ctx->band_width < 1 || ctx->band_width > 64 || ctx->leaf_size < 2 || ctx->leaf_size > 32) {
+  const int bw = ctx->band_width;
+  if ((bw != 4 && bw != 8 && bw != 16 && bw != 32 && bw != 64) || ctx->leaf_size < 2 ||
+      ctx->leaf_size > 32) {
     delete ctx;
     return FRACLAP_ERR_INVALID_ARG;
   }

@@ -180,8 +180,11 @@ struct Stage2 {
 int stage2_take(Arena* ar, int64_t n, int b, Stage2* s);
 int sb2st_run(fraclap_ctx* ctx, double* band, int64_t n, int b, double* d, double* e, Stage2* s,
               cudaStream_t st);
+// Z <- Q2 Z through a transposed copy Yt (ncols x n, ld ldy >= ncols).
 int q2_apply_run(fraclap_ctx* ctx, const Stage2* s, int64_t n, int b, double* Z, int64_t ldz,
-                 int64_t ncols, cudaStream_t st);
+                 int64_t ncols, double* Yt, int64_t ldy, cudaStream_t st);
+int transpose_run(fraclap_ctx* ctx, const double* A, int64_t lda, double* Bm, int64_t ldb,
+                  int64_t rows, int64_t cols, cudaStream_t st);
 
 size_t stedc_ws(const fraclap_ctx* ctx, int64_t n);
 int stedc_run(fraclap_ctx* ctx, const double* d, const double* e, int64_t n, double* lambda,

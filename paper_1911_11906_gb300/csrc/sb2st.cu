@@ -208,64 +208,148 @@ __global__ void band_diagonals(const double* band, int ldb, int64_t n, double* d
   if (i + 1 < n) e[i] = band[1 + i * ldb];
 }
 
-// Z <- Q2 Z.  One warp per 32 columns (lane = column); per warp a window of
-// b rows in shared memory, slot of row r = r mod b.
-constexpr int Q2_WARPS = 2;
+// Y <- Y Q2^T, i.e. Z <- Q2 Z on the transpose Y = Z^T (ld >= n), so that a
+// row of Z is contiguous.  For each step k the reflectors H(s, k), s
+// descending, act on a window of B rows of Z that slides up by one row per
+// reflector.  A warp owns CPW = 32/P columns of Z; its lanes split the window
+// into P parts of R = B/P rows each, held in registers: the dot product of a
+// reflector with a column is a partial sum per part plus a butterfly over the
+// P parts, and the slide moves one row per part boundary with a shuffle.  The
+// CTA stages the reflectors of the next D steps in shared memory (double
+// buffered) while it applies the current D; the rows entering the window are
+// loaded one batch ahead.  Work: 4 L n flops per reflector of length L.
+constexpr int Q2T_WARPS = 8, Q2T_D = 8;
 
-__global__ void __launch_bounds__(Q2_WARPS * 32)
-q2_apply_kernel(const double* refl, const double* rtau, int64_t n, int b, int64_t kmax,
-                double* Z, int64_t ldz, int64_t ncols) {
-  extern __shared__ double win_all[];
+template <int B, int P>
+__global__ void __launch_bounds__(Q2T_WARPS * 32, 2)
+q2t_apply_kernel(const double* __restrict__ refl, const double* __restrict__ rtau, int64_t n,
+                 int64_t kmax, double* Y, int64_t ldy, int64_t ncols) {
+  constexpr int R = B / P, CPW = 32 / P, D = Q2T_D, NT = Q2T_WARPS * 32;
+  constexpr int PER = (D * B + NT - 1) / NT;  // staged doubles per thread
+  __shared__ double vbuf[2][D][B];
+  __shared__ double tbuf[2][D];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* win = win_all + (size_t)warp * b * 32;
-  const int64_t col = ((int64_t)blockIdx.x * Q2_WARPS + warp) * 32 + lane;
+  const int part = lane / CPW, cl = lane % CPW;
+  const int64_t col = ((int64_t)blockIdx.x * Q2T_WARPS + warp) * CPW + cl;
   const bool active = col < ncols;
-  double* zc = Z + (active ? col : 0) * ldz;
+  double* yc = Y + (active ? col : 0);
+  const unsigned full = 0xffffffffu;
+
   for (int64_t k = 0; k < kmax; ++k) {
-    const int64_t smax = n - 2 - k * b;
+    const int64_t smax = n - 2 - k * B;
     if (smax < 0) break;
-    int64_t lo = n, hi = n - 1;  // window rows [lo, hi] (empty)
-    for (int64_t s = smax; s >= 0; --s) {
-      const int64_t r0 = s + 1 + k * b;
-      const int L = (int)((n - r0 < b) ? n - r0 : b);
-      const int64_t r1 = r0 + L - 1;
-      // slide: drop rows > r1, add row r0
-      while (hi > r1) {
-        if (active) zc[hi] = win[(hi % b) * 32 + lane];
-        --hi;
+    const int64_t nbatch = (smax + D) / D;  // reflectors s = smax .. 0
+    // stage a batch of reflectors (q = batch * D + j  <->  s = smax - q)
+    auto fetch = [&](int64_t batch, double* vr, double* tr) {
+      for (int e = 0; e < PER; ++e) {
+        const int t = threadIdx.x + e * NT;
+        double v = 0.0;
+        if (t < D * B) {
+          const int j = t / B, c = t % B;
+          const int64_t sj = smax - (batch * D + j);
+          if (sj >= 0) v = __ldg(refl + (sj * kmax + k) * B + c);
+        }
+        vr[e] = v;
       }
-      if (r0 < lo) {
-        lo = r0;
-        win[(r0 % b) * 32 + lane] = active ? zc[r0] : 0.0;
+      double tv = 0.0;
+      if (threadIdx.x < D) {
+        const int64_t sj = smax - (batch * D + threadIdx.x);
+        if (sj >= 0) tv = __ldg(rtau + sj * kmax + k);
       }
-      const double tu = __ldg(rtau + s * kmax + k);
-      if (tu == 0.0) continue;
-      const double* v = refl + (s * kmax + k) * b;
-      const double va = (lane < L) ? __ldg(v + lane) : 0.0;
-      const double vb = (lane + 32 < L) ? __ldg(v + lane + 32) : 0.0;
-      double acc0 = 0.0, acc1 = 0.0;
-      int t = 0;
-      for (; t + 1 < L; t += 2) {
-        const double v0 = __shfl_sync(0xffffffffu, t < 32 ? va : vb, t & 31);
-        const double v1 = __shfl_sync(0xffffffffu, (t + 1) < 32 ? va : vb, (t + 1) & 31);
-        acc0 = fma(v0, win[((r0 + t) % b) * 32 + lane], acc0);
-        acc1 = fma(v1, win[((r0 + t + 1) % b) * 32 + lane], acc1);
+      *tr = tv;
+    };
+    auto store = [&](int buf, const double* vr, double tr) {
+      for (int e = 0; e < PER; ++e) {
+        const int t = threadIdx.x + e * NT;
+        if (t < D * B) vbuf[buf][t / B][t % B] = vr[e];
       }
-      if (t < L) {
-        const double v0 = __shfl_sync(0xffffffffu, t < 32 ? va : vb, t & 31);
-        acc0 = fma(v0, win[((r0 + t) % b) * 32 + lane], acc0);
+      if (threadIdx.x < D) tbuf[buf][threadIdx.x] = tr;
+    };
+    double vr[PER], tr;
+    fetch(0, vr, &tr);
+    __syncthreads();  // previous k's readers are done with the buffers
+    store(0, vr, tr);
+
+    int64_t r0 = n - 1;  // window rows r0 .. r0 + B - 1 (rows >= n are zero)
+    double w[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int64_t row = r0 + part * R + i;
+      w[i] = (active && row < n) ? yc[row * ldy] : 0.0;
+    }
+    double pf[D];  // rows entering the window during the current batch (part 0)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const int64_t row = r0 - 1 - j;
+      pf[j] = (part == 0 && active && row >= 1 + k * B) ? yc[row * ldy] : 0.0;
+    }
+    __syncthreads();
+    for (int64_t batch = 0; batch < nbatch; ++batch) {
+      const int buf = (int)(batch & 1);
+      const bool more = batch + 1 < nbatch;
+      if (more) fetch(batch + 1, vr, &tr);
+      double pn[D];  // rows for the next batch
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const int64_t row = r0 - 1 - D - j;
+        pn[j] = (more && part == 0 && active && row >= 1 + k * B) ? yc[row * ldy] : 0.0;
       }
-      const double w = tu * (acc0 + acc1);
-      for (t = 0; t < L; ++t) {
-        const double vt = __shfl_sync(0xffffffffu, t < 32 ? va : vb, t & 31);
-        double* z = &win[((r0 + t) % b) * 32 + lane];
-        *z = fma(-w, vt, *z);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const int64_t s = smax - (batch * D + j);
+        if (s < 0) break;
+        const double* v = &vbuf[buf][j][part * R];
+        double d0 = 0.0, d1 = 0.0;
+#pragma unroll
+        for (int i = 0; i < R; i += 2) {
+          d0 = fma(v[i], w[i], d0);
+          if (i + 1 < R) d1 = fma(v[i + 1], w[i + 1], d1);
+        }
+        double dot = d0 + d1;
+#pragma unroll
+        for (int o = CPW; o < 32; o <<= 1) dot += __shfl_xor_sync(full, dot, o);
+        const double f = tbuf[buf][j] * dot;
+#pragma unroll
+        for (int i = 0; i < R; ++i) w[i] = fma(-f, v[i], w[i]);
+        if (s > 0) {  // slide the window up by one row
+          const double out = w[R - 1];
+          const int64_t leaving = r0 + B - 1;
+          if (part == P - 1 && active && leaving < n) yc[leaving * ldy] = out;
+          const double prev = __shfl_up_sync(full, out, CPW);
+#pragma unroll
+          for (int i = R - 1; i > 0; --i) w[i] = w[i - 1];
+          w[0] = (part == 0) ? pf[j] : prev;
+          --r0;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < D; ++j) pf[j] = pn[j];
+      if (more) {
+        store(buf ^ 1, vr, tr);
+        __syncthreads();
       }
     }
-    while (hi >= lo) {  // flush
-      if (active) zc[hi] = win[(hi % b) * 32 + lane];
-      --hi;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {  // flush the final window (rows 1 + kB ..)
+      const int64_t row = r0 + part * R + i;
+      if (active && row < n) yc[row * ldy] = w[i];
     }
+  }
+}
+
+// 32 x 32 tiled transpose: B(j, i) = A(i, j), A is rows x cols.
+__global__ void transpose_kernel(const double* A, int64_t lda, double* Bm, int64_t ldb, int64_t rows,
+                                 int64_t cols) {
+  __shared__ double tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  for (int t = threadIdx.y; t < 32; t += blockDim.y) {
+    const int64_t i = i0 + threadIdx.x, j = j0 + t;
+    if (i < rows && j < cols) tile[t][threadIdx.x] = A[i + j * lda];
+  }
+  __syncthreads();
+  for (int t = threadIdx.y; t < 32; t += blockDim.y) {
+    const int64_t j = j0 + threadIdx.x, i = i0 + t;
+    if (i < rows && j < cols) Bm[j + i * ldb] = tile[threadIdx.x][t];
   }
 }
 
@@ -305,17 +389,40 @@ int sb2st_run(fraclap_ctx* ctx, double* band, int64_t n, int b, double* d, doubl
   return 0;
 }
 
-int q2_apply_run(fraclap_ctx* ctx, const Stage2* s, int64_t n, int b, double* Z, int64_t ldz,
-                 int64_t ncols, cudaStream_t st) {
-  if (n < 2 || ncols <= 0) return 0;
-  const size_t smem = sizeof(double) * (size_t)Q2_WARPS * b * 32;
-  FL_CUDA(ctx, cudaFuncSetAttribute(q2_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int64_t grid = cdiv(ncols, 32 * Q2_WARPS);
-  q2_apply_kernel<<<(unsigned)grid, Q2_WARPS * 32, smem, st>>>(s->refl, s->rtau, n, b, s->kmax, Z, ldz,
-                                                               ncols);
+int transpose_run(fraclap_ctx* ctx, const double* A, int64_t lda, double* Bm, int64_t ldb,
+                  int64_t rows, int64_t cols, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return 0;
+  dim3 grid((unsigned)cdiv(rows, 32), (unsigned)cdiv(cols, 32));
+  FL_CHECK(ctx, grid.y <= 65535, FRACLAP_ERR_UNSUPPORTED, "transpose: too many columns");
+  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(A, lda, Bm, ldb, rows, cols);
   count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   return 0;
+}
+
+// Z <- Q2 Z (n x ncols, ld ldz), through the transposed copy Yt (ld >= ncols).
+int q2_apply_run(fraclap_ctx* ctx, const Stage2* s, int64_t n, int b, double* Z, int64_t ldz,
+                 int64_t ncols, double* Yt, int64_t ldy, cudaStream_t st) {
+  if (n < 2 || ncols <= 0) return 0;
+  FL_TRY(transpose_run(ctx, Z, ldz, Yt, ldy, n, ncols, st));
+  int cpw = 0;
+#define FL_Q2T(BB, PP)                                                                     \
+  if (b == BB) {                                                                           \
+    cpw = 32 / PP;                                                                         \
+    const int64_t grid = cdiv(ncols, (int64_t)cpw * Q2T_WARPS);                             \
+    q2t_apply_kernel<BB, PP><<<(unsigned)grid, Q2T_WARPS * 32, 0, st>>>(s->refl, s->rtau, n, \
+                                                                       s->kmax, Yt, ldy, ncols); \
+    count_launch(ctx);                                                                     \
+  }
+  FL_Q2T(4, 1)
+  FL_Q2T(8, 2)
+  FL_Q2T(16, 4)
+  FL_Q2T(32, 8)
+  FL_Q2T(64, 8)
+#undef FL_Q2T
+  FL_CHECK(ctx, cpw != 0, FRACLAP_ERR_UNSUPPORTED, "q2 back-transformation: band width %d not in {4, 8, 16, 32, 64}", b);
+  FL_CUDA(ctx, cudaGetLastError());
+  return transpose_run(ctx, Yt, ldy, Z, ldz, ncols, n, st);
 }
 
 }  // namespace fraclap
