@@ -110,6 +110,29 @@ int eig_full(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_t lda,
              size_t work_bytes, int32_t* info_dev, fraclap_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * eig_full_mixed — the same decomposition through the mixed-precision route:
+ * the reduction to band form, the bulge chasing, the divide-and-conquer
+ * eigenvector merges and both back-transformations run in FP32 (the FP32
+ * pipe of GB300 is ~58x its FP64 pipe); the Householder norms and scalings,
+ * the secular equations and the deflation stay FP64.  FP64 accuracy is then
+ * regained by `refine_iters` iterations of Ogita-Aishima refinement
+ * (R = I - V^T V and S = V^T A V in FP64 with A applied through its CSR
+ * form; clusters of close eigenvalues are diagonalised exactly).  One
+ * iteration reaches the eig_full tolerances on the stencil matrices; two are
+ * the default recommendation.
+ *
+ *  A_dev      double[lda*n] dense, lower triangle read (the FP32 stages).
+ *  rowptr_dev, col_dev, val_dev: the same matrix in CSR (from fd_assemble).
+ *  lambda_dev, V_dev: as eig_full.  n <= 65535.
+ *  work: fraclap_eig_mixed_workspace_bytes(ctx, n) bytes.
+ * ---------------------------------------------------------------------- */
+size_t fraclap_eig_mixed_workspace_bytes(const fraclap_ctx* ctx, int64_t n);
+int eig_full_mixed(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_t lda,
+                   const int64_t* rowptr_dev, const int32_t* col_dev, const double* val_dev,
+                   int refine_iters, double* lambda_dev, double* V_dev, int64_t ldv,
+                   void* work_dev, size_t work_bytes, int32_t* info_dev, fraclap_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * frac_apply — the spectral solution operator of Sec. II,
  * eq. (poisson_solution) and the sum v after eq. (discrete_laplace):
  *   u_j = V diag(lambda^{-alpha_j / 2}) V^T f_{pair_f[j]},  j = 0..k-1.
@@ -200,13 +223,20 @@ enum {
   FRACLAP_STAGE_BACK_Q2 = 4,        /* back-transformation by the bulge-chasing reflectors */
   FRACLAP_STAGE_BACK_Q1 = 5,        /* back-transformation by the panel reflectors */
   FRACLAP_STAGE_APPLY = 6,          /* frac_apply */
-  FRACLAP_STAGE_COUNT = 7
+  FRACLAP_STAGE_REFINE = 7,         /* Ogita-Aishima refinement (eig_full_mixed) */
+  FRACLAP_STAGE_COUNT = 8
 };
 /* With enable != 0, every later stage records a CUDA event pair on its stream. */
 int fraclap_set_profiling(fraclap_ctx* ctx, int enable);
 /* Waits for the recorded events, writes the summed milliseconds (and the
  * number of records, count_out may be NULL) per stage id, and forgets them. */
 int fraclap_stage_times(fraclap_ctx* ctx, double* ms_out, int64_t* count_out, int nstages);
+/* Statistics of the last eig_full_mixed refinement, 8 values per iteration:
+ * the cluster threshold delta, the estimates of ||S - D||_2 and ||R||_2 used
+ * for it, ||S - D||_F, ||R||_F, the Gershgorin bound of ||A||_2, the number
+ * of clusters and the largest cluster.  Copies at most max_values values and
+ * returns how many there are. */
+int fraclap_refine_stats(const fraclap_ctx* ctx, double* out, int max_values);
 /* Number of kernels the context has launched so far. */
 long long fraclap_launch_count(const fraclap_ctx* ctx);
 

@@ -15,6 +15,7 @@ from ._binding import (  # noqa: F401
     library_path,
     fd_assemble,
     eig_full,
+    eig_full_mixed,
     frac_apply,
     tridiagonalize,
     tridiag_eig,

@@ -25,6 +25,8 @@ SIGNATURES = {
     "fd_assemble": (_i32, [_p, _p, _i32, _p, _dbl, _p, _p, _p, _p, _p, _p, _p, _i64, _p]),
     "fraclap_eig_workspace_bytes": (_sz, [_p, _i64]),
     "eig_full": (_i32, [_p, _p, _i64, _i64, _p, _p, _i64, _p, _sz, _p, _p]),
+    "fraclap_eig_mixed_workspace_bytes": (_sz, [_p, _i64]),
+    "eig_full_mixed": (_i32, [_p, _p, _i64, _i64, _p, _p, _p, _i32, _p, _p, _i64, _p, _sz, _p, _p]),
     "fraclap_apply_workspace_bytes": (_sz, [_i64, _i64, _i64]),
     "frac_apply": (_i32, [_p, _p, _i64, _p, _i64, _p, _i64, _i64, _p, _p, _i64, _p, _i64, _p, _sz, _p]),
     "frac_apply_noalloc": (_i32, [_p, _i64, _p, _i64, _p, _i64, _i64, _p, _p, _i64, _p, _i64, _p, _p]),
@@ -34,6 +36,7 @@ SIGNATURES = {
     "fraclap_set_profiling": (_i32, [_p, _i32]),
     "fraclap_stage_times": (_i32, [_p, _p, _p, _i32]),
     "fraclap_launch_count": (ctypes.c_longlong, [_p]),
+    "fraclap_refine_stats": (_i32, [_p, _p, _i32]),
     "fraclap_dgemm": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64, _p]),
 }
 
@@ -107,7 +110,8 @@ class Context:
             msg = self.lib.fraclap_last_error(self.handle).decode()
             raise FraclapError(rc, msg)
 
-    STAGES = ("assemble", "band_reduction", "bulge_chasing", "tridiag_dc", "back_q2", "back_q1", "apply")
+    STAGES = ("assemble", "band_reduction", "bulge_chasing", "tridiag_dc", "back_q2", "back_q1", "apply",
+              "refine")
 
     def set_profiling(self, enable: bool = True):
         self.check(self.lib.fraclap_set_profiling(self.handle, int(enable)))
@@ -119,6 +123,16 @@ class Context:
         cnt = (ctypes.c_int64 * n)()
         self.check(self.lib.fraclap_stage_times(self.handle, ms, cnt, n))
         return {s: (ms[i], cnt[i]) for i, s in enumerate(self.STAGES)}
+
+    REFINE_FIELDS = ("delta", "norm2_S_minus_D", "norm2_R", "fro_S_minus_D", "fro_R", "norm2_A_bound",
+                     "clusters", "largest_cluster")
+
+    def refine_stats(self) -> list:
+        """Per iteration of the last mixed-precision refinement: dict of REFINE_FIELDS."""
+        buf = (ctypes.c_double * 512)()
+        nv = self.lib.fraclap_refine_stats(self.handle, buf, 512)
+        f = self.REFINE_FIELDS
+        return [dict(zip(f, buf[i:i + len(f)])) for i in range(0, min(nv, 512), len(f))]
 
     def launch_count(self) -> int:
         return int(self.lib.fraclap_launch_count(self.handle))
@@ -199,6 +213,28 @@ def eig_full(A: torch.Tensor, ctx: Context | None = None, stream=None, workspace
     st = ctypes.c_void_p(_stream(stream))
     ctx.check(ctx.lib.eig_full(ctx.handle, _ptr(A), n, _ld(A), _ptr(lam), _ptr(V), max(n, 1),
                                _ptr(workspace), workspace.numel(), None, st))
+    if sync:
+        ctx.sync(stream)
+    return lam, V
+
+
+def eig_full_mixed(A: torch.Tensor, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
+                   refine_iters: int = 2, ctx: Context | None = None, stream=None,
+                   workspace: torch.Tensor | None = None, sync: bool = True):
+    """Mixed-precision decomposition (FP32 stages + Ogita-Aishima refinement).
+    A: dense lower triangle; (rowptr, col, val): the same matrix in CSR."""
+    ctx = ctx or default_context()
+    A = _f64_colmajor(A, "A")
+    n = A.shape[0]
+    lam = torch.empty(n, dtype=torch.float64, device=A.device)
+    V = empty_colmajor(n, n, A.device)
+    if workspace is None:
+        nbytes = ctx.lib.fraclap_eig_mixed_workspace_bytes(ctx.handle, n)
+        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=A.device)
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.eig_full_mixed(ctx.handle, _ptr(A), n, _ld(A), _ptr(rowptr), _ptr(col), _ptr(val),
+                                     int(refine_iters), _ptr(lam), _ptr(V), max(n, 1), _ptr(workspace),
+                                     workspace.numel(), None, st))
     if sync:
         ctx.sync(stream)
     return lam, V

@@ -3,6 +3,8 @@
 // stencil assembly in assemble.cu).
 #include <stdarg.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace fraclap {
@@ -62,78 +64,118 @@ __global__ void set_identity(double* Z, int64_t ldz, int64_t n) {
   Z[i + j * ldz] = (i == j) ? 1.0 : 0.0;
 }
 
-__global__ void copy_lower(const double* A, int64_t lda, double* B, int64_t ldb, int64_t n) {
+template <class T>
+__global__ void copy_lower(const double* A, int64_t lda, T* B, int64_t ldb, int64_t n) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n * n) return;
   const int64_t i = p % n, j = p / n;
-  if (i >= j) B[i + j * ldb] = A[i + j * lda];
+  if (i >= j) B[i + j * ldb] = (T)A[i + j * lda];
 }
 
+__global__ void widen(const float* Z, int64_t n, double* V, int64_t ldv) {
+  const int64_t total = n * n;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = p % n, j = p / n;
+    V[i + j * ldv] = (double)Z[p];
+  }
+}
+
+template <class T>
 struct EigWork {
-  double* Aw;     // n x n working copy
-  double* band;   // 2b x n
+  T* Aw;          // n x n working copy (later the transposed eigenvectors)
+  T* band;        // 2b x n
   double* d;      // n
   double* e;      // n
-  double* W1;     // b x n
-  double* W2;     // b x n
-  Stage1 s1;
-  Stage2 s2;
+  T* W1;          // b x n
+  T* W2;          // b x n
+  Stage1T<T> s1;
+  Stage2T<T> s2;
 };
 
-int eig_take(Arena* ar, const fraclap_ctx* ctx, int64_t n, EigWork* w) {
+template <class T>
+int eig_take(Arena* ar, const fraclap_ctx* ctx, int64_t n, EigWork<T>* w) {
   const int b = ctx->band_width;
-  w->Aw = ar->take<double>(n * n);
-  w->band = ar->take<double>(2 * (int64_t)b * n);
+  w->Aw = ar->take<T>(n * n);
+  w->band = ar->take<T>(2 * (int64_t)b * n);
   w->d = ar->take<double>(n);
   w->e = ar->take<double>(n);
-  w->W1 = ar->take<double>((int64_t)b * n);
-  w->W2 = ar->take<double>((int64_t)b * n);
-  stage1_take(ar, n, b, ctx->sm_count, &w->s1);
-  stage2_take(ar, n, b, &w->s2);
+  w->W1 = ar->take<T>((int64_t)b * n);
+  w->W2 = ar->take<T>((int64_t)b * n);
+  stage1_take<T>(ar, n, b, ctx->sm_count, &w->s1);
+  stage2_take<T>(ar, n, b, &w->s2);
   return 0;
 }
 
+}  // namespace
+
 size_t eig_ws_bytes(const fraclap_ctx* ctx, int64_t n, bool with_dc) {
   Arena ar;
-  EigWork w;
-  eig_take(&ar, ctx, n, &w);
+  EigWork<double> w;
+  eig_take<double>(&ar, ctx, n, &w);
   size_t s = ar.off;
-  if (with_dc) s += stedc_ws(ctx, n);
+  if (with_dc) s += stedc_ws<double>(ctx, n);
   return s + 4096;
 }
 
-// Reduction of A to tridiagonal form (d, e) in w; optionally Z <- Q1 Q2 Z.
-int reduce(fraclap_ctx* ctx, const double* A, int64_t n, int64_t lda, EigWork* w, cudaStream_t st) {
+namespace {
+
+size_t mixed_ws_bytes(const fraclap_ctx* ctx, int64_t n) {
+  Arena ar;
+  EigWork<float> w;
+  eig_take<float>(&ar, ctx, n, &w);
+  ar.take<float>(n * n);  // Z (FP32 eigenvectors)
+  return ar.off + stedc_ws<float>(ctx, n) + refine_ws(ctx, n) + 8192;
+}
+
+// Reduction of A to tridiagonal form (d, e) in w.
+template <class T>
+int reduce(fraclap_ctx* ctx, const double* A, int64_t n, int64_t lda, EigWork<T>* w, cudaStream_t st) {
   const int b = ctx->band_width;
-  copy_lower<<<(unsigned)cdiv(n * n, 256), 256, 0, st>>>(A, lda, w->Aw, n, n);
+  copy_lower<T><<<(unsigned)cdiv(n * n, 256), 256, 0, st>>>(A, lda, w->Aw, n, n);
   count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   {
     StageTimer t(ctx, kStageBandReduction, st);
-    FL_TRY(sy2sb_run(ctx, w->Aw, n, n, b, w->band, &w->s1, st));
+    FL_TRY(sy2sb_run<T>(ctx, w->Aw, n, n, b, w->band, &w->s1, st));
   }
   {
     StageTimer t(ctx, kStageBulgeChasing, st);
-    FL_TRY(sb2st_run(ctx, w->band, n, b, w->d, w->e, &w->s2, st));
+    FL_TRY(sb2st_run<T>(ctx, w->band, n, b, w->d, w->e, &w->s2, st));
   }
   return 0;
 }
 
-int back_transform(fraclap_ctx* ctx, int64_t n, EigWork* w, double* Z, int64_t ldz,
-                   cudaStream_t st) {
+template <class T>
+int back_transform(fraclap_ctx* ctx, int64_t n, EigWork<T>* w, T* Z, int64_t ldz, cudaStream_t st) {
   const int b = ctx->band_width;
   {
     StageTimer t(ctx, kStageBackQ2, st);
-    FL_TRY(q2_apply_run(ctx, &w->s2, n, b, Z, ldz, n, w->Aw, n, st));
+    FL_TRY(q2_apply_run<T>(ctx, &w->s2, n, b, Z, ldz, n, w->Aw, n, st));
   }
   {
     StageTimer t(ctx, kStageBackQ1, st);
-    FL_TRY(q1_apply_run(ctx, &w->s1, n, b, Z, ldz, n, w->W1, w->W2, st));
+    FL_TRY(q1_apply_run<T>(ctx, &w->s1, n, b, Z, ldz, n, w->W1, w->W2, st));
   }
   return 0;
 }
 
 }  // namespace
+
+size_t cluster_eig_ws(const fraclap_ctx* ctx, int64_t c) { return eig_ws_bytes(ctx, c, true); }
+
+int cluster_eig(fraclap_ctx* ctx, double* S, int64_t c, double* w, double* Q, Arena* ar,
+                cudaStream_t st) {
+  // the band width and SM count of the caller's context; sized like cluster_eig_ws
+  EigWork<double> ew;
+  eig_take<double>(ar, ctx, c, &ew);
+  FL_CHECK(ctx, ew.s2.progress != nullptr, FRACLAP_ERR_ALLOC, "cluster eig: workspace too small");
+  FL_TRY(reduce<double>(ctx, S, c, c, &ew, st));
+  FL_TRY(stedc_run<double>(ctx, ew.d, ew.e, c, w, Q, c, ar, st));
+  FL_TRY(back_transform<double>(ctx, c, &ew, Q, c, st));
+  return 0;
+}
+
 }  // namespace fraclap
 
 using namespace fraclap;
@@ -219,7 +261,7 @@ extern "C" size_t fraclap_eig_workspace_bytes(const fraclap_ctx* ctx, int64_t n)
 
 extern "C" size_t fraclap_tridiag_workspace_bytes(const fraclap_ctx* ctx, int64_t n) {
   if (!ctx || n <= 0) return 0;
-  return stedc_ws(ctx, n) + 4096;
+  return stedc_ws<double>(ctx, n) + 4096;
 }
 
 extern "C" int eig_full(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_t lda,
@@ -234,15 +276,15 @@ extern "C" int eig_full(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_
   FL_CHECK(ctx, n < (1LL << 31) / 64, FRACLAP_ERR_UNSUPPORTED, "eig_full: n too large");
   Arena ar;
   FL_TRY(get_workspace(ctx, work_dev, work_bytes, eig_ws_bytes(ctx, n, true), &ar));
-  EigWork w;
-  eig_take(&ar, ctx, n, &w);
+  EigWork<double> w;
+  eig_take<double>(&ar, ctx, n, &w);
   FL_CHECK(ctx, w.s2.progress != nullptr, FRACLAP_ERR_ALLOC, "eig_full: workspace too small");
-  FL_TRY(reduce(ctx, A_dev, n, lda, &w, st));
+  FL_TRY(reduce<double>(ctx, A_dev, n, lda, &w, st));
   {
     StageTimer t(ctx, kStageTridiagDC, st);
-    FL_TRY(stedc_run(ctx, w.d, w.e, n, lambda_dev, V_dev, ldv, &ar, st));
+    FL_TRY(stedc_run<double>(ctx, w.d, w.e, n, lambda_dev, V_dev, ldv, &ar, st));
   }
-  FL_TRY(back_transform(ctx, n, &w, V_dev, ldv, st));
+  FL_TRY(back_transform<double>(ctx, n, &w, V_dev, ldv, st));
   if (info_dev) FL_CUDA(ctx, cudaMemcpyAsync(info_dev, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   return 0;
 }
@@ -259,17 +301,17 @@ extern "C" int fraclap_tridiagonalize(fraclap_ctx* ctx, const double* A_dev, int
   FL_CHECK(ctx, lda >= n && (!Q_dev || ldq >= n), FRACLAP_ERR_INVALID_ARG, "tridiagonalize: leading dimension < n");
   Arena ar;
   FL_TRY(get_workspace(ctx, work_dev, work_bytes, eig_ws_bytes(ctx, n, false), &ar));
-  EigWork w;
-  eig_take(&ar, ctx, n, &w);
+  EigWork<double> w;
+  eig_take<double>(&ar, ctx, n, &w);
   FL_CHECK(ctx, w.s2.progress != nullptr, FRACLAP_ERR_ALLOC, "tridiagonalize: workspace too small");
-  FL_TRY(reduce(ctx, A_dev, n, lda, &w, st));
+  FL_TRY(reduce<double>(ctx, A_dev, n, lda, &w, st));
   FL_CUDA(ctx, cudaMemcpyAsync(d_dev, w.d, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   if (n > 1) FL_CUDA(ctx, cudaMemcpyAsync(e_dev, w.e, sizeof(double) * (n - 1), cudaMemcpyDeviceToDevice, st));
   if (Q_dev) {
     set_identity<<<(unsigned)cdiv(n * n, 256), 256, 0, st>>>(Q_dev, ldq, n);
     count_launch(ctx);
     FL_CUDA(ctx, cudaGetLastError());
-    FL_TRY(back_transform(ctx, n, &w, Q_dev, ldq, st));
+    FL_TRY(back_transform<double>(ctx, n, &w, Q_dev, ldq, st));
   }
   return 0;
 }
@@ -284,9 +326,9 @@ extern "C" int fraclap_tridiag_eig(fraclap_ctx* ctx, const double* d_dev, const 
            "tridiag_eig: null pointer");
   FL_CHECK(ctx, ldz >= n, FRACLAP_ERR_INVALID_ARG, "tridiag_eig: ldz < n");
   Arena ar;
-  FL_TRY(get_workspace(ctx, work_dev, work_bytes, stedc_ws(ctx, n) + 4096, &ar));
+  FL_TRY(get_workspace(ctx, work_dev, work_bytes, stedc_ws<double>(ctx, n) + 4096, &ar));
   StageTimer t(ctx, kStageTridiagDC, (cudaStream_t)stream);
-  return stedc_run(ctx, d_dev, e_dev, n, lambda_dev, Z_dev, ldz, &ar, (cudaStream_t)stream);
+  return stedc_run<double>(ctx, d_dev, e_dev, n, lambda_dev, Z_dev, ldz, &ar, (cudaStream_t)stream);
 }
 
 extern "C" int fraclap_dgemm(fraclap_ctx* ctx, int trans_a, int trans_b, int64_t m, int64_t n,
@@ -334,3 +376,54 @@ extern "C" int fraclap_stage_times(fraclap_ctx* ctx, double* ms_out, int64_t* co
 }
 
 extern "C" long long fraclap_launch_count(const fraclap_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+extern "C" size_t fraclap_eig_mixed_workspace_bytes(const fraclap_ctx* ctx, int64_t n) {
+  if (!ctx || n <= 0) return 0;
+  return mixed_ws_bytes(ctx, n);
+}
+
+extern "C" int eig_full_mixed(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_t lda,
+                              const int64_t* rowptr_dev, const int32_t* col_dev,
+                              const double* val_dev, int refine_iters, double* lambda_dev,
+                              double* V_dev, int64_t ldv, void* work_dev, size_t work_bytes,
+                              int32_t* info_dev, fraclap_stream_t stream) {
+  if (!ctx) return FRACLAP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  FL_CHECK(ctx, n >= 0, FRACLAP_ERR_INVALID_ARG, "eig_full_mixed: n < 0");
+  if (n == 0) return 0;
+  FL_CHECK(ctx, A_dev && rowptr_dev && col_dev && val_dev && lambda_dev && V_dev,
+           FRACLAP_ERR_INVALID_ARG, "eig_full_mixed: null pointer");
+  FL_CHECK(ctx, lda >= n && ldv >= n, FRACLAP_ERR_INVALID_ARG, "eig_full_mixed: leading dimension < n");
+  FL_CHECK(ctx, refine_iters >= 0 && refine_iters <= 8, FRACLAP_ERR_INVALID_ARG,
+           "eig_full_mixed: refine_iters must be 0..8");
+  FL_CHECK(ctx, n <= 65535, FRACLAP_ERR_UNSUPPORTED, "eig_full_mixed: n > 65535");
+  Arena ar;
+  FL_TRY(get_workspace(ctx, work_dev, work_bytes, mixed_ws_bytes(ctx, n), &ar));
+  EigWork<float> w;
+  eig_take<float>(&ar, ctx, n, &w);
+  float* Z = ar.take<float>(n * n);
+  FL_CHECK(ctx, Z != nullptr, FRACLAP_ERR_ALLOC, "eig_full_mixed: workspace too small");
+  FL_TRY(reduce<float>(ctx, A_dev, n, lda, &w, st));
+  {
+    StageTimer t(ctx, kStageTridiagDC, st);
+    FL_TRY(stedc_run<float>(ctx, w.d, w.e, n, lambda_dev, Z, n, &ar, st));
+  }
+  FL_TRY(back_transform<float>(ctx, n, &w, Z, n, st));
+  {
+    StageTimer t(ctx, kStageRefine, st);
+    widen<<<(unsigned)std::min<int64_t>(cdiv(n * n, 256), 152 * 16), 256, 0, st>>>(Z, n, V_dev, ldv);
+    count_launch(ctx);
+    FL_CUDA(ctx, cudaGetLastError());
+    Arena rar = ar;  // the refinement reuses everything after the FP32 stages
+    FL_TRY(refine_run(ctx, n, rowptr_dev, col_dev, val_dev, V_dev, ldv, lambda_dev, refine_iters, &rar, st));
+  }
+  if (info_dev) FL_CUDA(ctx, cudaMemcpyAsync(info_dev, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  return 0;
+}
+
+extern "C" int fraclap_refine_stats(const fraclap_ctx* ctx, double* out, int max_values) {
+  if (!ctx || max_values < 0 || (max_values > 0 && !out)) return FRACLAP_ERR_INVALID_ARG;
+  const int nv = (int)ctx->refine_stats.size();
+  for (int i = 0; i < nv && i < max_values; ++i) out[i] = ctx->refine_stats[i];
+  return nv;
+}

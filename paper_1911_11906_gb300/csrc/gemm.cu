@@ -17,8 +17,8 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
-template <bool TA, int MODE>
-__device__ __forceinline__ void load_a(double (*As)[BM + 1], const double* A, int64_t lda,
+template <class T, bool TA, int MODE>
+__device__ __forceinline__ void load_a(T (*As)[BM + 1], const T* A, int64_t lda,
                                        int64_t M, int64_t K, int64_t m0, int64_t k0) {
   const int tid = threadIdx.x;
   if (MODE == kGemmSymA) {
@@ -26,7 +26,7 @@ __device__ __forceinline__ void load_a(double (*As)[BM + 1], const double* A, in
     for (int i = 0; i < 4; ++i) {
       const int m = tid % BM, k = tid / BM + 4 * i;
       const int64_t gm = m0 + m, gk = k0 + k;
-      double v = 0.0;
+      T v = T(0);
       if (gm < M && gk < K) v = (gm >= gk) ? A[gm + gk * lda] : A[gk + gm * lda];
       As[k][m] = v;
     }
@@ -35,20 +35,20 @@ __device__ __forceinline__ void load_a(double (*As)[BM + 1], const double* A, in
     for (int i = 0; i < 4; ++i) {
       const int m = tid % BM, k = tid / BM + 4 * i;
       const int64_t gm = m0 + m, gk = k0 + k;
-      As[k][m] = (gm < M && gk < K) ? A[gm + gk * lda] : 0.0;
+      As[k][m] = (gm < M && gk < K) ? A[gm + gk * lda] : T(0);
     }
   } else {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int k = tid % BK, m = tid / BK + 16 * i;
       const int64_t gm = m0 + m, gk = k0 + k;
-      As[k][m] = (gm < M && gk < K) ? A[gk + gm * lda] : 0.0;
+      As[k][m] = (gm < M && gk < K) ? A[gk + gm * lda] : T(0);
     }
   }
 }
 
-template <bool TB>
-__device__ __forceinline__ void load_b(double (*Bs)[BN + 1], const double* B, int64_t ldb,
+template <class T, bool TB>
+__device__ __forceinline__ void load_b(T (*Bs)[BN + 1], const T* B, int64_t ldb,
                                        int64_t N, int64_t K, int64_t n0, int64_t k0) {
   const int tid = threadIdx.x;
   if (!TB) {
@@ -56,32 +56,32 @@ __device__ __forceinline__ void load_b(double (*Bs)[BN + 1], const double* B, in
     for (int i = 0; i < 4; ++i) {
       const int k = tid % BK, n = tid / BK + 16 * i;
       const int64_t gn = n0 + n, gk = k0 + k;
-      Bs[k][n] = (gn < N && gk < K) ? B[gk + gn * ldb] : 0.0;
+      Bs[k][n] = (gn < N && gk < K) ? B[gk + gn * ldb] : T(0);
     }
   } else {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int n = tid % BN, k = tid / BN + 4 * i;
       const int64_t gn = n0 + n, gk = k0 + k;
-      Bs[k][n] = (gn < N && gk < K) ? B[gn + gk * ldb] : 0.0;
+      Bs[k][n] = (gn < N && gk < K) ? B[gn + gk * ldb] : T(0);
     }
   }
 }
 
-template <bool TA, bool TB, int MODE>
-__device__ __forceinline__ void accumulate(double (&acc)[4][4], double (*As)[BM + 1],
-                                           double (*Bs)[BN + 1], const double* A, int64_t lda,
-                                           const double* B, int64_t ldb, int64_t M, int64_t N,
+template <class T, bool TA, bool TB, int MODE>
+__device__ __forceinline__ void accumulate(T (&acc)[4][4], T (*As)[BM + 1],
+                                           T (*Bs)[BN + 1], const T* A, int64_t lda,
+                                           const T* B, int64_t ldb, int64_t M, int64_t N,
                                            int64_t K, int64_t m0, int64_t n0, int64_t kbeg,
                                            int64_t kend) {
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-    load_a<TA, MODE>(As, A, lda, M, kend, m0, k0);
-    load_b<TB>(Bs, B, ldb, N, kend, n0, k0);
+    load_a<T, TA, MODE>(As, A, lda, M, kend, m0, k0);
+    load_b<T, TB>(Bs, B, ldb, N, kend, n0, k0);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
 #pragma unroll
@@ -95,21 +95,21 @@ __device__ __forceinline__ void accumulate(double (&acc)[4][4], double (*As)[BM 
   }
 }
 
-template <bool TA, bool TB, int MODE, bool ATOMIC>
-__device__ __forceinline__ void gemm_tile(const GemmDesc& d, int64_t m0, int64_t n0, int64_t kbeg,
+template <class T, bool TA, bool TB, int MODE, bool ATOMIC>
+__device__ __forceinline__ void gemm_tile(const GemmDescT<T>& d, int64_t m0, int64_t n0, int64_t kbeg,
                                           int64_t kend) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
   if (MODE == kGemmLowerC && m0 + BM - 1 < n0) return;  // tile entirely above the diagonal
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  accumulate<TA, TB, MODE>(acc, As, Bs, d.A, d.lda, d.B, d.ldb, d.M, d.N, d.K, m0, n0, kbeg, kend);
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  accumulate<T, TA, TB, MODE>(acc, As, Bs, d.A, d.lda, d.B, d.ldb, d.M, d.N, d.K, m0, n0, kbeg, kend);
   if (d.K2 > 0 && kbeg == 0)
-    accumulate<TA, TB, MODE>(acc, As, Bs, d.A2, d.lda2, d.B2, d.ldb2, d.M, d.N, d.K2, m0, n0, 0,
-                             d.K2);
+    accumulate<T, TA, TB, MODE>(acc, As, Bs, d.A2, d.lda2, d.B2, d.ldb2, d.M, d.N, d.K2, m0, n0, 0,
+                                d.K2);
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -120,29 +120,29 @@ __device__ __forceinline__ void gemm_tile(const GemmDesc& d, int64_t m0, int64_t
       const int64_t gn = n0 + tx + 16 * j;
       if (gn >= d.N) continue;
       if (MODE == kGemmLowerC && gm < gn) continue;
-      double* c = d.C + gm + gn * d.ldc;
-      const double v = d.alpha * acc[i][j];
+      T* c = d.C + gm + gn * d.ldc;
+      const T v = T(d.alpha) * acc[i][j];
       if (ATOMIC) {
         atomicAdd(c, v);
       } else {
-        *c = (d.beta == 0.0) ? v : v + d.beta * *c;
+        *c = (d.beta == 0.0) ? v : v + T(d.beta) * *c;
       }
     }
   }
 }
 
-template <bool TA, bool TB, int MODE, bool ATOMIC>
-__global__ void __launch_bounds__(NT) gemm_kernel(GemmDesc d, int64_t kchunk) {
+template <class T, bool TA, bool TB, int MODE, bool ATOMIC>
+__global__ void __launch_bounds__(NT) gemm_kernel(GemmDescT<T> d, int64_t kchunk) {
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
   const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
   const int64_t kend = (kbeg + kchunk < d.K) ? kbeg + kchunk : d.K;
   if (kbeg > 0 && kbeg >= d.K) return;  // z-slice 0 always runs (K = 0: C = beta C)
-  gemm_tile<TA, TB, MODE, ATOMIC>(d, m0, n0, kbeg, kend);
+  gemm_tile<T, TA, TB, MODE, ATOMIC>(d, m0, n0, kbeg, kend);
 }
 
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(NT) gemm_batched_kernel(const GemmDesc* descs) {
-  const GemmDesc d = descs[blockIdx.z];
+template <class T, bool TA, bool TB>
+__global__ void __launch_bounds__(NT) gemm_batched_kernel(const GemmDescT<T>* descs) {
+  const GemmDescT<T> d = descs[blockIdx.z];
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
   if (d.M <= 0 || d.N <= 0 || m0 >= d.M || n0 >= d.N) return;
   if (d.K <= 0) {  // C = beta C
@@ -151,27 +151,27 @@ __global__ void __launch_bounds__(NT) gemm_batched_kernel(const GemmDesc* descs)
       for (int j = 0; j < 4; ++j) {
         const int64_t gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
         if (gm < d.M && gn < d.N) {
-          double* c = d.C + gm + gn * d.ldc;
-          *c = (d.beta == 0.0) ? 0.0 : d.beta * *c;
+          T* c = d.C + gm + gn * d.ldc;
+          *c = (d.beta == 0.0) ? T(0) : T(d.beta) * *c;
         }
       }
     return;
   }
-  gemm_tile<TA, TB, kGemmPlain, false>(d, m0, n0, 0, d.K);
+  gemm_tile<T, TA, TB, kGemmPlain, false>(d, m0, n0, 0, d.K);
 }
 
-template <bool TA, bool TB, int MODE>
-int launch(fraclap_ctx* ctx, const GemmDesc& d, int split_k, cudaStream_t st) {
+template <class T, bool TA, bool TB, int MODE>
+int launch(fraclap_ctx* ctx, const GemmDescT<T>& d, int split_k, cudaStream_t st) {
   const int64_t gx = cdiv(d.M, BM), gy = cdiv(d.N, BN);
   FL_CHECK(ctx, gy <= 65535, FRACLAP_ERR_UNSUPPORTED, "gemm: N = %lld too large", (long long)d.N);
   if (split_k <= 1 || d.K2 > 0) {
-    gemm_kernel<TA, TB, MODE, false><<<dim3((unsigned)gx, (unsigned)gy, 1), NT, 0, st>>>(
+    gemm_kernel<T, TA, TB, MODE, false><<<dim3((unsigned)gx, (unsigned)gy, 1), NT, 0, st>>>(
         d, d.K > 0 ? d.K : 1);
     count_launch(ctx);
   } else {
     int64_t kchunk = cdiv(cdiv(d.K, split_k), BK) * BK;
     const int64_t gz = cdiv(d.K, kchunk);
-    gemm_kernel<TA, TB, MODE, true><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), NT, 0, st>>>(
+    gemm_kernel<T, TA, TB, MODE, true><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), NT, 0, st>>>(
         d, kchunk);
     count_launch(ctx);
   }
@@ -181,7 +181,8 @@ int launch(fraclap_ctx* ctx, const GemmDesc& d, int split_k, cudaStream_t st) {
 
 }  // namespace
 
-int gemm(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDesc& d, int split_k,
+template <class T>
+int gemm(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDescT<T>& d, int split_k,
          cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0) return 0;
   FL_CHECK(ctx, mode != kGemmSymA || (!ta && d.M == d.K), FRACLAP_ERR_INVALID_ARG,
@@ -189,15 +190,15 @@ int gemm(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDesc& d, i
   FL_CHECK(ctx, split_k <= 1 || d.beta == 1.0, FRACLAP_ERR_INVALID_ARG,
            "gemm: split-K accumulates into C (beta must be 1)");
   if (d.K <= 0 && d.K2 <= 0) {  // C = beta C
-    GemmDesc z = d;
+    GemmDescT<T> z = d;
     z.K = 0;
     z.K2 = 0;
-    return launch<false, false, kGemmPlain>(ctx, z, 1, st);
+    return launch<T, false, false, kGemmPlain>(ctx, z, 1, st);
   }
-#define FL_GEMM_CASE(TA, TB)                                                        \
-  if (ta == TA && tb == TB) {                                                       \
-    if (mode == kGemmPlain) return launch<TA, TB, kGemmPlain>(ctx, d, split_k, st); \
-    if (mode == kGemmLowerC) return launch<TA, TB, kGemmLowerC>(ctx, d, split_k, st); \
+#define FL_GEMM_CASE(TA, TB)                                                           \
+  if (ta == TA && tb == TB) {                                                          \
+    if (mode == kGemmPlain) return launch<T, TA, TB, kGemmPlain>(ctx, d, split_k, st);  \
+    if (mode == kGemmLowerC) return launch<T, TA, TB, kGemmLowerC>(ctx, d, split_k, st); \
   }
   FL_GEMM_CASE(false, false)
   FL_GEMM_CASE(false, true)
@@ -205,25 +206,31 @@ int gemm(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDesc& d, i
   FL_GEMM_CASE(true, true)
 #undef FL_GEMM_CASE
   if (mode == kGemmSymA) {
-    if (tb) return launch<false, true, kGemmSymA>(ctx, d, split_k, st);
-    return launch<false, false, kGemmSymA>(ctx, d, split_k, st);
+    if (tb) return launch<T, false, true, kGemmSymA>(ctx, d, split_k, st);
+    return launch<T, false, false, kGemmSymA>(ctx, d, split_k, st);
   }
   return set_error(ctx, FRACLAP_ERR_INVALID_ARG, "gemm: bad mode");
 }
 
-int gemm_batched(fraclap_ctx* ctx, bool ta, bool tb, const GemmDesc* d_descs, int count,
+template <class T>
+int gemm_batched(fraclap_ctx* ctx, bool ta, bool tb, const GemmDescT<T>* d_descs, int count,
                  int64_t max_m, int64_t max_n, cudaStream_t st) {
   if (count <= 0 || max_m <= 0 || max_n <= 0) return 0;
   const int64_t gx = cdiv(max_m, BM), gy = cdiv(max_n, BN);
   FL_CHECK(ctx, gy <= 65535 && count <= 65535, FRACLAP_ERR_UNSUPPORTED, "gemm_batched: too large");
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)count);
-  if (!ta && !tb) gemm_batched_kernel<false, false><<<grid, NT, 0, st>>>(d_descs);
-  else if (!ta && tb) gemm_batched_kernel<false, true><<<grid, NT, 0, st>>>(d_descs);
-  else if (ta && !tb) gemm_batched_kernel<true, false><<<grid, NT, 0, st>>>(d_descs);
-  else gemm_batched_kernel<true, true><<<grid, NT, 0, st>>>(d_descs);
+  if (!ta && !tb) gemm_batched_kernel<T, false, false><<<grid, NT, 0, st>>>(d_descs);
+  else if (!ta && tb) gemm_batched_kernel<T, false, true><<<grid, NT, 0, st>>>(d_descs);
+  else if (ta && !tb) gemm_batched_kernel<T, true, false><<<grid, NT, 0, st>>>(d_descs);
+  else gemm_batched_kernel<T, true, true><<<grid, NT, 0, st>>>(d_descs);
   count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   return 0;
 }
+
+template int gemm<double>(fraclap_ctx*, bool, bool, GemmMode, const GemmDescT<double>&, int, cudaStream_t);
+template int gemm<float>(fraclap_ctx*, bool, bool, GemmMode, const GemmDescT<float>&, int, cudaStream_t);
+template int gemm_batched<double>(fraclap_ctx*, bool, bool, const GemmDescT<double>*, int, int64_t, int64_t, cudaStream_t);
+template int gemm_batched<float>(fraclap_ctx*, bool, bool, const GemmDescT<float>*, int, int64_t, int64_t, cudaStream_t);
 
 }  // namespace fraclap

@@ -26,6 +26,9 @@ struct fraclap_ctx {
   bool profiling = false;        // record CUDA events around every stage
   struct StageEvent { int stage; cudaEvent_t start, stop; };
   std::vector<StageEvent> stage_events;
+  // per refinement iteration: delta, ||S-D||_2 est, ||R||_2 est, ||S-D||_F,
+  // ||R||_F, ||A||_2 bound, clusters, largest cluster
+  std::vector<double> refine_stats;
 };
 
 namespace fraclap {
@@ -65,7 +68,8 @@ enum Stage : int {
   kStageBackQ2 = 4,
   kStageBackQ1 = 5,
   kStageApply = 6,
-  kStageCount = 7
+  kStageRefine = 7,
+  kStageCount = 8
 };
 
 // Records CUDA events around a stage on `st` when profiling is on.
@@ -122,27 +126,32 @@ enum GemmMode : int {
   kGemmSymA = 2,      // A is symmetric, only its lower triangle is read (M == K)
 };
 
-struct GemmDesc {
+template <class T>
+struct GemmDescT {
   int64_t M, N, K;
-  const double* A; int64_t lda;
-  const double* B; int64_t ldb;
-  double* C; int64_t ldc;
+  const T* A; int64_t lda;
+  const T* B; int64_t ldb;
+  T* C; int64_t ldc;
   // optional second product accumulated into the same C (K2 = 0: none):
   // C = alpha (op(A) op(B) + op(A2) op(B2)) + beta C, same transposes.
-  const double* A2; int64_t lda2;
-  const double* B2; int64_t ldb2;
+  const T* A2; int64_t lda2;
+  const T* B2; int64_t ldb2;
   int64_t K2;
   double alpha, beta;
 };
+using GemmDesc = GemmDescT<double>;
 
-// One product; split_k > 1 accumulates partial sums with atomics (beta must be
-// 1 and C pre-scaled/zeroed by the caller).
-int gemm(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDesc& d, int split_k,
+// One product (T = double: FP64 FMA; T = float: FP32 FMA with FP32
+// accumulation); split_k > 1 accumulates partial sums with atomics (beta must
+// be 1 and C pre-scaled/zeroed by the caller).
+template <class T>
+int gemm(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDescT<T>& d, int split_k,
          cudaStream_t st);
 // Batched over a device array of descriptors; grid covers max_m x max_n tiles,
 // tiles outside a descriptor's M x N exit.  Descriptors with M, N or K <= 0
 // are skipped.
-int gemm_batched(fraclap_ctx* ctx, bool ta, bool tb, const GemmDesc* d_descs, int count,
+template <class T>
+int gemm_batched(fraclap_ctx* ctx, bool ta, bool tb, const GemmDescT<T>* d_descs, int count,
                  int64_t max_m, int64_t max_n, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
@@ -150,45 +159,76 @@ int gemm_batched(fraclap_ctx* ctx, bool ta, bool tb, const GemmDesc* d_descs, in
 // ---------------------------------------------------------------------------
 // Stage 1 (dense -> band) workspace: compact-WY panels kept for the
 // back-transformation.
-struct Stage1 {
-  double* Vstore;    // sum_j m_j * b: explicit V of every panel
-  double* Tstore;    // npanel * b * b
+// T is the storage/GEMM type (double, or float on the mixed path); the
+// Householder norms, scalings and the T-factor recurrence are FP64 always.
+template <class T>
+struct Stage1T {
+  T* Vstore;         // sum_j m_j * b: explicit V of every panel
+  T* Tstore;         // npanel * b * b
   double* tau;       // npanel * b
-  double* XT;        // n * b
-  double* X;         // n * b
-  double* Y;         // b * b
-  double* Mm;        // b * b
+  T* XT;             // n * b
+  T* X;              // n * b
+  T* Y;              // b * b
+  T* Mm;             // b * b
   double* gram;      // b * b
   double* partials;  // 2 * G * 2b
   int64_t npanel;
   int64_t vtotal;
 };
+using Stage1 = Stage1T<double>;
 int64_t stage1_panels(int64_t n, int b);
-int stage1_take(Arena* ar, int64_t n, int b, int G, Stage1* s);
-int sy2sb_run(fraclap_ctx* ctx, double* Aw, int64_t n, int64_t lda, int b, double* band,
-              Stage1* s, cudaStream_t st);
-int q1_apply_run(fraclap_ctx* ctx, const Stage1* s, int64_t n, int b, double* Z, int64_t ldz,
-                 int64_t ncols, double* W1, double* W2, cudaStream_t st);
+template <class T>
+int stage1_take(Arena* ar, int64_t n, int b, int G, Stage1T<T>* s);
+template <class T>
+int sy2sb_run(fraclap_ctx* ctx, T* Aw, int64_t n, int64_t lda, int b, T* band, Stage1T<T>* s,
+              cudaStream_t st);
+template <class T>
+int q1_apply_run(fraclap_ctx* ctx, const Stage1T<T>* s, int64_t n, int b, T* Z, int64_t ldz,
+                 int64_t ncols, T* W1, T* W2, cudaStream_t st);
 
 // Stage 2 (band -> tridiagonal) workspace: the bulge-chasing reflectors.
-struct Stage2 {
-  double* refl;   // (n-1) * kmax * b
+template <class T>
+struct Stage2T {
+  T* refl;        // (n-1) * kmax * b
   double* rtau;   // (n-1) * kmax
   int* progress;  // n + 1
   int64_t kmax;
 };
-int stage2_take(Arena* ar, int64_t n, int b, Stage2* s);
-int sb2st_run(fraclap_ctx* ctx, double* band, int64_t n, int b, double* d, double* e, Stage2* s,
+using Stage2 = Stage2T<double>;
+template <class T>
+int stage2_take(Arena* ar, int64_t n, int b, Stage2T<T>* s);
+// Band (T) -> tridiagonal (d, e in FP64).
+template <class T>
+int sb2st_run(fraclap_ctx* ctx, T* band, int64_t n, int b, double* d, double* e, Stage2T<T>* s,
               cudaStream_t st);
 // Z <- Q2 Z through a transposed copy Yt (ncols x n, ld ldy >= ncols).
-int q2_apply_run(fraclap_ctx* ctx, const Stage2* s, int64_t n, int b, double* Z, int64_t ldz,
-                 int64_t ncols, double* Yt, int64_t ldy, cudaStream_t st);
-int transpose_run(fraclap_ctx* ctx, const double* A, int64_t lda, double* Bm, int64_t ldb,
-                  int64_t rows, int64_t cols, cudaStream_t st);
+template <class T>
+int q2_apply_run(fraclap_ctx* ctx, const Stage2T<T>* s, int64_t n, int b, T* Z, int64_t ldz,
+                 int64_t ncols, T* Yt, int64_t ldy, cudaStream_t st);
+template <class T>
+int transpose_run(fraclap_ctx* ctx, const T* A, int64_t lda, T* Bm, int64_t ldb, int64_t rows,
+                  int64_t cols, cudaStream_t st);
 
+// Tridiagonal divide and conquer: secular equations, deflation and the
+// Gu-Eisenstat vectors in FP64; eigenvectors stored and merged in T.
+template <class T>
 size_t stedc_ws(const fraclap_ctx* ctx, int64_t n);
-int stedc_run(fraclap_ctx* ctx, const double* d, const double* e, int64_t n, double* lambda,
-              double* Z, int64_t ldz, Arena* arena, cudaStream_t st);
+template <class T>
+int stedc_run(fraclap_ctx* ctx, const double* d, const double* e, int64_t n, double* lambda, T* Z,
+              int64_t ldz, Arena* arena, cudaStream_t st);
+
+// Dense FP64 eigendecomposition of a small symmetric c x c matrix S (lower
+// triangle, ld c; overwritten) into w (ascending) and Q (c x c, ld c), with
+// the same stages as eig_full; used for large clusters in the refinement.
+size_t cluster_eig_ws(const fraclap_ctx* ctx, int64_t c);
+int cluster_eig(fraclap_ctx* ctx, double* S, int64_t c, double* w, double* Q, Arena* ar,
+                cudaStream_t st);
+
+// Ogita-Aishima refinement of (X, lambda) against the CSR matrix A.
+size_t refine_ws(const fraclap_ctx* ctx, int64_t n);
+int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col,
+               const double* val, double* X, int64_t ldx, double* lambda, int iters, Arena* ar,
+               cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // device helpers

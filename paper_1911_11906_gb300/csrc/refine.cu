@@ -1,0 +1,563 @@
+// Ogita-Aishima iterative refinement of a full symmetric eigendecomposition
+// (T. Ogita, K. Aishima, JJIAM 35, 2018; clustered eigenvalues: JJIAM 36,
+// 2019), written from the method's mathematics.  One iteration, with X the
+// current approximate eigenvector matrix (FP64, n x n):
+//   R = I - X^T X,  S = X^T A X                 (FP64, lower triangles)
+//   l_i = s_ii / (1 - r_ii)
+//   delta = 2 (||S - diag(l)||_F + ||A||_2 ||R||_F)
+//   E_ij = (s_ij + l_j r_ij) / (l_j - l_i)   if |l_j - l_i| > delta
+//        = r_ij / 2                           otherwise (and on the diagonal)
+//   X <- X + X E                               (the product in FP32: E is small)
+// then the columns are sorted by l, and every cluster is diagonalised exactly:
+// S_c = X_c^T A X_c (FP64), Jacobi on S_c, X_c <- X_c Q_c.  A cluster is a run
+// of sorted positions joined by "unsafe" pairs: |l_j - l_i| <= delta (the
+// method's own test), or a first-order coefficient |E_ij| above 1e-2, whose
+// second-order error would spoil the quadratic convergence when the starting
+// vectors are only FP32-accurate (this safeguard is ours).  Using the lower triangles of R and S as symmetric
+// matrices keeps E_ij + E_ji = r_ij, so orthogonality improves to first order
+// exactly.  A enters only through products with its CSR form (5/7 nonzeros
+// per row).
+#include <string.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace fraclap {
+namespace {
+
+// Y(:, j) = A X(:, j) for j < ncols; A in CSR.  grid (rows / 128, column chunks)
+__global__ void spmm_csr(int64_t n, const int64_t* __restrict__ rowptr,
+                         const int32_t* __restrict__ col, const double* __restrict__ val,
+                         const double* X, int64_t ldx, int64_t ncols, double* Y, int64_t ldy) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t p0 = rowptr[i], p1 = rowptr[i + 1];
+  for (int64_t j = blockIdx.y; j < ncols; j += gridDim.y) {
+    const double* x = X + j * ldx;
+    double s = 0.0;
+    for (int64_t p = p0; p < p1; ++p) s = fma(val[p], x[col[p]], s);
+    Y[i + j * ldy] = s;
+  }
+}
+
+// R(i,i) += 1 (R holds -X^T X on entry).
+__global__ void add_identity(double* R, int64_t ldr, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) R[i + i * ldr] += 1.0;
+}
+
+__global__ void ritz_values(const double* S, int64_t lds, const double* R, int64_t ldr, int64_t n,
+                            double* lt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) lt[i] = S[i + i * lds] / (1.0 - R[i + i * ldr]);
+}
+
+// Partial sums of ||S - diag(l)||_F^2 and ||R||_F^2 over the lower triangles.
+__global__ void frob_norms(const double* S, int64_t lds, const double* R, int64_t ldr,
+                           const double* lt, int64_t n, double* acc) {
+  double s2 = 0.0, r2 = 0.0;
+  const int64_t total = n * n;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = p % n, j = p / n;
+    if (i < j) continue;
+    const double s = S[i + j * lds], r = R[i + j * ldr];
+    if (i == j) {
+      s2 += (s - lt[i]) * (s - lt[i]);
+      r2 += r * r;
+    } else {
+      s2 += 2.0 * s * s;
+      r2 += 2.0 * r * r;
+    }
+  }
+  __shared__ double red[2][32];
+  s2 = warp_sum(s2);
+  r2 = warp_sum(r2);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s2;
+    red[1][threadIdx.x >> 5] = r2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (unsigned w = 0; w < blockDim.x / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    atomicAdd(acc, a);
+    atomicAdd(acc + 1, b);
+  }
+}
+
+// y = M x for a symmetric M stored in its lower triangle (diagonal shifted by
+// -shift[i] when shift is given); one thread per row.
+__global__ void symv_lower(const double* M, int64_t ldm, const double* shift, int64_t n,
+                           const double* x, double* y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    const double m = (j <= i) ? M[i + j * ldm] : M[j + i * ldm];
+    s = fma(m, x[j], s);
+  }
+  if (shift) s -= shift[i] * x[i];
+  y[i] = s;
+}
+
+// x = y / ||y||, est = ||y|| (one block).
+__global__ void normalize_vec(const double* y, int64_t n, double* x, double* est) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += y[i] * y[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double nrm = sqrt(red[0]);
+  const double inv = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = y[i] * inv;
+  if (threadIdx.x == 0) *est = nrm;
+}
+
+__global__ void start_vec(double* x, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    // deterministic, sign-varying start with components in every direction
+    const uint64_t h = (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+    x[i] = ((double)(h >> 11) * (1.0 / 9007199254740992.0) - 0.5) / sqrt((double)n);
+  }
+}
+
+// Gershgorin bound of ||A||_2 (max absolute row sum), atomically maxed as bits.
+__global__ void gershgorin(int64_t n, const int64_t* rowptr, const double* val,
+                           unsigned long long* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s += fabs(val[p]);
+  atomicMax(out, (unsigned long long)__double_as_longlong(s));  // non-negative doubles order as bits
+}
+
+// delta = 2 (||S - D||_2 + ||A||_2 ||R||_2) with the 2-norms of S - D and R
+// estimated by power iteration (times a safety factor 2, the estimates being
+// lower bounds) and capped by their Frobenius norms; ||A||_2 by Gershgorin.
+__global__ void cluster_threshold(const double* acc, const double* est, const unsigned long long* nA,
+                                  double* delta) {
+  const double na = __longlong_as_double((long long)*nA);
+  const double s2 = fmin(2.0 * est[0], sqrt(acc[0]));
+  const double r2 = fmin(2.0 * est[1], sqrt(acc[1]));
+  *delta = 2.0 * (s2 + na * r2);
+}
+
+// Unsafe pairs: |l_j - l_i| <= delta, or a first-order coefficient
+// |s_ij + l r_ij| / |l_j - l_i| above tau.  Each unsafe pair (i, j) stretches
+// the span starting at its smaller sorted position to its larger one.
+__global__ void unsafe_spans(const double* S, int64_t lds, const double* R, int64_t ldr,
+                             const double* lt, const int* rank, const double* delta, double tau,
+                             int64_t n, int* reach) {
+  const int64_t total = n * n;
+  const double dl = *delta;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = p % n, j = p / n;
+    if (i <= j) continue;  // strictly lower triangle
+    const double g = fabs(lt[j] - lt[i]);
+    const double s = S[i + j * lds], r = R[i + j * ldr];
+    const double num = fmax(fabs(s + lt[j] * r), fabs(s + lt[i] * r));
+    if (g <= dl || num > tau * g) {
+      const int a = min(rank[i], rank[j]), b = max(rank[i], rank[j]);
+      atomicMax(reach + a, b);
+    }
+  }
+}
+
+__global__ void init_reach(int* reach, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) reach[i] = (int)i;
+}
+
+// Merges the spans (sorted positions) into clusters: cid[pos] = cluster
+// index or -1; list = (start, size) pairs; *count.  One thread.
+__global__ void merge_spans(const int* reach, int64_t n, int* cid, int* list, int* count) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int c = 0;
+  int64_t i = 0;
+  while (i < n) {
+    int64_t j = reach[i], k = i;
+    while (k <= j) {
+      if (reach[k] > j) j = reach[k];
+      ++k;
+    }
+    if (j > i) {
+      list[2 * c] = (int)i;
+      list[2 * c + 1] = (int)(j - i + 1);
+      for (int64_t q = i; q <= j; ++q) cid[q] = c;
+      ++c;
+    } else {
+      cid[i] = -1;
+    }
+    i = j + 1;
+  }
+  *count = c;
+}
+
+// E (FP32) and X32 (FP32 copy of X); pairs inside one cluster get r_ij / 2.
+__global__ void correction(const double* S, int64_t lds, const double* R, int64_t ldr,
+                           const double* lt, const int* rank, const int* cid, int64_t n, float* E,
+                           int64_t lde, const double* X, int64_t ldx, float* X32) {
+  const int64_t total = n * n;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = p % n, j = p / n;
+    const int64_t a = (i >= j) ? i : j, b = (i >= j) ? j : i;  // lower-triangle element
+    const double r = R[a + b * ldr], s = S[a + b * lds];
+    double e;
+    const int ci = cid[rank[i]], cj = cid[rank[j]];
+    if (i == j || (ci >= 0 && ci == cj)) {
+      e = 0.5 * r;
+    } else {
+      e = (s + lt[j] * r) / (lt[j] - lt[i]);
+    }
+    E[i + j * lde] = (float)e;
+    X32[i + j * n] = (float)X[i + j * ldx];
+  }
+}
+
+__global__ void add_correction(double* X, int64_t ldx, const float* P, int64_t n) {
+  const int64_t total = n * n;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = p % n, j = p / n;
+    X[i + j * ldx] += (double)P[p];
+  }
+}
+
+// rank of l_i in ascending order (ties by index); O(n^2) comparisons, one thread per i
+__global__ void ranks(const double* lt, int64_t n, int* rank) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = lt[i];
+  int64_t r = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    const double u = lt[j];
+    r += (u < v) || (u == v && j < i);
+  }
+  rank[i] = (int)r;
+}
+
+// Xs(:, rank[j]) = X(:, j); ls(rank[j]) = l_j.  grid (rows / 256, n)
+__global__ void permute_columns(const double* X, int64_t ldx, const int* rank, int64_t n,
+                                double* Xs, const double* lt, double* ls) {
+  const int64_t j = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t dst = rank[j];
+  if (i < n) Xs[i + dst * n] = X[i + j * ldx];
+  if (i == 0) ls[dst] = lt[j];
+}
+
+__global__ void copy_columns(const double* Xs, int64_t n, double* X, int64_t ldx) {
+  const int64_t total = n * n;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = p % n, j = p / n;
+    X[i + j * ldx] = Xs[p];
+  }
+}
+
+// Cyclic Jacobi on one symmetric c x c block (c <= 64), one CTA.
+// In: Sc (ld c).  Out: Q (ld c, eigenvectors in columns), w (eigenvalues),
+// both ascending.
+constexpr int kMaxCluster = 64;
+// A pair whose first-order coefficient exceeds this is diagonalised exactly
+// inside a cluster instead (its second-order error would not be small).
+constexpr double kUnsafeTau = 1e-2;
+
+__global__ void cluster_jacobi(const double* Sc, int c, double* Q, double* w, int32_t* status) {
+  __shared__ double a[kMaxCluster][kMaxCluster + 1];
+  __shared__ double q[kMaxCluster][kMaxCluster + 1];
+  __shared__ double rot[2];
+  __shared__ int s_done;
+  const int tid = threadIdx.x;
+  for (int p = tid; p < c * c; p += blockDim.x) {
+    const int i = p % c, j = p / c;
+    a[i][j] = 0.5 * (Sc[i + j * c] + Sc[j + i * c]);
+    q[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    if (tid == 0) {
+      double off = 0.0, fro = 0.0;
+      for (int i = 0; i < c; ++i)
+        for (int j = 0; j < c; ++j) {
+          fro += a[i][j] * a[i][j];
+          if (i != j) off += a[i][j] * a[i][j];
+        }
+      s_done = (off <= 1e-30 * fro) || fro == 0.0;
+    }
+    __syncthreads();
+    if (s_done) break;
+    for (int pi = 0; pi + 1 < c; ++pi)
+      for (int qi = pi + 1; qi < c; ++qi) {
+        if (tid == 0) {
+          const double apq = a[pi][qi];
+          double cs = 1.0, sn = 0.0;
+          if (fabs(apq) > 1e-18 * (fabs(a[pi][pi]) + fabs(a[qi][qi]))) {
+            const double theta = (a[qi][qi] - a[pi][pi]) / (2.0 * apq);
+            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            cs = 1.0 / sqrt(t * t + 1.0);
+            sn = t * cs;
+          }
+          rot[0] = cs;
+          rot[1] = sn;
+        }
+        __syncthreads();
+        const double cs = rot[0], sn = rot[1];
+        if (sn != 0.0) {
+          if (tid < c) {  // columns pi, qi
+            const double xp = a[tid][pi], xq = a[tid][qi];
+            a[tid][pi] = cs * xp - sn * xq;
+            a[tid][qi] = sn * xp + cs * xq;
+            const double vp = q[tid][pi], vq = q[tid][qi];
+            q[tid][pi] = cs * vp - sn * vq;
+            q[tid][qi] = sn * vp + cs * vq;
+          }
+          __syncthreads();
+          if (tid < c) {  // rows pi, qi
+            const double xp = a[pi][tid], xq = a[qi][tid];
+            a[pi][tid] = cs * xp - sn * xq;
+            a[qi][tid] = sn * xp + cs * xq;
+          }
+        }
+        __syncthreads();
+      }
+    if (sweep == 49 && tid == 0) raise_status(status, FRACLAP_ERR_NO_CONVERGENCE);
+  }
+  // ascending order (selection by thread 0), then write out
+  __shared__ int perm[kMaxCluster];
+  if (tid == 0) {
+    for (int i = 0; i < c; ++i) perm[i] = i;
+    for (int i = 0; i + 1 < c; ++i) {
+      int m = i;
+      for (int j = i + 1; j < c; ++j)
+        if (a[perm[j]][perm[j]] < a[perm[m]][perm[m]]) m = j;
+      const int t = perm[i];
+      perm[i] = perm[m];
+      perm[m] = t;
+    }
+  }
+  __syncthreads();
+  for (int p = tid; p < c * c; p += blockDim.x) {
+    const int i = p % c, j = p / c;
+    Q[i + j * c] = q[i][perm[j]];
+  }
+  if (tid < c) w[tid] = a[perm[tid]][perm[tid]];
+}
+
+// l_j = (x_j^T (A x_j)) / (x_j^T x_j); one block per column.
+__global__ void rayleigh(const double* X, int64_t ldx, const double* AX, int64_t ldax, int64_t n,
+                         double* l) {
+  const int64_t j = blockIdx.x;
+  const double* x = X + j * ldx;
+  const double* y = AX + j * ldax;
+  double num = 0.0, den = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    num = fma(x[i], y[i], num);
+    den = fma(x[i], x[i], den);
+  }
+  __shared__ double red[2][32];
+  num = warp_sum(num);
+  den = warp_sum(den);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = num;
+    red[1][threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (unsigned w = 0; w < blockDim.x / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    l[j] = a / b;
+  }
+}
+
+}  // namespace
+
+// Largest cluster the refinement diagonalises (clusters above 64 go through
+// the FP64 dense eigensolver of this library).
+constexpr int64_t kMaxBigCluster = 2048;
+
+size_t refine_ws(const fraclap_ctx* ctx, int64_t n) {
+  Arena ar;
+  ar.take<double>(n * n);      // AX, then sorted X
+  ar.take<double>(n * n);      // R
+  ar.take<double>(n * n);      // S
+  ar.take<float>(n * n);       // E
+  ar.take<float>(n * n);       // X32
+  ar.take<float>(n * n);       // P
+  ar.take<double>(n);          // l
+  ar.take<double>(n);          // sorted l
+  ar.take<int>(n);             // ranks
+  ar.take<int>(n);             // span reach
+  ar.take<int>(n);             // cluster id per sorted position
+  ar.take<int>(2 * n + 2);     // cluster list + count
+  ar.take<double>(8);          // norms, delta
+  const int64_t cmax = std::min<int64_t>(n, kMaxBigCluster);
+  ar.take<double>(n * cmax * 2 + 2 * cmax * cmax + cmax);
+  return ar.off + cluster_eig_ws(ctx, cmax);
+}
+
+int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col,
+               const double* val, double* X, int64_t ldx, double* lambda, int iters, Arena* ar,
+               cudaStream_t st) {
+  double* AX = ar->take<double>(n * n);
+  double* R = ar->take<double>(n * n);
+  double* S = ar->take<double>(n * n);
+  float* E = ar->take<float>(n * n);
+  float* X32 = ar->take<float>(n * n);
+  float* P = ar->take<float>(n * n);
+  double* lt = ar->take<double>(n);
+  double* ls = ar->take<double>(n);
+  int* rank = ar->take<int>(n);
+  int* reach = ar->take<int>(n);
+  int* cid = ar->take<int>(n);
+  int* clist = ar->take<int>(2 * n + 2);
+  double* scal = ar->take<double>(8);
+  ctx->refine_stats.clear();
+  const int64_t cmax = std::min<int64_t>(n, kMaxBigCluster);
+  double* cbuf = ar->take<double>(n * cmax * 2 + 2 * cmax * cmax + cmax);
+  Arena car = *ar;  // workspace of the dense eigensolver used on big clusters
+  FL_CHECK(ctx, cbuf != nullptr, FRACLAP_ERR_ALLOC, "refine: workspace too small");
+  const unsigned rows = (unsigned)cdiv(n, 128);
+  const unsigned flat = (unsigned)std::min<int64_t>(cdiv(n * n, 256), 152 * 16);
+  unsigned long long* nA = reinterpret_cast<unsigned long long*>(scal + 2);
+  double* delta = scal + 3;
+  using D64 = GemmDescT<double>;
+  using D32 = GemmDescT<float>;
+  for (int it = 0; it < iters; ++it) {
+    // AX = A X
+    spmm_csr<<<dim3(rows, (unsigned)std::min<int64_t>(n, 4096)), 128, 0, st>>>(n, rowptr, col, val, X, ldx, n, AX, n);
+    count_launch(ctx);
+    // R = I - X^T X, S = X^T (A X): lower triangles, FP64
+    FL_TRY(gemm<double>(ctx, true, false, kGemmLowerC, D64{n, n, n, X, ldx, X, ldx, R, n, nullptr, 0, nullptr, 0, 0, -1.0, 0.0}, 1, st));
+    add_identity<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(R, n, n);
+    count_launch(ctx);
+    FL_TRY(gemm<double>(ctx, true, false, kGemmLowerC, D64{n, n, n, X, ldx, AX, n, S, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
+    ritz_values<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(S, n, R, n, n, lt);
+    count_launch(ctx);
+    FL_CUDA(ctx, cudaMemsetAsync(scal, 0, 8 * sizeof(double), st));
+    frob_norms<<<flat, 256, 0, st>>>(S, n, R, n, lt, n, scal);
+    count_launch(ctx);
+    gershgorin<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, rowptr, val, nA);
+    count_launch(ctx);
+    {  // 2-norm estimates of S - diag(l) and R (power iteration)
+      double* xv = ls;              // reuse: n doubles
+      double* yv = AX;              // reuse: first n doubles
+      for (int which = 0; which < 2; ++which) {
+        const double* M = which == 0 ? S : R;
+        const double* shift = which == 0 ? lt : nullptr;
+        start_vec<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(xv, n);
+        count_launch(ctx);
+        for (int pit = 0; pit < 12; ++pit) {
+          symv_lower<<<(unsigned)cdiv(n, 128), 128, 0, st>>>(M, n, shift, n, xv, yv);
+          normalize_vec<<<1, 1024, 0, st>>>(yv, n, xv, scal + 4 + which);
+          count_launch(ctx);
+          count_launch(ctx);
+        }
+      }
+    }
+    cluster_threshold<<<1, 1, 0, st>>>(scal, scal + 4, nA, delta);
+    count_launch(ctx);
+    // clusters from unsafe pairs, in sorted order
+    ranks<<<(unsigned)cdiv(n, 128), 128, 0, st>>>(lt, n, rank);
+    count_launch(ctx);
+    init_reach<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(reach, n);
+    count_launch(ctx);
+    unsafe_spans<<<flat, 256, 0, st>>>(S, n, R, n, lt, rank, delta, kUnsafeTau, n, reach);
+    count_launch(ctx);
+    merge_spans<<<1, 1, 0, st>>>(reach, n, cid, clist + 1, clist);
+    count_launch(ctx);
+    correction<<<flat, 256, 0, st>>>(S, n, R, n, lt, rank, cid, n, E, n, X, ldx, X32);
+    count_launch(ctx);
+    // X += X E  (product in FP32)
+    FL_TRY(gemm<float>(ctx, false, false, kGemmPlain, D32{n, n, n, X32, n, E, n, P, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
+    add_correction<<<flat, 256, 0, st>>>(X, ldx, P, n);
+    count_launch(ctx);
+    // sort the columns by l
+    FL_CHECK(ctx, n <= 65535, FRACLAP_ERR_UNSUPPORTED, "refine: n too large");
+    permute_columns<<<dim3((unsigned)cdiv(n, 256), (unsigned)n), 256, 0, st>>>(X, ldx, rank, n, AX, lt, ls);
+    count_launch(ctx);
+    copy_columns<<<flat, 256, 0, st>>>(AX, n, X, ldx);
+    count_launch(ctx);
+    FL_CUDA(ctx, cudaMemcpyAsync(lambda, ls, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    int ncl = 0;
+    double hs[8];
+    FL_CUDA(ctx, cudaMemcpyAsync(&ncl, clist, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FL_CUDA(ctx, cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    FL_CUDA(ctx, cudaStreamSynchronize(st));
+    std::vector<int> cl(2 * (size_t)std::max(ncl, 0));
+    if (ncl > 0)
+      FL_CUDA(ctx, cudaMemcpy(cl.data(), clist + 1, sizeof(int) * 2 * ncl, cudaMemcpyDeviceToHost));
+    {
+      unsigned long long nab;
+      memcpy(&nab, &hs[2], sizeof(nab));
+      double na;
+      memcpy(&na, &nab, sizeof(na));
+      int cmaxseen = 0;
+      for (int q = 0; q < ncl; ++q) cmaxseen = std::max(cmaxseen, cl[2 * q + 1]);
+      const double row[8] = {hs[3], hs[4], hs[5], sqrt(hs[0]), sqrt(hs[1]), na, (double)ncl, (double)cmaxseen};
+      ctx->refine_stats.insert(ctx->refine_stats.end(), row, row + 8);
+    }
+    if (ncl > 0) {
+      double* AXc = cbuf;                        // n x c
+      double* Xn = cbuf + n * cmax;              // n x c
+      double* Sc = Xn + n * cmax;                // c x c
+      double* Qc = Sc + cmax * cmax;
+      for (int q = 0; q < ncl; ++q) {
+        const int i0 = cl[2 * q], c = cl[2 * q + 1];
+        FL_CHECK(ctx, c <= cmax, FRACLAP_ERR_UNSUPPORTED,
+                 "refine: a cluster of %d eigenvalues exceeds %lld", c, (long long)cmax);
+        double* Xc = X + (int64_t)i0 * ldx;
+        spmm_csr<<<dim3(rows, (unsigned)c), 128, 0, st>>>(n, rowptr, col, val, Xc, ldx, c, AXc, n);
+        count_launch(ctx);
+        FL_CUDA(ctx, cudaMemsetAsync(Sc, 0, sizeof(double) * c * c, st));
+        FL_TRY(gemm<double>(ctx, true, false, kGemmPlain, D64{c, c, n, Xc, ldx, AXc, n, Sc, c, nullptr, 0, nullptr, 0, 0, 1.0, 1.0}, (int)cdiv(n, 512), st));
+        if (c <= kMaxCluster) {
+          cluster_jacobi<<<1, 64, 0, st>>>(Sc, c, Qc, lambda + i0, ctx->d_status);
+          count_launch(ctx);
+        } else {
+          Arena sub = car;
+          FL_TRY(cluster_eig(ctx, Sc, c, lambda + i0, Qc, &sub, st));
+        }
+        FL_TRY(gemm<double>(ctx, false, false, kGemmPlain, D64{n, c, c, Xc, ldx, Qc, c, Xn, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
+        FL_CUDA(ctx, cudaMemcpy2DAsync(Xc, ldx * sizeof(double), Xn, n * sizeof(double), n * sizeof(double), c,
+                                       cudaMemcpyDeviceToDevice, st));
+      }
+    }
+    FL_CUDA(ctx, cudaGetLastError());
+  }
+  if (iters > 0) {  // eigenvalues: Rayleigh quotients of the refined vectors, ascending
+    spmm_csr<<<dim3(rows, (unsigned)std::min<int64_t>(n, 4096)), 128, 0, st>>>(n, rowptr, col, val, X, ldx, n, AX, n);
+    count_launch(ctx);
+    rayleigh<<<(unsigned)n, 256, 0, st>>>(X, ldx, AX, n, n, lt);
+    count_launch(ctx);
+    ranks<<<(unsigned)cdiv(n, 128), 128, 0, st>>>(lt, n, rank);
+    count_launch(ctx);
+    permute_columns<<<dim3((unsigned)cdiv(n, 256), (unsigned)n), 256, 0, st>>>(X, ldx, rank, n, AX, lt, ls);
+    count_launch(ctx);
+    copy_columns<<<flat, 256, 0, st>>>(AX, n, X, ldx);
+    count_launch(ctx);
+    FL_CUDA(ctx, cudaMemcpyAsync(lambda, ls, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    FL_CUDA(ctx, cudaGetLastError());
+  }
+  return 0;
+}
+
+}  // namespace fraclap

@@ -30,32 +30,35 @@ __device__ __forceinline__ int64_t sb_nsteps(int64_t s, int64_t n, int b) {
   return (n - 2 - s) / b + 1;  // valid for s <= n - 2
 }
 
+template <class T>
 struct SbArgs {
-  double* band;   // ld = 2b, band(i - j, j) = A(i, j)
+  T* band;        // ld = 2b, band(i - j, j) = A(i, j)
   int64_t n;
   int b;
   int64_t kmax;   // steps of sweep 0
-  double* refl;   // (n-1) * kmax * b
+  T* refl;        // (n-1) * kmax * b
   double* rtau;   // (n-1) * kmax
   int* progress;  // n, completed steps per sweep
   int32_t* status;
   long long limit;
 };
 
-__global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs a) {
-  extern __shared__ double sm[];
+template <class T>
+__global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
   const int b = a.b, ldb = 2 * b;
   const int64_t n = a.n;
-  double* xv = sm;                 // b
-  double* F = xv + 64;             // b x b  (F[t + q*b])
-  double* D = F + 64 * 64;         // b x b  full symmetric (D[t + u*b])
-  double* E = D + 64 * 64;         // b x b  (E[t + u*b])
-  double* pw = E + 64 * 64;        // b
-  double* wq = pw + 64;            // b
+  T* xv = sm;                 // b
+  T* F = xv + 64;             // b x b  (F[t + q*b])
+  T* D = F + 64 * 64;         // b x b  full symmetric (D[t + u*b])
+  T* E = D + 64 * 64;         // b x b  (E[t + u*b])
+  T* pw = E + 64 * 64;        // b
+  T* wq = pw + 64;            // b
   __shared__ double s_coef[4];
   __shared__ int s_abort;
   const int tid = threadIdx.x;
-  double* band = a.band;
+  T* band = a.band;
 #define BAND(i, j) band[((i) - (j)) + (int64_t)(j) * ldb]
 
   for (int64_t s = blockIdx.x; s < n - 1; s += gridDim.x) {
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs a) {
       for (int p = tid; p < L * L; p += SB_NT) {
         const int t = p % L, u = p / L;
         if (t >= u) {
-          const double v = __ldcg(&BAND(r0 + t, r0 + u));
+          const T v = __ldcg(&BAND(r0 + t, r0 + u));
           D[t + u * b] = v;
           D[u + t * b] = v;
         }
@@ -110,10 +113,10 @@ __global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs a) {
         E[t + u * b] = __ldcg(&BAND(r1 + 1 + t, r0 + u));
       }
       __syncthreads();
-      // ---- Householder vector from x (warp 0) ----
+      // ---- Householder vector from x (warp 0), norms and scaling in FP64 ----
       if (tid < 32) {
         double tail = 0.0;
-        for (int t = 1 + tid; t < L; t += 32) tail += xv[t] * xv[t];
+        for (int t = 1 + tid; t < L; t += 32) tail += (double)xv[t] * (double)xv[t];
         tail = warp_sum(tail);
         const double x0 = xv[0];
         double beta = x0, v0 = 1.0, tu = 0.0;
@@ -130,25 +133,26 @@ __global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs a) {
         }
         __syncwarp();
         const double inv = 1.0 / v0;
-        for (int t = 1 + tid; t < L; t += 32) xv[t] = (tu == 0.0) ? 0.0 : xv[t] * inv;
-        if (tid == 0) xv[0] = 1.0;
+        for (int t = 1 + tid; t < L; t += 32) xv[t] = (tu == 0.0) ? T(0) : (T)((double)xv[t] * inv);
+        if (tid == 0) xv[0] = T(1);
       }
       __syncthreads();
       const double beta = s_coef[0], tu = s_coef[1];
-      double* rv = a.refl + ((int64_t)s * a.kmax + k) * b;
-      for (int t = tid; t < b; t += SB_NT) rv[t] = (t < L) ? xv[t] : 0.0;
+      const T tuT = (T)tu;
+      T* rv = a.refl + ((int64_t)s * a.kmax + k) * b;
+      for (int t = tid; t < b; t += SB_NT) rv[t] = (t < L) ? xv[t] : T(0);
       if (tid == 0) a.rtau[s * a.kmax + k] = tu;
       if (tu != 0.0) {
         // ---- F <- H F, E <- E H, p = tau D v ----
         for (int q = tid; q < nf; q += SB_NT) {
-          double w = 0.0;
+          T w = T(0);
           for (int t = 0; t < L; ++t) w += xv[t] * F[t + q * b];
-          wq[q] = tu * w;
+          wq[q] = tuT * w;
         }
         for (int t = tid; t < L; t += SB_NT) {
-          double p = 0.0;
+          T p = T(0);
           for (int u = 0; u < L; ++u) p += D[t + u * b] * xv[u];
-          pw[t] = tu * p;
+          pw[t] = tuT * p;
         }
         __syncthreads();
         for (int p = tid; p < L * nf; p += SB_NT) {
@@ -157,17 +161,17 @@ __global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs a) {
         }
         if (tid == 0) {
           double pv = 0.0;
-          for (int t = 0; t < L; ++t) pv += pw[t] * xv[t];
+          for (int t = 0; t < L; ++t) pv += (double)pw[t] * (double)xv[t];
           s_coef[3] = 0.5 * tu * pv;
         }
         __syncthreads();
-        const double K = s_coef[3];
+        const T K = (T)s_coef[3];
         for (int t = tid; t < L; t += SB_NT) pw[t] -= K * xv[t];  // w = p - K v
         // E <- E H : y_t = tau E(t,:) v
         for (int t = tid; t < Lb; t += SB_NT) {
-          double y = 0.0;
+          T y = T(0);
           for (int u = 0; u < L; ++u) y += E[t + u * b] * xv[u];
-          y *= tu;
+          y *= tuT;
           for (int u = 0; u < L; ++u) E[t + u * b] -= y * xv[u];
         }
         __syncthreads();
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs a) {
         }
         __syncthreads();
         // ---- store ----
-        for (int t = tid; t < L; t += SB_NT) __stcg(&BAND(r0 + t, c), (t == 0) ? beta : 0.0);
+        for (int t = tid; t < L; t += SB_NT) __stcg(&BAND(r0 + t, c), (t == 0) ? (T)beta : T(0));
         for (int p = tid; p < L * nf; p += SB_NT) {
           const int t = p % L, q = p / L;
           __stcg(&BAND(r0 + t, c + 1 + q), F[t + q * b]);
@@ -201,7 +205,8 @@ __global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs a) {
 #undef BAND
 }
 
-__global__ void band_diagonals(const double* band, int ldb, int64_t n, double* d, double* e) {
+template <class T>
+__global__ void band_diagonals(const T* band, int ldb, int64_t n, double* d, double* e) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   d[i] = band[i * ldb];
@@ -220,19 +225,19 @@ __global__ void band_diagonals(const double* band, int ldb, int64_t n, double* d
 // loaded one batch ahead.  Work: 4 L n flops per reflector of length L.
 constexpr int Q2T_WARPS = 8, Q2T_D = 8;
 
-template <int B, int P>
+template <class T, int B, int P>
 __global__ void __launch_bounds__(Q2T_WARPS * 32, 2)
-q2t_apply_kernel(const double* __restrict__ refl, const double* __restrict__ rtau, int64_t n,
-                 int64_t kmax, double* Y, int64_t ldy, int64_t ncols) {
+q2t_apply_kernel(const T* __restrict__ refl, const double* __restrict__ rtau, int64_t n,
+                 int64_t kmax, T* Y, int64_t ldy, int64_t ncols) {
   constexpr int R = B / P, CPW = 32 / P, D = Q2T_D, NT = Q2T_WARPS * 32;
   constexpr int PER = (D * B + NT - 1) / NT;  // staged doubles per thread
-  __shared__ double vbuf[2][D][B];
-  __shared__ double tbuf[2][D];
+  __shared__ T vbuf[2][D][B];
+  __shared__ T tbuf[2][D];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int part = lane / CPW, cl = lane % CPW;
   const int64_t col = ((int64_t)blockIdx.x * Q2T_WARPS + warp) * CPW + cl;
   const bool active = col < ncols;
-  double* yc = Y + (active ? col : 0);
+  T* yc = Y + (active ? col : 0);
   const unsigned full = 0xffffffffu;
 
   for (int64_t k = 0; k < kmax; ++k) {
@@ -240,10 +245,10 @@ q2t_apply_kernel(const double* __restrict__ refl, const double* __restrict__ rta
     if (smax < 0) break;
     const int64_t nbatch = (smax + D) / D;  // reflectors s = smax .. 0
     // stage a batch of reflectors (q = batch * D + j  <->  s = smax - q)
-    auto fetch = [&](int64_t batch, double* vr, double* tr) {
+    auto fetch = [&](int64_t batch, T* vr, T* tr) {
       for (int e = 0; e < PER; ++e) {
         const int t = threadIdx.x + e * NT;
-        double v = 0.0;
+        T v = T(0);
         if (t < D * B) {
           const int j = t / B, c = t % B;
           const int64_t sj = smax - (batch * D + j);
@@ -251,71 +256,71 @@ q2t_apply_kernel(const double* __restrict__ refl, const double* __restrict__ rta
         }
         vr[e] = v;
       }
-      double tv = 0.0;
+      T tv = T(0);
       if (threadIdx.x < D) {
         const int64_t sj = smax - (batch * D + threadIdx.x);
-        if (sj >= 0) tv = __ldg(rtau + sj * kmax + k);
+        if (sj >= 0) tv = (T)__ldg(rtau + sj * kmax + k);
       }
       *tr = tv;
     };
-    auto store = [&](int buf, const double* vr, double tr) {
+    auto store = [&](int buf, const T* vr, T tr) {
       for (int e = 0; e < PER; ++e) {
         const int t = threadIdx.x + e * NT;
         if (t < D * B) vbuf[buf][t / B][t % B] = vr[e];
       }
       if (threadIdx.x < D) tbuf[buf][threadIdx.x] = tr;
     };
-    double vr[PER], tr;
+    T vr[PER], tr;
     fetch(0, vr, &tr);
     __syncthreads();  // previous k's readers are done with the buffers
     store(0, vr, tr);
 
     int64_t r0 = n - 1;  // window rows r0 .. r0 + B - 1 (rows >= n are zero)
-    double w[R];
+    T w[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int64_t row = r0 + part * R + i;
-      w[i] = (active && row < n) ? yc[row * ldy] : 0.0;
+      w[i] = (active && row < n) ? yc[row * ldy] : T(0);
     }
-    double pf[D];  // rows entering the window during the current batch (part 0)
+    T pf[D];  // rows entering the window during the current batch (part 0)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       const int64_t row = r0 - 1 - j;
-      pf[j] = (part == 0 && active && row >= 1 + k * B) ? yc[row * ldy] : 0.0;
+      pf[j] = (part == 0 && active && row >= 1 + k * B) ? yc[row * ldy] : T(0);
     }
     __syncthreads();
     for (int64_t batch = 0; batch < nbatch; ++batch) {
       const int buf = (int)(batch & 1);
       const bool more = batch + 1 < nbatch;
       if (more) fetch(batch + 1, vr, &tr);
-      double pn[D];  // rows for the next batch
+      T pn[D];  // rows for the next batch
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         const int64_t row = r0 - 1 - D - j;
-        pn[j] = (more && part == 0 && active && row >= 1 + k * B) ? yc[row * ldy] : 0.0;
+        pn[j] = (more && part == 0 && active && row >= 1 + k * B) ? yc[row * ldy] : T(0);
       }
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         const int64_t s = smax - (batch * D + j);
         if (s < 0) break;
-        const double* v = &vbuf[buf][j][part * R];
-        double d0 = 0.0, d1 = 0.0;
+        const T* v = &vbuf[buf][j][part * R];
+        T d0 = T(0), d1 = T(0);
 #pragma unroll
         for (int i = 0; i < R; i += 2) {
           d0 = fma(v[i], w[i], d0);
           if (i + 1 < R) d1 = fma(v[i + 1], w[i + 1], d1);
         }
-        double dot = d0 + d1;
+        T dot = d0 + d1;
 #pragma unroll
         for (int o = CPW; o < 32; o <<= 1) dot += __shfl_xor_sync(full, dot, o);
-        const double f = tbuf[buf][j] * dot;
+        const T f = tbuf[buf][j] * dot;
 #pragma unroll
         for (int i = 0; i < R; ++i) w[i] = fma(-f, v[i], w[i]);
         if (s > 0) {  // slide the window up by one row
-          const double out = w[R - 1];
+          const T out = w[R - 1];
           const int64_t leaving = r0 + B - 1;
           if (part == P - 1 && active && leaving < n) yc[leaving * ldy] = out;
-          const double prev = __shfl_up_sync(full, out, CPW);
+          const T prev = __shfl_up_sync(full, out, CPW);
 #pragma unroll
           for (int i = R - 1; i > 0; --i) w[i] = w[i - 1];
           w[0] = (part == 0) ? pf[j] : prev;
@@ -338,9 +343,10 @@ q2t_apply_kernel(const double* __restrict__ refl, const double* __restrict__ rta
 }
 
 // 32 x 32 tiled transpose: B(j, i) = A(i, j), A is rows x cols.
-__global__ void transpose_kernel(const double* A, int64_t lda, double* Bm, int64_t ldb, int64_t rows,
+template <class T>
+__global__ void transpose_kernel(const T* A, int64_t lda, T* Bm, int64_t ldb, int64_t rows,
                                  int64_t cols) {
-  __shared__ double tile[32][33];
+  __shared__ T tile[32][33];
   const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
   for (int t = threadIdx.y; t < 32; t += blockDim.y) {
     const int64_t i = i0 + threadIdx.x, j = j0 + t;
@@ -355,64 +361,68 @@ __global__ void transpose_kernel(const double* A, int64_t lda, double* Bm, int64
 
 }  // namespace
 
-int stage2_take(Arena* ar, int64_t n, int b, Stage2* s) {
+template <class T>
+int stage2_take(Arena* ar, int64_t n, int b, Stage2T<T>* s) {
   s->kmax = (n >= 2) ? (n - 2) / b + 1 : 0;
   const int64_t nsw = (n >= 2) ? n - 1 : 0;
-  s->refl = ar->take<double>(nsw * s->kmax * b);
+  s->refl = ar->take<T>(nsw * s->kmax * b);
   s->rtau = ar->take<double>(nsw * s->kmax);
   s->progress = ar->take<int>(n + 1);
   return 0;
 }
 
-int sb2st_run(fraclap_ctx* ctx, double* band, int64_t n, int b, double* d, double* e, Stage2* s,
+template <class T>
+int sb2st_run(fraclap_ctx* ctx, T* band, int64_t n, int b, double* d, double* e, Stage2T<T>* s,
               cudaStream_t st) {
   if (n >= 2) {
     FL_CUDA(ctx, cudaMemsetAsync(s->progress, 0, sizeof(int) * (n + 1), st));
     FL_CUDA(ctx, cudaMemsetAsync(s->rtau, 0, sizeof(double) * (n - 1) * s->kmax, st));
-    SbArgs a{band, n, b, s->kmax, s->refl, s->rtau, s->progress, ctx->d_status, ctx->wait_cycles};
-    const size_t smem = sizeof(double) * (64 + 3 * 64 * 64 + 2 * 64);
-    FL_CUDA(ctx, cudaFuncSetAttribute(sb2st_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SbArgs<T> a{band, n, b, s->kmax, s->refl, s->rtau, s->progress, ctx->d_status, ctx->wait_cycles};
+    const size_t smem = sizeof(T) * (64 + 3 * 64 * 64 + 2 * 64);
+    FL_CUDA(ctx, cudaFuncSetAttribute(sb2st_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sb2st_kernel, SB_NT, smem));
+    FL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sb2st_kernel<T>, SB_NT, smem));
     FL_CHECK(ctx, per_sm >= 1, FRACLAP_ERR_UNSUPPORTED, "sb2st: kernel does not fit on an SM");
     int64_t G = (int64_t)ctx->sm_count * per_sm;
     if (G > n - 1) G = n - 1;
     void* args[] = {&a};
     count_launch(ctx);
-      FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)sb2st_kernel, dim3((unsigned)G), dim3(SB_NT), args, smem, st));
+    FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)sb2st_kernel<T>, dim3((unsigned)G), dim3(SB_NT), args, smem, st));
   }
   if (n >= 1) {
-    band_diagonals<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(band, 2 * b, n, d, e);
+    band_diagonals<T><<<(unsigned)cdiv(n, 256), 256, 0, st>>>(band, 2 * b, n, d, e);
     count_launch(ctx);
     FL_CUDA(ctx, cudaGetLastError());
   }
   return 0;
 }
 
-int transpose_run(fraclap_ctx* ctx, const double* A, int64_t lda, double* Bm, int64_t ldb,
-                  int64_t rows, int64_t cols, cudaStream_t st) {
+template <class T>
+int transpose_run(fraclap_ctx* ctx, const T* A, int64_t lda, T* Bm, int64_t ldb, int64_t rows,
+                  int64_t cols, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return 0;
   dim3 grid((unsigned)cdiv(rows, 32), (unsigned)cdiv(cols, 32));
   FL_CHECK(ctx, grid.y <= 65535, FRACLAP_ERR_UNSUPPORTED, "transpose: too many columns");
-  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(A, lda, Bm, ldb, rows, cols);
+  transpose_kernel<T><<<grid, dim3(32, 8), 0, st>>>(A, lda, Bm, ldb, rows, cols);
   count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   return 0;
 }
 
 // Z <- Q2 Z (n x ncols, ld ldz), through the transposed copy Yt (ld >= ncols).
-int q2_apply_run(fraclap_ctx* ctx, const Stage2* s, int64_t n, int b, double* Z, int64_t ldz,
-                 int64_t ncols, double* Yt, int64_t ldy, cudaStream_t st) {
+template <class T>
+int q2_apply_run(fraclap_ctx* ctx, const Stage2T<T>* s, int64_t n, int b, T* Z, int64_t ldz,
+                 int64_t ncols, T* Yt, int64_t ldy, cudaStream_t st) {
   if (n < 2 || ncols <= 0) return 0;
-  FL_TRY(transpose_run(ctx, Z, ldz, Yt, ldy, n, ncols, st));
+  FL_TRY(transpose_run<T>(ctx, Z, ldz, Yt, ldy, n, ncols, st));
   int cpw = 0;
-#define FL_Q2T(BB, PP)                                                                     \
-  if (b == BB) {                                                                           \
-    cpw = 32 / PP;                                                                         \
-    const int64_t grid = cdiv(ncols, (int64_t)cpw * Q2T_WARPS);                             \
-    q2t_apply_kernel<BB, PP><<<(unsigned)grid, Q2T_WARPS * 32, 0, st>>>(s->refl, s->rtau, n, \
-                                                                       s->kmax, Yt, ldy, ncols); \
-    count_launch(ctx);                                                                     \
+#define FL_Q2T(BB, PP)                                                                        \
+  if (b == BB) {                                                                              \
+    cpw = 32 / PP;                                                                            \
+    const int64_t grid = cdiv(ncols, (int64_t)cpw * Q2T_WARPS);                                \
+    q2t_apply_kernel<T, BB, PP><<<(unsigned)grid, Q2T_WARPS * 32, 0, st>>>(s->refl, s->rtau, n, \
+                                                                          s->kmax, Yt, ldy, ncols); \
+    count_launch(ctx);                                                                        \
   }
   FL_Q2T(4, 1)
   FL_Q2T(8, 2)
@@ -422,7 +432,16 @@ int q2_apply_run(fraclap_ctx* ctx, const Stage2* s, int64_t n, int b, double* Z,
 #undef FL_Q2T
   FL_CHECK(ctx, cpw != 0, FRACLAP_ERR_UNSUPPORTED, "q2 back-transformation: band width %d not in {4, 8, 16, 32, 64}", b);
   FL_CUDA(ctx, cudaGetLastError());
-  return transpose_run(ctx, Yt, ldy, Z, ldz, ncols, n, st);
+  return transpose_run<T>(ctx, Yt, ldy, Z, ldz, ncols, n, st);
 }
+
+template int stage2_take<double>(Arena*, int64_t, int, Stage2T<double>*);
+template int stage2_take<float>(Arena*, int64_t, int, Stage2T<float>*);
+template int sb2st_run<double>(fraclap_ctx*, double*, int64_t, int, double*, double*, Stage2T<double>*, cudaStream_t);
+template int sb2st_run<float>(fraclap_ctx*, float*, int64_t, int, double*, double*, Stage2T<float>*, cudaStream_t);
+template int transpose_run<double>(fraclap_ctx*, const double*, int64_t, double*, int64_t, int64_t, int64_t, cudaStream_t);
+template int transpose_run<float>(fraclap_ctx*, const float*, int64_t, float*, int64_t, int64_t, int64_t, cudaStream_t);
+template int q2_apply_run<double>(fraclap_ctx*, const Stage2T<double>*, int64_t, int, double*, int64_t, int64_t, double*, int64_t, cudaStream_t);
+template int q2_apply_run<float>(fraclap_ctx*, const Stage2T<float>*, int64_t, int, float*, int64_t, int64_t, float*, int64_t, cudaStream_t);
 
 }  // namespace fraclap

@@ -40,6 +40,7 @@ struct MergeInfo {
   int64_t nrot; // rotations recorded
 };
 
+template <class T>
 struct DcBuf {
   double* D;      // n: working diagonal (beta subtracted at split points)
   double* Dp;     // n: sorted (signed) D of the merge
@@ -58,11 +59,11 @@ struct DcBuf {
   int* outsrc;    // n: final column -> source (>= 0: new column i; < 0: -1 - deflated sorted pos)
   double* outval; // n: final eigenvalues
   MergeInfo* info;  // per merge
-  GemmDesc* desc;   // per merge
-  double* Wq;     // gathered Q, n_m x n_m per merge
-  double* Qnd;    // survivors' columns, n_m x K
-  double* U;      // K x K (ld n_m)
-  double* G;      // n_m x K (ld n_m)
+  GemmDescT<T>* desc;  // per merge
+  T* Wq;          // gathered Q, n_m x n_m per merge
+  T* Qnd;         // survivors' columns, n_m x K
+  T* U;           // K x K (ld n_m)
+  T* G;           // n_m x K (ld n_m)
 };
 
 // ----------------------------------------------------------------------------
@@ -83,8 +84,9 @@ __global__ void dc_setup(const double* d, const double* e, int64_t n, int L, dou
 }
 
 // One warp per leaf; leaf size <= 32.
+template <class T>
 __global__ void dc_leaf(const double* D, const double* e, int64_t n, int L, double* lambda,
-                        double* Z, int64_t ldz, int32_t* status) {
+                        T* Z, int64_t ldz, int32_t* status) {
   __shared__ double sd[4][32], se[4][32], sc[4][32], ss[4][32];
   __shared__ double sz[4][32][33];
   __shared__ int sperm[4][32];
@@ -184,13 +186,14 @@ __global__ void dc_leaf(const double* D, const double* e, int64_t n, int L, doub
   __syncwarp();
   if (lane < m) {
     lambda[lo + lane] = d[sperm[w][lane]];
-    for (int c = 0; c < m; ++c) Z[(lo + lane) + (lo + c) * ldz] = sz[w][lane][sperm[w][c]];
+    for (int c = 0; c < m; ++c) Z[(lo + lane) + (lo + c) * ldz] = (T)sz[w][lane][sperm[w][c]];
   }
 }
 
 // ----------------------------------------------------------------------------
 // Merge preparation: one CTA per merge, sequential parts on thread 0.
-__global__ void dc_merge_prep(DcBuf B, const double* e, const double* lambda, const double* Z,
+template <class T>
+__global__ void dc_merge_prep(DcBuf<T> B, const double* e, const double* lambda, const T* Z,
                               int64_t ldz, int64_t n, int L, int level, int64_t nmax) {
   const int64_t j = blockIdx.x;
   const int64_t span = (int64_t)1 << level;
@@ -205,7 +208,7 @@ __global__ void dc_merge_prep(DcBuf B, const double* e, const double* lambda, co
   const double beta = e[mid - 1];
   const double sgn = (beta < 0.0) ? -1.0 : 1.0;
   for (int64_t i = threadIdx.x; i < nm; i += blockDim.x) {
-    zloc[i] = (i < n1) ? Z[(mid - 1) + (lo + i) * ldz] : Z[mid + (lo + i) * ldz];
+    zloc[i] = (i < n1) ? (double)Z[(mid - 1) + (lo + i) * ldz] : (double)Z[mid + (lo + i) * ldz];
     dloc[i] = sgn * lambda[lo + i];
   }
   __syncthreads();
@@ -288,7 +291,7 @@ __global__ void dc_merge_prep(DcBuf B, const double* e, const double* lambda, co
   inf->nrot = nrot;
   // GEMM descriptor: G = Qnd (nm x K) * U (K x K)
   const int64_t off = lo * nmax;
-  GemmDesc d{};
+  GemmDescT<T> d{};
   d.M = nm; d.N = K; d.K = K;
   d.A = B.Qnd + off; d.lda = nm;
   d.B = B.U + off; d.ldb = nm;
@@ -300,31 +303,33 @@ __global__ void dc_merge_prep(DcBuf B, const double* e, const double* lambda, co
 
 // Gather Q columns into sorted order and apply the deflation rotations.
 // grid: (ceil(nmax/128), nmerge); thread = row of the merge block.
-__global__ void dc_gather(DcBuf B, const double* Z, int64_t ldz, int64_t nmax) {
+template <class T>
+__global__ void dc_gather(DcBuf<T> B, const T* Z, int64_t ldz, int64_t nmax) {
   const MergeInfo inf = B.info[blockIdx.y];
   const int64_t nm = inf.hi - inf.lo;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nm) return;
   const int64_t lo = inf.lo, n1 = inf.mid - inf.lo;
-  double* Wq = B.Wq + lo * nmax;
+  T* Wq = B.Wq + lo * nmax;
   const int* perm = B.perm + lo;
   for (int64_t i = 0; i < nm; ++i) {
     const int64_t c = perm[i];
     // block-diagonal: row r of block 1 pairs with columns of block 1 only
     const bool same = (r < n1) == (c < n1);
-    Wq[r + i * nm] = same ? Z[(lo + r) + (lo + c) * ldz] : 0.0;
+    Wq[r + i * nm] = same ? Z[(lo + r) + (lo + c) * ldz] : T(0);
   }
   for (int64_t q = 0; q < inf.nrot; ++q) {
     const int64_t a = B.rot_i[lo + q], b = B.rot_j[lo + q];
     const double c = B.rot_c[lo + q], s = B.rot_s[lo + q];
     const double xa = Wq[r + a * nm], xb = Wq[r + b * nm];
-    Wq[r + a * nm] = c * xa + s * xb;
-    Wq[r + b * nm] = -s * xa + c * xb;
+    Wq[r + a * nm] = (T)(c * xa + s * xb);
+    Wq[r + b * nm] = (T)(-s * xa + c * xb);
   }
 }
 
 // Secular equation roots; thread = root.
-__global__ void dc_secular(DcBuf B, int32_t* status) {
+template <class T>
+__global__ void dc_secular(DcBuf<T> B, int32_t* status) {
   const MergeInfo inf = B.info[blockIdx.y];
   const int64_t K = inf.K;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -403,7 +408,8 @@ __global__ void dc_secular(DcBuf B, int32_t* status) {
 }
 
 // Gu-Eisenstat: zhat_i^2 = (lam_{K-1} - d_i)/rho * prod_{j<K-1} (lam_j - d_i)/(d_j' - d_i).
-__global__ void dc_zhat(DcBuf B) {
+template <class T>
+__global__ void dc_zhat(DcBuf<T> B) {
   const MergeInfo inf = B.info[blockIdx.y];
   const int64_t K = inf.K;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -422,7 +428,8 @@ __global__ void dc_zhat(DcBuf B) {
 }
 
 // U(:, i) = zhat ./ (d - lambda_i), normalised; one CTA per (column, merge).
-__global__ void dc_vectors(DcBuf B, int64_t nmax) {
+template <class T>
+__global__ void dc_vectors(DcBuf<T> B, int64_t nmax) {
   const MergeInfo inf = B.info[blockIdx.y];
   const int64_t K = inf.K, i = blockIdx.x;
   if (i >= K) return;
@@ -431,11 +438,10 @@ __global__ void dc_vectors(DcBuf B, int64_t nmax) {
   const double* zh = B.zhat + inf.lo;
   const double t = B.tau[inf.lo + i];
   const double dorg = dd[B.org[inf.lo + i]];
-  double* u = B.U + inf.lo * nmax + i * nm;
+  T* u = B.U + inf.lo * nmax + i * nm;
   double s = 0.0;
   for (int64_t j = threadIdx.x; j < K; j += blockDim.x) {
     const double v = zh[j] / ((dd[j] - dorg) - t);
-    u[j] = v;
     s += v * v;
   }
   __shared__ double red[32];
@@ -449,23 +455,26 @@ __global__ void dc_vectors(DcBuf B, int64_t nmax) {
   }
   __syncthreads();
   const double inv = 1.0 / sqrt(red[0]);
-  for (int64_t j = threadIdx.x; j < K; j += blockDim.x) u[j] *= inv;
+  for (int64_t j = threadIdx.x; j < K; j += blockDim.x)
+    u[j] = (T)(zh[j] / ((dd[j] - dorg) - t) * inv);
 }
 
 // Qnd(:, q) = Wq(:, kept[q]) for survivors; grid (ceil(nmax/128), nmerge).
-__global__ void dc_gather_kept(DcBuf B, int64_t nmax) {
+template <class T>
+__global__ void dc_gather_kept(DcBuf<T> B, int64_t nmax) {
   const MergeInfo inf = B.info[blockIdx.y];
   const int64_t nm = inf.hi - inf.lo;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nm) return;
-  const double* Wq = B.Wq + inf.lo * nmax;
-  double* Q = B.Qnd + inf.lo * nmax;
+  const T* Wq = B.Wq + inf.lo * nmax;
+  T* Q = B.Qnd + inf.lo * nmax;
   const int* kept = B.kept + inf.lo;
   for (int64_t q = 0; q < inf.K; ++q) Q[r + q * nm] = Wq[r + (int64_t)kept[q] * nm];
 }
 
 // Final ascending order of the merged spectrum (thread 0 per merge).
-__global__ void dc_order(DcBuf B) {
+template <class T>
+__global__ void dc_order(DcBuf<T> B) {
   if (threadIdx.x != 0) return;
   const MergeInfo inf = B.info[blockIdx.x];
   const int64_t lo = inf.lo, nm = inf.hi - inf.lo, K = inf.K, nd = nm - K;
@@ -497,14 +506,15 @@ __global__ void dc_order(DcBuf B) {
 }
 
 // Z(lo:hi, lo + p) = chosen column; lambda(lo + p) = value.  grid (nmax, nmerge).
-__global__ void dc_scatter(DcBuf B, double* lambda, double* Z, int64_t ldz, int64_t nmax) {
+template <class T>
+__global__ void dc_scatter(DcBuf<T> B, double* lambda, T* Z, int64_t ldz, int64_t nmax) {
   const MergeInfo inf = B.info[blockIdx.y];
   const int64_t nm = inf.hi - inf.lo, p = blockIdx.x;
   if (p >= nm) return;
   const int src = B.outsrc[inf.lo + p];
-  const double* col = (src >= 0) ? B.G + inf.lo * nmax + (int64_t)src * nm
-                                 : B.Wq + inf.lo * nmax + (int64_t)(-1 - src) * nm;
-  double* dst = Z + inf.lo + (inf.lo + p) * ldz;
+  const T* col = (src >= 0) ? B.G + inf.lo * nmax + (int64_t)src * nm
+                            : B.Wq + inf.lo * nmax + (int64_t)(-1 - src) * nm;
+  T* dst = Z + inf.lo + (inf.lo + p) * ldz;
   for (int64_t r = threadIdx.x; r < nm; r += blockDim.x) dst[r] = col[r];
   if (threadIdx.x == 0) lambda[inf.lo + p] = B.outval[inf.lo + p];
 }
@@ -525,7 +535,8 @@ int64_t level_nmax(int64_t n, int L, int level) {
   return mx;
 }
 
-int take_bufs(Arena* ar, int64_t n, int L, DcBuf* B) {
+template <class T>
+int take_bufs(Arena* ar, int64_t n, int L, DcBuf<T>* B) {
   B->D = ar->take<double>(n);
   B->Dp = ar->take<double>(n);
   B->zp = ar->take<double>(n);
@@ -544,65 +555,72 @@ int take_bufs(Arena* ar, int64_t n, int L, DcBuf* B) {
   B->outval = ar->take<double>(n);
   const int64_t nmerge_max = (L >= 1) ? ((int64_t)1 << (L - 1)) : 1;
   B->info = ar->take<MergeInfo>(nmerge_max);
-  B->desc = ar->take<GemmDesc>(nmerge_max);
+  B->desc = ar->take<GemmDescT<T>>(nmerge_max);
   // per-merge n_m x n_m blocks at offset lo * nmax (<= n * n in total + slack)
   const int64_t big = (n + 2) * n;
-  B->Wq = ar->take<double>(big);
-  B->Qnd = ar->take<double>(big);
-  B->U = ar->take<double>(big);
-  B->G = ar->take<double>(big);
+  B->Wq = ar->take<T>(big);
+  B->Qnd = ar->take<T>(big);
+  B->U = ar->take<T>(big);
+  B->G = ar->take<T>(big);
   return 0;
 }
 
 }  // namespace
 
+template <class T>
 size_t stedc_ws(const fraclap_ctx* ctx, int64_t n) {
   Arena ar;
-  DcBuf B;
-  take_bufs(&ar, n, tree_levels(n, ctx->leaf_size), &B);
+  DcBuf<T> B;
+  take_bufs<T>(&ar, n, tree_levels(n, ctx->leaf_size), &B);
   return ar.off;
 }
 
-int stedc_run(fraclap_ctx* ctx, const double* d, const double* e, int64_t n, double* lambda,
-              double* Z, int64_t ldz, Arena* ar, cudaStream_t st) {
+template <class T>
+int stedc_run(fraclap_ctx* ctx, const double* d, const double* e, int64_t n, double* lambda, T* Z,
+              int64_t ldz, Arena* ar, cudaStream_t st) {
   if (n <= 0) return 0;
   const int L = tree_levels(n, ctx->leaf_size);
-  DcBuf B;
-  take_bufs(ar, n, L, &B);
+  DcBuf<T> B;
+  take_bufs<T>(ar, n, L, &B);
   FL_CHECK(ctx, B.G != nullptr, FRACLAP_ERR_ALLOC, "stedc: workspace too small");
-  FL_CUDA(ctx, cudaMemset2DAsync(Z, ldz * sizeof(double), 0, n * sizeof(double), n, st));
+  FL_CUDA(ctx, cudaMemset2DAsync(Z, ldz * sizeof(T), 0, n * sizeof(T), n, st));
   dc_setup<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(d, e, n, L, B.D);
   count_launch(ctx);
   const int64_t nleaf = (int64_t)1 << L;
-  dc_leaf<<<(unsigned)cdiv(nleaf, 4), 128, 0, st>>>(B.D, e, n, L, lambda, Z, ldz, ctx->d_status);
+  dc_leaf<T><<<(unsigned)cdiv(nleaf, 4), 128, 0, st>>>(B.D, e, n, L, lambda, Z, ldz, ctx->d_status);
   count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   for (int level = 1; level <= L; ++level) {
     const int64_t nmerge = (int64_t)1 << (L - level);
     const int64_t nmax = level_nmax(n, L, level);
     FL_CHECK(ctx, nmerge <= 65535 && nmax < (1LL << 31), FRACLAP_ERR_UNSUPPORTED, "stedc: too large");
-    dc_merge_prep<<<(unsigned)nmerge, 128, 0, st>>>(B, e, lambda, Z, ldz, n, L, level, nmax);
+    dc_merge_prep<T><<<(unsigned)nmerge, 128, 0, st>>>(B, e, lambda, Z, ldz, n, L, level, nmax);
     count_launch(ctx);
     const dim3 rows((unsigned)cdiv(nmax, 128), (unsigned)nmerge);
-    dc_gather<<<rows, 128, 0, st>>>(B, Z, ldz, nmax);
+    dc_gather<T><<<rows, 128, 0, st>>>(B, Z, ldz, nmax);
     count_launch(ctx);
-    dc_secular<<<rows, 128, 0, st>>>(B, ctx->d_status);
+    dc_secular<T><<<rows, 128, 0, st>>>(B, ctx->d_status);
     count_launch(ctx);
-    dc_zhat<<<rows, 128, 0, st>>>(B);
+    dc_zhat<T><<<rows, 128, 0, st>>>(B);
     count_launch(ctx);
-    dc_vectors<<<dim3((unsigned)nmax, (unsigned)nmerge), 128, 0, st>>>(B, nmax);
+    dc_vectors<T><<<dim3((unsigned)nmax, (unsigned)nmerge), 128, 0, st>>>(B, nmax);
     count_launch(ctx);
-    dc_gather_kept<<<rows, 128, 0, st>>>(B, nmax);
+    dc_gather_kept<T><<<rows, 128, 0, st>>>(B, nmax);
     count_launch(ctx);
     FL_CUDA(ctx, cudaGetLastError());
-    FL_TRY(gemm_batched(ctx, false, false, B.desc, (int)nmerge, nmax, nmax, st));
-    dc_order<<<(unsigned)nmerge, 32, 0, st>>>(B);
+    FL_TRY(gemm_batched<T>(ctx, false, false, B.desc, (int)nmerge, nmax, nmax, st));
+    dc_order<T><<<(unsigned)nmerge, 32, 0, st>>>(B);
     count_launch(ctx);
-    dc_scatter<<<dim3((unsigned)nmax, (unsigned)nmerge), 128, 0, st>>>(B, lambda, Z, ldz, nmax);
+    dc_scatter<T><<<dim3((unsigned)nmax, (unsigned)nmerge), 128, 0, st>>>(B, lambda, Z, ldz, nmax);
     count_launch(ctx);
     FL_CUDA(ctx, cudaGetLastError());
   }
   return 0;
 }
+
+template size_t stedc_ws<double>(const fraclap_ctx*, int64_t);
+template size_t stedc_ws<float>(const fraclap_ctx*, int64_t);
+template int stedc_run<double>(fraclap_ctx*, const double*, const double*, int64_t, double*, double*, int64_t, Arena*, cudaStream_t);
+template int stedc_run<float>(fraclap_ctx*, const double*, const double*, int64_t, double*, float*, int64_t, Arena*, cudaStream_t);
 
 }  // namespace fraclap

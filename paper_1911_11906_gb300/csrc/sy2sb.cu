@@ -20,11 +20,13 @@ constexpr int PQR_NT = 256;
 // On exit P holds R on and above its diagonal (the band block) and the
 // reflectors below it; Vout gets the explicit unit lower-trapezoidal V
 // (m x bw, ld ldv); tau[bw]; T: bw x bw upper triangular (ld bw).
+template <class T>
 __global__ void __launch_bounds__(PQR_NT)
-panel_qr_kernel(double* P, int64_t ldp, int64_t m, int bw, double* Vout, int64_t ldv,
-                double* tau, double* T, double* partials, double* gram, unsigned* bar,
+panel_qr_kernel(T* P, int64_t ldp, int64_t m, int bw, T* Vout, int64_t ldv,
+                double* tau, T* Tf, double* partials, double* gram, unsigned* bar,
                 long long limit, int32_t* status, int64_t rows_per_cta) {
-  extern __shared__ double S[];  // rows_per_cta x bw, column-major (ld rows_per_cta)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);  // rows_per_cta x bw, column-major (ld rows_per_cta)
   __shared__ double red[2 * 64 + 4];
   __shared__ double sw[64];
   __shared__ double s_coef[4];  // beta, v0, tau
@@ -50,13 +52,13 @@ panel_qr_kernel(double* P, int64_t ldp, int64_t m, int bw, double* Vout, int64_t
       for (int64_t r = r0 + lane; r < nr; r += 32) {
         const int64_t gr = rb + r;
         if (j == c && gr == c) continue;  // g_c is the tail sum of squares (rows > c)
-        s += S[r + c * ld] * S[r + j * ld];
+        s += (double)S[r + c * ld] * (double)S[r + j * ld];
       }
       s = warp_sum(s);
       if (lane == 0) part[j] = s;
     }
     for (int j = c + tid; j < bw; j += PQR_NT)
-      part[bw + j] = (c >= rb && c < re) ? S[(c - rb) + j * ld] : 0.0;
+      part[bw + j] = (c >= rb && c < re) ? (double)S[(c - rb) + j * ld] : 0.0;
     if (!grid_barrier(bar, G, limit, status)) return;
     // every CTA reduces the partials in the same order (identical results)
     for (int t = tid; t < 2 * (bw - c); t += PQR_NT) {
@@ -96,13 +98,15 @@ panel_qr_kernel(double* P, int64_t ldp, int64_t m, int bw, double* Vout, int64_t
       double vr;
       if (gr == c) {
         vr = 1.0;
-        S[r + c * ld] = beta;
+        S[r + c * ld] = (T)beta;
       } else {
-        vr = (tu == 0.0) ? 0.0 : S[r + c * ld] * inv_v0;
-        S[r + c * ld] = vr;
+        vr = (tu == 0.0) ? 0.0 : (double)S[r + c * ld] * inv_v0;
+        S[r + c * ld] = (T)vr;
       }
-      if (tu != 0.0)
-        for (int j = c + 1; j < bw; ++j) S[r + j * ld] -= vr * sw[j];
+      if (tu != 0.0) {
+        const T vt = (T)vr;
+        for (int j = c + 1; j < bw; ++j) S[r + j * ld] -= vt * (T)sw[j];
+      }
     }
     __syncthreads();
   }
@@ -112,10 +116,10 @@ panel_qr_kernel(double* P, int64_t ldp, int64_t m, int bw, double* Vout, int64_t
   for (int c = 0; c < bw; ++c)
     for (int64_t r = tid; r < nr; r += PQR_NT) {
       const int64_t gr = rb + r;
-      const double s = S[r + c * ld];
+      const T s = S[r + c * ld];
       P[gr + c * ldp] = s;
-      double v = 0.0;
-      if (c < nref) v = (gr < c) ? 0.0 : (gr == c ? 1.0 : s);
+      T v = T(0);
+      if (c < nref) v = (gr < c) ? T(0) : (gr == c ? T(1) : s);
       Vout[gr + c * ldv] = v;
     }
   // Gram matrix V^T V (upper part) accumulated over CTAs
@@ -126,8 +130,8 @@ panel_qr_kernel(double* P, int64_t ldp, int64_t m, int bw, double* Vout, int64_t
     for (int64_t r = 0; r < nr; ++r) {
       const int64_t gr = rb + r;
       if (gr < j) continue;
-      const double vi = (gr == i) ? 1.0 : (gr < i ? 0.0 : S[r + i * ld]);
-      const double vj = (gr == j) ? 1.0 : S[r + j * ld];
+      const double vi = (gr == i) ? 1.0 : (gr < i ? 0.0 : (double)S[r + i * ld]);
+      const double vj = (gr == j) ? 1.0 : (double)S[r + j * ld];
       s += vi * vj;
     }
     if (s != 0.0) atomicAdd(&gram[i + j * bw], s);
@@ -151,65 +155,68 @@ panel_qr_kernel(double* P, int64_t ldp, int64_t m, int bw, double* Vout, int64_t
     if (tid == 0) Ts[i + i * bw] = ti;
     __syncthreads();
   }
-  for (int p = tid; p < bw * bw; p += PQR_NT) T[p] = Ts[p];
+  for (int p = tid; p < bw * bw; p += PQR_NT) Tf[p] = (T)Ts[p];
 }
 
 // Band extraction: band(off, j) = A(j + off, j) for off <= b, 0 for b < off < ldb.
-__global__ void extract_band(const double* A, int64_t lda, int64_t n, int b, double* band,
-                             int ldb) {
+template <class T>
+__global__ void extract_band(const T* A, int64_t lda, int64_t n, int b, T* band, int ldb) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n * ldb) return;
   const int off = (int)(p % ldb);
   const int64_t j = p / ldb;
   const int64_t i = j + off;
-  band[p] = (off <= b && i < n) ? A[i + j * lda] : 0.0;
+  band[p] = (off <= b && i < n) ? A[i + j * lda] : T(0);
 }
 
 }  // namespace
 
 int64_t stage1_panels(int64_t n, int b) { return (n > b) ? cdiv(n - b, b) : 0; }
 
-int stage1_take(Arena* ar, int64_t n, int b, int G, Stage1* s) {
+template <class T>
+int stage1_take(Arena* ar, int64_t n, int b, int G, Stage1T<T>* s) {
   s->npanel = stage1_panels(n, b);
   s->vtotal = 0;
   for (int64_t j = 0; j < s->npanel; ++j) s->vtotal += (n - j * b - b) * b;
-  s->Vstore = ar->take<double>(s->vtotal);
-  s->Tstore = ar->take<double>(s->npanel * b * b);
+  s->Vstore = ar->take<T>(s->vtotal);
+  s->Tstore = ar->take<T>(s->npanel * b * b);
   s->tau = ar->take<double>(s->npanel * b);
-  s->XT = ar->take<double>(n * b);
-  s->X = ar->take<double>(n * b);
-  s->Y = ar->take<double>((int64_t)b * b);
-  s->Mm = ar->take<double>((int64_t)b * b);
+  s->XT = ar->take<T>(n * b);
+  s->X = ar->take<T>(n * b);
+  s->Y = ar->take<T>((int64_t)b * b);
+  s->Mm = ar->take<T>((int64_t)b * b);
   s->gram = ar->take<double>((int64_t)b * b);
   s->partials = ar->take<double>(2 * (int64_t)G * 2 * b);
   return 0;
 }
 
-static int panel_grid(fraclap_ctx* ctx, int64_t m, int bw, int64_t* rows_per_cta, size_t* smem) {
+static int panel_grid(fraclap_ctx* ctx, int64_t m, int bw, size_t elem, int64_t* rows_per_cta,
+                      size_t* smem) {
   int G = ctx->sm_count;
   if (m < (int64_t)G * 8) G = (int)cdiv(m, 8);
   if (G < 1) G = 1;
   *rows_per_cta = cdiv(m, G);
   G = (int)cdiv(m, *rows_per_cta);
-  *smem = (size_t)(*rows_per_cta) * bw * sizeof(double);
+  *smem = (size_t)(*rows_per_cta) * bw * elem;
   return G;
 }
 
 // Reduces Aw (n x n, lower triangle valid, overwritten) to band form and
 // writes the band (ld 2b, offsets 0..2b-1, zero beyond b) to `band`.
-int sy2sb_run(fraclap_ctx* ctx, double* Aw, int64_t n, int64_t lda, int b, double* band,
-              Stage1* s, cudaStream_t st) {
+template <class T>
+int sy2sb_run(fraclap_ctx* ctx, T* Aw, int64_t n, int64_t lda, int b, T* band, Stage1T<T>* s,
+              cudaStream_t st) {
   const int ldb = 2 * b;
   int64_t voff = 0;
   for (int64_t p = 0; p < s->npanel; ++p) {
     const int64_t j0 = p * b, m = n - j0 - b;
-    double* P = Aw + (j0 + b) + j0 * lda;
-    double* V = s->Vstore + voff;
-    double* T = s->Tstore + p * b * b;
+    T* P = Aw + (j0 + b) + j0 * lda;
+    T* V = s->Vstore + voff;
+    T* Tf = s->Tstore + p * b * b;
     int64_t rows_per_cta;
     size_t smem;
-    const int G = panel_grid(ctx, m, b, &rows_per_cta, &smem);
-    FL_CHECK(ctx, smem <= 200 * 1024, FRACLAP_ERR_UNSUPPORTED, "sy2sb: panel too tall (%lld)", (long long)m);
+    const int G = panel_grid(ctx, m, b, sizeof(T), &rows_per_cta, &smem);
+    FL_CHECK(ctx, smem <= 180 * 1024, FRACLAP_ERR_UNSUPPORTED, "sy2sb: panel too tall (%lld)", (long long)m);
     FL_CUDA(ctx, cudaMemsetAsync(s->gram, 0, sizeof(double) * b * b, st));
     FL_CUDA(ctx, cudaMemsetAsync(ctx->d_barrier, 0, 2 * sizeof(unsigned), st));
     {
@@ -221,35 +228,29 @@ int sy2sb_run(fraclap_ctx* ctx, double* Aw, int64_t n, int64_t lda, int b, doubl
       unsigned* bar = ctx->d_barrier;
       long long limit = ctx->wait_cycles;
       int32_t* status = ctx->d_status;
-      void* args[] = {&P, &ldp, &mm, &bw, &V, &ldv, &tau, &T, &partials, &gram, &bar, &limit, &status, &rows_per_cta};
-      FL_CUDA(ctx, cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      void* args[] = {&P, &ldp, &mm, &bw, &V, &ldv, &tau, &Tf, &partials, &gram, &bar, &limit, &status, &rows_per_cta};
+      FL_CUDA(ctx, cudaFuncSetAttribute(panel_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       count_launch(ctx);
-      FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(PQR_NT), args, smem, st));
+      FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)panel_qr_kernel<T>, dim3(G), dim3(PQR_NT), args, smem, st));
     }
-    double* A22 = Aw + (j0 + b) + (j0 + b) * lda;
-    GemmDesc d{};
+    T* A22 = Aw + (j0 + b) + (j0 + b) * lda;
+    using D = GemmDescT<T>;
     // XT = V T  (m x b)
-    d = GemmDesc{m, b, b, V, m, T, b, s->XT, m, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
-    FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+    FL_TRY(gemm<T>(ctx, false, false, kGemmPlain, D{m, b, b, V, m, Tf, b, s->XT, m, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
     // X = A22 XT (A22 symmetric, lower triangle)
-    d = GemmDesc{m, b, m, A22, lda, s->XT, m, s->X, m, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
-    FL_TRY(gemm(ctx, false, false, kGemmSymA, d, 1, st));
+    FL_TRY(gemm<T>(ctx, false, false, kGemmSymA, D{m, b, m, A22, lda, s->XT, m, s->X, m, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
     // Y = V^T X  (b x b), split over the long dimension
-    FL_CUDA(ctx, cudaMemsetAsync(s->Y, 0, sizeof(double) * b * b, st));
-    d = GemmDesc{b, b, m, V, m, s->X, m, s->Y, b, nullptr, 0, nullptr, 0, 0, 1.0, 1.0};
-    FL_TRY(gemm(ctx, true, false, kGemmPlain, d, (int)cdiv(m, 256), st));
+    FL_CUDA(ctx, cudaMemsetAsync(s->Y, 0, sizeof(T) * b * b, st));
+    FL_TRY(gemm<T>(ctx, true, false, kGemmPlain, D{b, b, m, V, m, s->X, m, s->Y, b, nullptr, 0, nullptr, 0, 0, 1.0, 1.0}, (int)cdiv(m, 256), st));
     // Mm = T^T Y
-    d = GemmDesc{b, b, b, T, b, s->Y, b, s->Mm, b, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
-    FL_TRY(gemm(ctx, true, false, kGemmPlain, d, 1, st));
+    FL_TRY(gemm<T>(ctx, true, false, kGemmPlain, D{b, b, b, Tf, b, s->Y, b, s->Mm, b, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
     // W = X - 1/2 V Mm  (in X)
-    d = GemmDesc{m, b, b, V, m, s->Mm, b, s->X, m, nullptr, 0, nullptr, 0, 0, -0.5, 1.0};
-    FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+    FL_TRY(gemm<T>(ctx, false, false, kGemmPlain, D{m, b, b, V, m, s->Mm, b, s->X, m, nullptr, 0, nullptr, 0, 0, -0.5, 1.0}, 1, st));
     // A22 -= W V^T + V W^T  (lower triangle)
-    d = GemmDesc{m, m, b, s->X, m, V, m, A22, lda, V, m, s->X, m, b, -1.0, 1.0};
-    FL_TRY(gemm(ctx, false, true, kGemmLowerC, d, 1, st));
+    FL_TRY(gemm<T>(ctx, false, true, kGemmLowerC, D{m, m, b, s->X, m, V, m, A22, lda, V, m, s->X, m, b, -1.0, 1.0}, 1, st));
     voff += m * b;
   }
-  extract_band<<<(unsigned)cdiv(n * ldb, 256), 256, 0, st>>>(Aw, lda, n, b, band, ldb);
+  extract_band<T><<<(unsigned)cdiv(n * ldb, 256), 256, 0, st>>>(Aw, lda, n, b, band, ldb);
   count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   return 0;
@@ -257,27 +258,32 @@ int sy2sb_run(fraclap_ctx* ctx, double* Aw, int64_t n, int64_t lda, int b, doubl
 
 // Back-transformation by Q1 = Q_0 Q_1 ... Q_{p-1}: Z <- Q1 Z (n x ncols).
 // Applied from the last panel to the first: Z(rows_j, :) -= V_j (T_j (V_j^T Z(rows_j, :))).
-int q1_apply_run(fraclap_ctx* ctx, const Stage1* s, int64_t n, int b, double* Z, int64_t ldz,
-                 int64_t ncols, double* W1, double* W2, cudaStream_t st) {
+template <class T>
+int q1_apply_run(fraclap_ctx* ctx, const Stage1T<T>* s, int64_t n, int b, T* Z, int64_t ldz,
+                 int64_t ncols, T* W1, T* W2, cudaStream_t st) {
   int64_t voff = s->vtotal;
+  using D = GemmDescT<T>;
   for (int64_t p = s->npanel - 1; p >= 0; --p) {
     const int64_t j0 = p * b, m = n - j0 - b;
     voff -= m * b;
-    const double* V = s->Vstore + voff;
-    const double* T = s->Tstore + p * b * b;
-    double* Zr = Z + (j0 + b);
-    GemmDesc d{};
+    const T* V = s->Vstore + voff;
+    const T* Tf = s->Tstore + p * b * b;
+    T* Zr = Z + (j0 + b);
     // W1 = V^T Zr  (b x ncols)
-    d = GemmDesc{b, ncols, m, V, m, Zr, ldz, W1, b, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
-    FL_TRY(gemm(ctx, true, false, kGemmPlain, d, 1, st));
+    FL_TRY(gemm<T>(ctx, true, false, kGemmPlain, D{b, ncols, m, V, m, Zr, ldz, W1, b, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
     // W2 = T W1
-    d = GemmDesc{b, ncols, b, T, b, W1, b, W2, b, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
-    FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+    FL_TRY(gemm<T>(ctx, false, false, kGemmPlain, D{b, ncols, b, Tf, b, W1, b, W2, b, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
     // Zr -= V W2
-    d = GemmDesc{m, ncols, b, V, m, W2, b, Zr, ldz, nullptr, 0, nullptr, 0, 0, -1.0, 1.0};
-    FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+    FL_TRY(gemm<T>(ctx, false, false, kGemmPlain, D{m, ncols, b, V, m, W2, b, Zr, ldz, nullptr, 0, nullptr, 0, 0, -1.0, 1.0}, 1, st));
   }
   return 0;
 }
+
+template int stage1_take<double>(Arena*, int64_t, int, int, Stage1T<double>*);
+template int stage1_take<float>(Arena*, int64_t, int, int, Stage1T<float>*);
+template int sy2sb_run<double>(fraclap_ctx*, double*, int64_t, int64_t, int, double*, Stage1T<double>*, cudaStream_t);
+template int sy2sb_run<float>(fraclap_ctx*, float*, int64_t, int64_t, int, float*, Stage1T<float>*, cudaStream_t);
+template int q1_apply_run<double>(fraclap_ctx*, const Stage1T<double>*, int64_t, int, double*, int64_t, int64_t, double*, double*, cudaStream_t);
+template int q1_apply_run<float>(fraclap_ctx*, const Stage1T<float>*, int64_t, int, float*, int64_t, int64_t, float*, float*, cudaStream_t);
 
 }  // namespace fraclap

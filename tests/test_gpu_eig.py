@@ -120,3 +120,44 @@ def test_eig_full_masked_vs_oracle(seed, b):
     U = O.frac_apply(V, lam, p.F, p.pair_f, p.pair_alpha)
     err = max(np.linalg.norm(U[:, j] - U_o[:, j]) / np.linalg.norm(U_o[:, j]) for j in range(U.shape[1]))
     assert err <= 1e-10
+
+
+def _csr_cuda(A):
+    return (torch.from_numpy(A.rowptr).cuda(), torch.from_numpy(A.col).cuda(), torch.from_numpy(A.val).cuda())
+
+
+@pytest.mark.parametrize("which,b,iters", [("square23", 32, 2), ("ellipse36", 32, 2), ("ellipse36", 64, 3),
+                                            ("ellipse64", 32, 3), ("ellipse48", 16, 2), ("square9", 8, 2),
+                                            ("cube6", 32, 2)])
+def test_eig_full_mixed_refined_vs_oracle(which, b, iters):
+    """FP32 stages + Ogita-Aishima refinement reach the FP64 tolerances."""
+    F = _F()
+    if which.startswith("square"):
+        p = I.square_problem(int(which[6:]))
+    elif which.startswith("cube"):
+        m = int(which[4:])
+        p = I.holed_cube_problem(m, n_holes=0, n_forcings=3)
+    else:
+        p = I.ellipse_problem(int(which[7:]), seed=17)
+    _, A = O.assemble(p.mask, p.h)
+    D = A.dense()
+    lam_o, V_o = O.eig_full(D)
+    lam, V = F.eig_full_mixed(_colmajor(D), *_csr_cuda(A), refine_iters=iters, ctx=F.Context(band_width=b))
+    lam, V = lam.cpu().numpy(), V.cpu().numpy()
+    _check_decomposition(D, lam_o, lam, V)
+    U_o = O.frac_apply(V_o, lam_o, p.F, p.pair_f, p.pair_alpha)
+    U = O.frac_apply(V, lam, p.F, p.pair_f, p.pair_alpha)
+    err = max(np.linalg.norm(U[:, j] - U_o[:, j]) / np.linalg.norm(U_o[:, j]) for j in range(U.shape[1]))
+    assert err <= 1e-10
+
+
+def test_eig_full_mixed_without_refinement_is_fp32_accurate():
+    F = _F()
+    p = I.ellipse_problem(30, seed=3)
+    _, A = O.assemble(p.mask, p.h)
+    D = A.dense()
+    lam_o, _ = O.eig_full(D)
+    lam, V = F.eig_full_mixed(_colmajor(D), *_csr_cuda(A), refine_iters=0)
+    lam, V = lam.cpu().numpy(), V.cpu().numpy()
+    assert np.max(np.abs(lam - lam_o)) <= 1e-4 * lam_o[-1]
+    assert np.max(np.abs(V.T @ V - np.eye(A.n))) <= 1e-4
