@@ -117,9 +117,12 @@ int eig_full(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_t lda,
  * the secular equations and the deflation stay FP64.  FP64 accuracy is then
  * regained by `refine_iters` iterations of Ogita-Aishima refinement
  * (R = I - V^T V and S = V^T A V in FP64 with A applied through its CSR
- * form; clusters of close eigenvalues are diagonalised exactly).  One
- * iteration reaches the eig_full tolerances on the stencil matrices; two are
- * the default recommendation.
+ * form, products on the tensor cores by error-free BF16 splitting; clusters
+ * of close eigenvalues, and pairs whose first-order correction would be
+ * large, are diagonalised exactly).  refine_iters is the maximum number of
+ * iterations; the loop stops after the first iteration that starts with
+ * ||I - V^T V||_2 and ||V^T A V - D||_2 / ||A||_2 below 1e-13.  FP32-accurate
+ * starting vectors at n ~ 10^4 take three or four.
  *
  *  A_dev      double[lda*n] dense, lower triangle read (the FP32 stages).
  *  rowptr_dev, col_dev, val_dev: the same matrix in CSR (from fd_assemble).
@@ -239,6 +242,18 @@ int fraclap_stage_times(fraclap_ctx* ctx, double* ms_out, int64_t* count_out, in
 int fraclap_refine_stats(const fraclap_ctx* ctx, double* out, int max_values);
 /* Number of kernels the context has launched so far. */
 long long fraclap_launch_count(const fraclap_ctx* ctx);
+
+/* C = alpha op(A) op(B) + beta C with FP64-accurate products formed on the
+ * BF16 tensor cores by Ozaki's error-free splitting into `slices` 8-bit slices
+ * per row/column (7 slices: full FP64 accuracy; fewer: about 8*slices bits
+ * relative to the row and column maxima).  The engine behind the
+ * refinement's residual products.  work: fraclap_dgemm_ozaki_workspace_bytes. */
+size_t fraclap_dgemm_ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices);
+int fraclap_dgemm_ozaki(fraclap_ctx* ctx, int trans_a, int trans_b, int64_t m, int64_t n,
+                        int64_t k, double alpha, const double* A_dev, int64_t lda,
+                        const double* B_dev, int64_t ldb, double beta, double* C_dev,
+                        int64_t ldc, int slices, void* work_dev, size_t work_bytes,
+                        fraclap_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -37,6 +37,9 @@ SIGNATURES = {
     "fraclap_stage_times": (_i32, [_p, _p, _p, _i32]),
     "fraclap_launch_count": (ctypes.c_longlong, [_p]),
     "fraclap_refine_stats": (_i32, [_p, _p, _i32]),
+    "fraclap_dgemm_ozaki_workspace_bytes": (_sz, [_i64, _i64, _i64, _i32]),
+    "fraclap_dgemm_ozaki": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64,
+                                   _i32, _p, _sz, _p]),
     "fraclap_dgemm": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64, _p]),
 }
 
@@ -312,6 +315,29 @@ def dgemm(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, alpha=
     st = ctypes.c_void_p(_stream(stream))
     ctx.check(ctx.lib.fraclap_dgemm(ctx.handle, int(trans_a), int(trans_b), m, n, k, float(alpha), _ptr(A),
                                     _ld(A), _ptr(B), _ld(B), float(beta), _ptr(C), _ld(C), st))
+    ctx.sync(stream)
+    return C
+
+
+def dgemm_ozaki(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, alpha=1.0, beta=0.0,
+                C: torch.Tensor | None = None, slices: int = 7, ctx: Context | None = None,
+                stream=None) -> torch.Tensor:
+    """C = alpha op(A) op(B) + beta C, FP64-accurate from BF16 tensor-core slices."""
+    ctx = ctx or default_context()
+    A = _f64_colmajor(A, "A")
+    B = _f64_colmajor(B, "B")
+    m = A.shape[1] if trans_a else A.shape[0]
+    k = A.shape[0] if trans_a else A.shape[1]
+    n = B.shape[0] if trans_b else B.shape[1]
+    if C is None:
+        C = empty_colmajor(m, n, A.device)
+        beta = 0.0
+    nbytes = ctx.lib.fraclap_dgemm_ozaki_workspace_bytes(m, n, k, slices)
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=A.device)
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.fraclap_dgemm_ozaki(ctx.handle, int(trans_a), int(trans_b), m, n, k, float(alpha), _ptr(A),
+                                          _ld(A), _ptr(B), _ld(B), float(beta), _ptr(C), _ld(C), int(slices),
+                                          _ptr(ws), ws.numel(), st))
     ctx.sync(stream)
     return C
 

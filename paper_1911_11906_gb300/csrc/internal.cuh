@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -223,6 +224,12 @@ int stedc_run(fraclap_ctx* ctx, const double* d, const double* e, int64_t n, dou
 size_t cluster_eig_ws(const fraclap_ctx* ctx, int64_t c);
 int cluster_eig(fraclap_ctx* ctx, double* S, int64_t c, double* w, double* Q, Arena* ar,
                 cudaStream_t st);
+
+// FP64-accurate GEMM through BF16 tensor-core slices (ozaki.cu).
+size_t ozaki_ws(int64_t M, int64_t N, int64_t K, int s);
+int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+               const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+               int64_t ldc, int s, bool lower, Arena* ar, cudaStream_t st);
 
 // Ogita-Aishima refinement of (X, lambda) against the CSR matrix A.
 size_t refine_ws(const fraclap_ctx* ctx, int64_t n);

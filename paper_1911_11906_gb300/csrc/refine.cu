@@ -274,6 +274,11 @@ __global__ void copy_columns(const double* Xs, int64_t n, double* X, int64_t ldx
 // In: Sc (ld c).  Out: Q (ld c, eigenvectors in columns), w (eigenvalues),
 // both ascending.
 constexpr int kMaxCluster = 64;
+// Stop after the iteration that starts with ||R||_2 and ||S - D||_2 / ||A||_2 below this
+// (its quadratic step lands at rounding level).
+constexpr double kConvergedR = 1e-9;
+// BF16 slices per operand in the refinement's residual products (7: FP64).
+constexpr int kRefineSlices = 7;
 // A pair whose first-order coefficient exceeds this is diagonalised exactly
 // inside a cluster instead (its second-order error would not be small).
 constexpr double kUnsafeTau = 1e-2;
@@ -391,8 +396,8 @@ __global__ void rayleigh(const double* X, int64_t ldx, const double* AX, int64_t
 }  // namespace
 
 // Largest cluster the refinement diagonalises (clusters above 64 go through
-// the FP64 dense eigensolver of this library).
-constexpr int64_t kMaxBigCluster = 2048;
+// the FP64 dense eigensolver of this library; its workspace is sized for n).
+constexpr int64_t kMaxBigCluster = 65535;
 
 size_t refine_ws(const fraclap_ctx* ctx, int64_t n) {
   Arena ar;
@@ -411,7 +416,7 @@ size_t refine_ws(const fraclap_ctx* ctx, int64_t n) {
   ar.take<double>(8);          // norms, delta
   const int64_t cmax = std::min<int64_t>(n, kMaxBigCluster);
   ar.take<double>(n * cmax * 2 + 2 * cmax * cmax + cmax);
-  return ar.off + cluster_eig_ws(ctx, cmax);
+  return ar.off + std::max(cluster_eig_ws(ctx, cmax), ozaki_ws(n, n, n, kRefineSlices));
 }
 
 int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col,
@@ -441,15 +446,23 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
   double* delta = scal + 3;
   using D64 = GemmDescT<double>;
   using D32 = GemmDescT<float>;
-  for (int it = 0; it < iters; ++it) {
+  bool converged = false;
+  for (int it = 0; it < iters && !converged; ++it) {
     // AX = A X
     spmm_csr<<<dim3(rows, (unsigned)std::min<int64_t>(n, 4096)), 128, 0, st>>>(n, rowptr, col, val, X, ldx, n, AX, n);
     count_launch(ctx);
-    // R = I - X^T X, S = X^T (A X): lower triangles, FP64
-    FL_TRY(gemm<double>(ctx, true, false, kGemmLowerC, D64{n, n, n, X, ldx, X, ldx, R, n, nullptr, 0, nullptr, 0, 0, -1.0, 0.0}, 1, st));
+    // R = I - X^T X, S = X^T (A X): lower triangles, FP64-accurate products
+    // from BF16 tensor-core slices (the slices live in the scratch arena)
+    {
+      Arena oz = *ar;
+      FL_TRY(ozaki_gemm(ctx, true, false, n, n, n, -1.0, X, ldx, X, ldx, 0.0, R, n, kRefineSlices, true, &oz, st));
+    }
     add_identity<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(R, n, n);
     count_launch(ctx);
-    FL_TRY(gemm<double>(ctx, true, false, kGemmLowerC, D64{n, n, n, X, ldx, AX, n, S, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
+    {
+      Arena oz = *ar;
+      FL_TRY(ozaki_gemm(ctx, true, false, n, n, n, 1.0, X, ldx, AX, n, 0.0, S, n, kRefineSlices, true, &oz, st));
+    }
     ritz_values<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(S, n, R, n, n, lt);
     count_launch(ctx);
     FL_CUDA(ctx, cudaMemsetAsync(scal, 0, 8 * sizeof(double), st));
@@ -514,6 +527,9 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
       for (int q = 0; q < ncl; ++q) cmaxseen = std::max(cmaxseen, cl[2 * q + 1]);
       const double row[8] = {hs[3], hs[4], hs[5], sqrt(hs[0]), sqrt(hs[1]), na, (double)ncl, (double)cmaxseen};
       ctx->refine_stats.insert(ctx->refine_stats.end(), row, row + 8);
+      // converged: this iteration started orthonormal to ~1e-14, so after its
+      // update the residuals are at rounding level
+      converged = (hs[5] <= kConvergedR) && (hs[4] <= kConvergedR * na);
     }
     if (ncl > 0) {
       double* AXc = cbuf;                        // n x c

@@ -8,10 +8,13 @@
 // column of the previous window in rows s+1+kb..s+(k+1)b and pushes the
 // bulge one window further.  Only that first column is annihilated; the rest
 // of the fill stays within 2b-1 diagonals of storage and is absorbed by the
-// later sweeps.  Step k of sweep s touches indices
-// [s+1+(k-1)b, s+(k+2)b], so it may run as soon as sweep s-1 has finished
-// its step k+3: sweeps run in a pipeline, one CTA per sweep in flight, each
-// CTA waiting (bounded in time) on a progress counter of its predecessor.
+// later sweeps.  Step k of sweep s touches only entries in rows
+// [s+1+kb, s+(k+2)b]; step k' of sweep s-1 touches rows from s+k'b on, so
+// the two are disjoint once k' >= k+3 (at k' = k+2 they share the entry
+// (s+(k+2)b, s+(k+1)b)).  Sweep s may therefore run step k as soon as sweep
+// s-1 has finished its step k+2: sweeps run in a pipeline, one CTA per sweep
+// in flight, each CTA waiting (bounded in time) on a progress counter of its
+// predecessor.
 //
 // The reflectors H(s,k) of one sweep act on disjoint rows; H(s,k) and
 // H(s',k') with k > k', s > s' or k < k', s < s' act on disjoint rows as
@@ -55,6 +58,7 @@ __global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs<T> a) {
   T* E = D + 64 * 64;         // b x b  (E[t + u*b])
   T* pw = E + 64 * 64;        // b
   T* wq = pw + 64;            // b
+  T* ey = wq + 64;            // b
   __shared__ double s_coef[4];
   __shared__ int s_abort;
   const int tid = threadIdx.x;
@@ -65,11 +69,11 @@ __global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs<T> a) {
     const int64_t ns = sb_nsteps(s, n, b);
     const int64_t ns_prev = (s > 0) ? sb_nsteps(s - 1, n, b) : 0;
     for (int64_t k = 0; k < ns; ++k) {
-      // ---- wait for sweep s-1 to have completed step k+3 ----
+      // ---- wait for sweep s-1 to have completed step k+2 ----
       if (tid == 0) {
         int ok = 1;
         if (s > 0) {
-          const int64_t need = (k + 4 < ns_prev) ? k + 4 : ns_prev;
+          const int64_t need = (k + 3 < ns_prev) ? k + 3 : ns_prev;
           const long long t0 = clock64();
           while (ld_acquire_gpu(a.progress + (s - 1)) < need) {
             if (*(volatile int32_t*)a.status != 0) { ok = 0; break; }
@@ -143,37 +147,52 @@ __global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs<T> a) {
       for (int t = tid; t < b; t += SB_NT) rv[t] = (t < L) ? xv[t] : T(0);
       if (tid == 0) a.rtau[s * a.kmax + k] = tu;
       if (tu != 0.0) {
-        // ---- F <- H F, E <- E H, p = tau D v ----
-        for (int q = tid; q < nf; q += SB_NT) {
-          T w = T(0);
-          for (int t = 0; t < L; ++t) w += xv[t] * F[t + q * b];
-          wq[q] = tuT * w;
-        }
-        for (int t = tid; t < L; t += SB_NT) {
-          T p = T(0);
-          for (int u = 0; u < L; ++u) p += D[t + u * b] * xv[u];
-          pw[t] = tuT * p;
+        // ---- wq = tau F^T v, pw = tau D v, y = tau E v: 4 threads per dot ----
+        {
+          const int part = tid & 3;
+          const int ntask = nf + L + Lb;
+          // warp-uniform trip count: every lane reaches the shuffles
+          for (int base = 0; base < ntask; base += SB_NT / 4) {
+            const int task = base + (tid >> 2);
+            T acc = T(0);
+            if (task >= ntask) {
+            } else if (task < nf) {
+              const T* col = F + task * b;
+              for (int t = part; t < L; t += 4) acc += xv[t] * col[t];
+            } else if (task < nf + L) {
+              const int t = task - nf;
+              for (int u = part; u < L; u += 4) acc += D[t + u * b] * xv[u];
+            } else {
+              const int t = task - nf - L;
+              for (int u = part; u < L; u += 4) acc += E[t + u * b] * xv[u];
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (part == 0 && task < ntask) {
+              if (task < nf) wq[task] = tuT * acc;
+              else if (task < nf + L) pw[task - nf] = tuT * acc;
+              else ey[task - nf - L] = tuT * acc;
+            }
+          }
         }
         __syncthreads();
         for (int p = tid; p < L * nf; p += SB_NT) {
           const int t = p % L, q = p / L;
           F[t + q * b] -= xv[t] * wq[q];
         }
-        if (tid == 0) {
+        for (int p = tid; p < Lb * L; p += SB_NT) {
+          const int t = p % Lb, u = p / Lb;
+          E[t + u * b] -= ey[t] * xv[u];
+        }
+        if (tid < 32) {  // K = tau/2 p^T v
           double pv = 0.0;
-          for (int t = 0; t < L; ++t) pv += (double)pw[t] * (double)xv[t];
-          s_coef[3] = 0.5 * tu * pv;
+          for (int t = tid; t < L; t += 32) pv += (double)pw[t] * (double)xv[t];
+          pv = warp_sum(pv);
+          if (tid == 0) s_coef[3] = 0.5 * tu * pv;
         }
         __syncthreads();
         const T K = (T)s_coef[3];
         for (int t = tid; t < L; t += SB_NT) pw[t] -= K * xv[t];  // w = p - K v
-        // E <- E H : y_t = tau E(t,:) v
-        for (int t = tid; t < Lb; t += SB_NT) {
-          T y = T(0);
-          for (int u = 0; u < L; ++u) y += E[t + u * b] * xv[u];
-          y *= tuT;
-          for (int u = 0; u < L; ++u) E[t + u * b] -= y * xv[u];
-        }
         __syncthreads();
         for (int p = tid; p < L * L; p += SB_NT) {
           const int t = p % L, u = p / L;
@@ -378,7 +397,7 @@ int sb2st_run(fraclap_ctx* ctx, T* band, int64_t n, int b, double* d, double* e,
     FL_CUDA(ctx, cudaMemsetAsync(s->progress, 0, sizeof(int) * (n + 1), st));
     FL_CUDA(ctx, cudaMemsetAsync(s->rtau, 0, sizeof(double) * (n - 1) * s->kmax, st));
     SbArgs<T> a{band, n, b, s->kmax, s->refl, s->rtau, s->progress, ctx->d_status, ctx->wait_cycles};
-    const size_t smem = sizeof(T) * (64 + 3 * 64 * 64 + 2 * 64);
+    const size_t smem = sizeof(T) * (64 + 3 * 64 * 64 + 3 * 64);
     FL_CUDA(ctx, cudaFuncSetAttribute(sb2st_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     FL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sb2st_kernel<T>, SB_NT, smem));

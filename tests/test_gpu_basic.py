@@ -113,3 +113,39 @@ def test_frac_apply_edge_cases(square_small):
     assert ei.value.code == -2
     # ... but alpha = 0 never evaluates the power
     F.frac_apply(Vd, _cuda(bad), _colmajor(p.F), [0], [0.0])
+
+
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (63, 65, 17), (130, 70, 300), (257, 33, 1000)])
+def test_dgemm_ozaki_is_fp64_accurate(ta, tb, m, n, k):
+    """BF16-slice products reach FP64 accuracy (7 slices) against an exact
+    reference computed with error-free accumulation (math.fsum)."""
+    import math
+    F = _F()
+    rng = np.random.default_rng(m + 7 * n + 13 * k)
+    A = rng.standard_normal((k, m) if ta else (m, k)) * np.exp(rng.uniform(-8, 8, size=(k, m) if ta else (m, k)))
+    B = rng.standard_normal((n, k) if tb else (k, n))
+    opA, opB = (A.T if ta else A), (B.T if tb else B)
+    C0 = rng.standard_normal((m, n))
+    C = _colmajor(C0)
+    F.dgemm_ozaki(_colmajor(A), _colmajor(B), trans_a=ta, trans_b=tb, alpha=0.5, beta=-2.0, C=C)
+    got = C.cpu().numpy()
+    for (i, j) in [(0, 0), (m - 1, n - 1), (m // 2, n // 3)]:
+        exact = 0.5 * math.fsum(opA[i, :] * opB[:, j]) - 2.0 * C0[i, j]
+        scale = 0.5 * np.abs(opA[i, :]).max() * np.abs(opB[:, j]).max() * k + 2 * abs(C0[i, j])
+        assert abs(got[i, j] - exact) <= 4e-16 * scale
+    ref = 0.5 * opA @ opB - 2.0 * C0
+    rowmax = np.abs(opA).max(axis=1)[:, None] * np.abs(opB).max(axis=0)[None, :] * k
+    assert np.max(np.abs(got - ref) / (rowmax + 1e-300)) <= 1e-15
+
+
+def test_dgemm_ozaki_fewer_slices_bound():
+    F = _F()
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((200, 300))
+    B = rng.standard_normal((300, 150))
+    ref = A @ B
+    for s in (3, 5):
+        got = F.dgemm_ozaki(_colmajor(A), _colmajor(B), slices=s).cpu().numpy()
+        scale = np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * 300
+        assert np.max(np.abs(got - ref) / scale) <= 2.0 ** (-8 * s + 4)

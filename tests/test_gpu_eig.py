@@ -126,9 +126,9 @@ def _csr_cuda(A):
     return (torch.from_numpy(A.rowptr).cuda(), torch.from_numpy(A.col).cuda(), torch.from_numpy(A.val).cuda())
 
 
-@pytest.mark.parametrize("which,b,iters", [("square23", 32, 2), ("ellipse36", 32, 2), ("ellipse36", 64, 3),
-                                            ("ellipse64", 32, 3), ("ellipse48", 16, 2), ("square9", 8, 2),
-                                            ("cube6", 32, 2)])
+@pytest.mark.parametrize("which,b,iters", [("square23", 32, 6), ("ellipse36", 32, 6), ("ellipse36", 64, 6),
+                                            ("ellipse64", 32, 6), ("ellipse48", 16, 6), ("square9", 8, 6),
+                                            ("cube6", 32, 6)])
 def test_eig_full_mixed_refined_vs_oracle(which, b, iters):
     """FP32 stages + Ogita-Aishima refinement reach the FP64 tolerances."""
     F = _F()
@@ -142,9 +142,13 @@ def test_eig_full_mixed_refined_vs_oracle(which, b, iters):
     _, A = O.assemble(p.mask, p.h)
     D = A.dense()
     lam_o, V_o = O.eig_full(D)
-    lam, V = F.eig_full_mixed(_colmajor(D), *_csr_cuda(A), refine_iters=iters, ctx=F.Context(band_width=b))
+    ctx = F.Context(band_width=b)
+    lam, V = F.eig_full_mixed(_colmajor(D), *_csr_cuda(A), refine_iters=iters, ctx=ctx)
     lam, V = lam.cpu().numpy(), V.cpu().numpy()
     _check_decomposition(D, lam_o, lam, V)
+    stats = ctx.refine_stats()
+    assert 1 <= len(stats) <= iters
+    assert stats[-1]["norm2_R"] <= 1e-13 or len(stats) == iters
     U_o = O.frac_apply(V_o, lam_o, p.F, p.pair_f, p.pair_alpha)
     U = O.frac_apply(V, lam, p.F, p.pair_f, p.pair_alpha)
     err = max(np.linalg.norm(U[:, j] - U_o[:, j]) / np.linalg.norm(U_o[:, j]) for j in range(U.shape[1]))
