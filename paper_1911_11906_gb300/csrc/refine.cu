@@ -527,8 +527,8 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
       for (int q = 0; q < ncl; ++q) cmaxseen = std::max(cmaxseen, cl[2 * q + 1]);
       const double row[8] = {hs[3], hs[4], hs[5], sqrt(hs[0]), sqrt(hs[1]), na, (double)ncl, (double)cmaxseen};
       ctx->refine_stats.insert(ctx->refine_stats.end(), row, row + 8);
-      // converged: this iteration started orthonormal to ~1e-14, so after its
-      // update the residuals are at rounding level
+      // converged: this iteration started with small residuals, so its
+      // quadratic step leaves them at rounding level
       converged = (hs[5] <= kConvergedR) && (hs[4] <= kConvergedR * na);
     }
     if (ncl > 0) {
