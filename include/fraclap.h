@@ -227,7 +227,8 @@ enum {
   FRACLAP_STAGE_BACK_Q1 = 5,        /* back-transformation by the panel reflectors */
   FRACLAP_STAGE_APPLY = 6,          /* frac_apply */
   FRACLAP_STAGE_REFINE = 7,         /* Ogita-Aishima refinement (eig_full_mixed) */
-  FRACLAP_STAGE_COUNT = 8
+  FRACLAP_STAGE_RESIDUAL_GEMM = 8,  /* its tensor-core residual products (inside REFINE) */
+  FRACLAP_STAGE_COUNT = 9
 };
 /* With enable != 0, every later stage records a CUDA event pair on its stream. */
 int fraclap_set_profiling(fraclap_ctx* ctx, int enable);

@@ -114,7 +114,7 @@ class Context:
             raise FraclapError(rc, msg)
 
     STAGES = ("assemble", "band_reduction", "bulge_chasing", "tridiag_dc", "back_q2", "back_q1", "apply",
-              "refine")
+              "refine", "residual_gemm")
 
     def set_profiling(self, enable: bool = True):
         self.check(self.lib.fraclap_set_profiling(self.handle, int(enable)))

@@ -70,7 +70,8 @@ enum Stage : int {
   kStageBackQ1 = 5,
   kStageApply = 6,
   kStageRefine = 7,
-  kStageCount = 8
+  kStageResidualGemm = 8,
+  kStageCount = 9
 };
 
 // Records CUDA events around a stage on `st` when profiling is on.

@@ -454,12 +454,14 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
     // R = I - X^T X, S = X^T (A X): lower triangles, FP64-accurate products
     // from BF16 tensor-core slices (the slices live in the scratch arena)
     {
+      StageTimer tm(ctx, kStageResidualGemm, st);
       Arena oz = *ar;
       FL_TRY(ozaki_gemm(ctx, true, false, n, n, n, -1.0, X, ldx, X, ldx, 0.0, R, n, kRefineSlices, true, &oz, st));
     }
     add_identity<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(R, n, n);
     count_launch(ctx);
     {
+      StageTimer tm(ctx, kStageResidualGemm, st);
       Arena oz = *ar;
       FL_TRY(ozaki_gemm(ctx, true, false, n, n, n, 1.0, X, ldx, AX, n, 0.0, S, n, kRefineSlices, true, &oz, st));
     }
