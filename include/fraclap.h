@@ -244,6 +244,11 @@ int fraclap_refine_stats(const fraclap_ctx* ctx, double* out, int max_values);
 /* Number of kernels the context has launched so far. */
 long long fraclap_launch_count(const fraclap_ctx* ctx);
 
+/* Tensor-core route of the BF16 slice products: 1 (default) = tcgen05.mma
+ * with TMA-loaded operands and tensor-memory accumulators; 0 = mma.sync
+ * (kept to cross-check the first). */
+int fraclap_set_tensor_route(fraclap_ctx* ctx, int route);
+
 /* C = alpha op(A) op(B) + beta C with FP64-accurate products formed on the
  * BF16 tensor cores by Ozaki's error-free splitting into `slices` 8-bit slices
  * per row/column (7 slices: full FP64 accuracy; fewer: about 8*slices bits

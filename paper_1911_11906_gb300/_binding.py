@@ -37,6 +37,7 @@ SIGNATURES = {
     "fraclap_stage_times": (_i32, [_p, _p, _p, _i32]),
     "fraclap_launch_count": (ctypes.c_longlong, [_p]),
     "fraclap_refine_stats": (_i32, [_p, _p, _i32]),
+    "fraclap_set_tensor_route": (_i32, [_p, _i32]),
     "fraclap_dgemm_ozaki_workspace_bytes": (_sz, [_i64, _i64, _i64, _i32]),
     "fraclap_dgemm_ozaki": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64,
                                    _i32, _p, _sz, _p]),
@@ -136,6 +137,10 @@ class Context:
         nv = self.lib.fraclap_refine_stats(self.handle, buf, 512)
         f = self.REFINE_FIELDS
         return [dict(zip(f, buf[i:i + len(f)])) for i in range(0, min(nv, 512), len(f))]
+
+    def set_tensor_route(self, route: int):
+        """1: tcgen05 + TMA slice products (default); 0: mma.sync."""
+        self.check(self.lib.fraclap_set_tensor_route(self.handle, int(route)))
 
     def launch_count(self) -> int:
         return int(self.lib.fraclap_launch_count(self.handle))

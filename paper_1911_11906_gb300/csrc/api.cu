@@ -427,3 +427,9 @@ extern "C" int fraclap_refine_stats(const fraclap_ctx* ctx, double* out, int max
   for (int i = 0; i < nv && i < max_values; ++i) out[i] = ctx->refine_stats[i];
   return nv;
 }
+
+extern "C" int fraclap_set_tensor_route(fraclap_ctx* ctx, int route) {
+  if (!ctx || (route != 0 && route != 1)) return FRACLAP_ERR_INVALID_ARG;
+  ctx->tensor_route = route;
+  return 0;
+}

@@ -14,8 +14,16 @@
 // are below 2^-8s relative to |row max| |column max| per term.  The result
 // C = alpha 2^(e_i + f_j) sum + beta C is formed in FP64.
 //
-// The tensor-core step is mma.sync m16n8k16 (BF16 in, FP32 accumulate).
+// Two tensor-core kernels compute the slice products: the sm_103a one uses
+// tcgen05.mma with operands brought into shared memory by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) and the FP32 chunk accumulators in
+// tensor memory, double-buffered so that the FP64 folding of one chunk
+// overlaps the products of the next; a plain mma.sync m16n8k16 kernel is kept
+// as the reference route for checking it.
+#include <cuda.h>
 #include <cuda_bf16.h>
+
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -23,6 +31,7 @@ namespace fraclap {
 namespace {
 
 constexpr int OZ_BM = 64, OZ_BN = 64, OZ_BK = 32, OZ_NT = 128, OZ_CHUNK = 256;
+constexpr int OZ_KPAD = 64;  // slice rows padded to a multiple of 64 (one TMA box)
 constexpr int OZ_LDS = OZ_BK / 2 + 4;  // shared row stride in 32-bit words (padded)
 
 // Exponent of the largest |entry| of each row of op(A) (rows = M, length K).
@@ -169,10 +178,302 @@ ozaki_kernel(const __nv_bfloat16* __restrict__ SA, const __nv_bfloat16* __restri
       }
 }
 
+
+// ----------------------------------------------------------------------------
+// tcgen05 route: CTA tile 128 (rows of op(A)) x 64 (columns of op(B)).
+// Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 2-5:
+// epilogue (TMEM lanes 32 (w % 4) ..), each thread one output row.
+// ----------------------------------------------------------------------------
+constexpr int TC_M = 128, TC_N = 64, TC_KB = 64, TC_STAGES = 4;
+constexpr int TC_A_BYTES = TC_M * TC_KB * 2, TC_B_BYTES = TC_N * TC_KB * 2;
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_THREADS = 192;
+constexpr uint32_t TC_TMEM_COLS = 128;  // two 64-column FP32 accumulators
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false after `limit` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > limit) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// SMEM descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+// kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, M 128, N 64.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                              ((uint32_t)(TC_M >> 4) << 24);
+__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                const int* __restrict__ ea, const int* __restrict__ eb, int64_t M, int64_t N, int64_t Kp,
+                int s, double alpha, double beta, double* C, int64_t ldc, int lower, long long limit,
+                int32_t* status) {
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * TC_M, n0 = (int64_t)blockIdx.y * TC_N;
+  if (lower && m0 + TC_M - 1 < n0) return;  // whole CTA: tile above the diagonal
+  const int nchunk = (int)((Kp + OZ_CHUNK - 1) / OZ_CHUNK);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < TC_STAGES; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 4);
+    }
+    mbar_init(&done_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int p = 0; p < s && ok; ++p)
+        for (int q = 0; p + q < s && ok; ++q)
+          for (int c = 0; c < nchunk && ok; ++c) {
+            const int64_t c0 = (int64_t)c * OZ_CHUNK;
+            const int nkb = (int)(((Kp - c0) < OZ_CHUNK ? (Kp - c0) : OZ_CHUNK) / TC_KB);
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+              const int st = it % TC_STAGES;
+              if (!mbar_wait(&empty_bar[st], ((it / TC_STAGES) & 1) ^ 1, limit) || *(volatile int*)&abort_sh) {
+                ok = false;
+                break;
+              }
+              unsigned char* a = smem + st * TC_STAGE_BYTES;
+              unsigned char* b = a + TC_A_BYTES;
+              mbar_expect_tx(&full_bar[st], TC_STAGE_BYTES);
+              const int kc = (int)(c0 + kb * TC_KB);
+              tma_load_3d(a, &mapA, &full_bar[st], kc, (int)m0, p);
+              tma_load_3d(b, &mapB, &full_bar[st], kc, (int)n0, q);
+            }
+          }
+      if (!ok) {
+        atomicCAS(status, 0, FRACLAP_ERR_TIMEOUT);
+        abort_sh = 1;
+        // let the copies already issued land before the CTA can exit
+        for (int j = (it > TC_STAGES ? it - TC_STAGES : 0); j < it; ++j)
+          mbar_wait(&full_bar[j % TC_STAGES], (j / TC_STAGES) & 1, limit);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int it = 0, chunk = 0;
+      bool ok = true;
+      for (int p = 0; p < s && ok; ++p)
+        for (int q = 0; p + q < s && ok; ++q)
+          for (int c = 0; c < nchunk && ok; ++c, ++chunk) {
+            const int buf = chunk & 1;
+            if (!mbar_wait(&acc_empty[buf], ((chunk >> 1) & 1) ^ 1, limit) || *(volatile int*)&abort_sh) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(buf * TC_N);
+            const int64_t c0 = (int64_t)c * OZ_CHUNK;
+            const int nkb = (int)(((Kp - c0) < OZ_CHUNK ? (Kp - c0) : OZ_CHUNK) / TC_KB);
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+              const int st = it % TC_STAGES;
+              if (!mbar_wait(&full_bar[st], (it / TC_STAGES) & 1, limit) || *(volatile int*)&abort_sh) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t a = smem_u32(smem + st * TC_STAGE_BYTES);
+              const uint32_t b = a + TC_A_BYTES;
+#pragma unroll
+              for (int kk = 0; kk < TC_KB / 16; ++kk)  // K = 16 per instruction: 32 bytes
+                umma(d, sdesc_k128(a + kk * 32), sdesc_k128(b + kk * 32), (kb > 0 || kk > 0) ? 1u : 0u);
+              umma_commit(&empty_bar[st]);  // frees the stage once these MMAs have read it
+            }
+            if (!ok) break;
+            umma_commit(&acc_full[buf]);  // the chunk's accumulator is complete
+          }
+      if (!ok) {
+        atomicCAS(status, 0, FRACLAP_ERR_TIMEOUT);
+        abort_sh = 1;
+      }
+      umma_commit(&done_bar);  // every MMA issued so far has finished when this fires
+      mbar_wait(&done_bar, 0, limit);
+    }
+  } else {
+    // ---------------- epilogue: FP64 folding ----------------
+    const int lg = warp & 3;                 // TMEM lane group of this warp
+    const int64_t row = m0 + lg * 32 + lane;  // output row of this thread
+    double sum[TC_N];
+#pragma unroll
+    for (int j = 0; j < TC_N; ++j) sum[j] = 0.0;
+    int chunk = 0;
+    bool ok = true;
+    for (int p = 0; p < s && ok; ++p)
+      for (int q = 0; p + q < s && ok; ++q) {
+        const double scale = ldexp(1.0, -8 * (p + q + 2));
+        for (int c = 0; c < nchunk; ++c, ++chunk) {
+          const int buf = chunk & 1;
+          if (!mbar_wait(&acc_full[buf], (chunk >> 1) & 1, limit) || *(volatile int*)&abort_sh) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * TC_N);
+#pragma unroll
+          for (int j0 = 0; j0 < TC_N; j0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(taddr + j0, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) sum[j0 + j] = fma((double)__uint_as_float(r[j]), scale, sum[j0 + j]);
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        }
+      }
+    if (!ok) {
+      if (lane == 0) atomicCAS(status, 0, FRACLAP_ERR_TIMEOUT);
+      abort_sh = 1;
+    } else if (row < M) {
+      const int er = ea[row];
+#pragma unroll
+      for (int j = 0; j < TC_N; ++j) {
+        const int64_t col = n0 + j;
+        if (col >= N || (lower && row < col)) continue;
+        const double v = ldexp(sum[j], er + eb[col]);
+        double* cp = C + row + col * ldc;
+        *cp = (beta == 0.0) ? alpha * v : alpha * v + beta * *cp;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// 3-D map over the slices S[s][rows][Kp] (bf16), box 64 (K) x box_rows x 1.
+bool slice_map(CUtensorMap* map, const __nv_bfloat16* S, int64_t rows, int64_t Kp, int s, int box_rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)s};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
+  const cuuint32_t box[3] = {TC_KB, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)S, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 }  // namespace
 
 size_t ozaki_ws(int64_t M, int64_t N, int64_t K, int s) {
-  const int64_t Kp = cdiv(K, OZ_BK) * OZ_BK;
+  const int64_t Kp = cdiv(std::max<int64_t>(K, 1), OZ_KPAD) * OZ_KPAD;
   Arena ar;
   ar.take<__nv_bfloat16>((int64_t)s * M * Kp);
   ar.take<__nv_bfloat16>((int64_t)s * N * Kp);
@@ -189,7 +490,7 @@ int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t
   if (M <= 0 || N <= 0) return 0;
   FL_CHECK(ctx, s >= 1 && s <= 8, FRACLAP_ERR_INVALID_ARG, "ozaki_gemm: slices must be 1..8");
   FL_CHECK(ctx, cdiv(N, OZ_BN) <= 65535, FRACLAP_ERR_UNSUPPORTED, "ozaki_gemm: N too large");
-  const int64_t Kp = cdiv(std::max<int64_t>(K, 1), OZ_BK) * OZ_BK;
+  const int64_t Kp = cdiv(std::max<int64_t>(K, 1), OZ_KPAD) * OZ_KPAD;
   __nv_bfloat16* SA = ar->take<__nv_bfloat16>((int64_t)s * M * Kp);
   __nv_bfloat16* SB = ar->take<__nv_bfloat16>((int64_t)s * N * Kp);
   int* ea = ar->take<int>(M);
@@ -205,8 +506,19 @@ int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t
   count_launch(ctx);
   make_slices<<<gs, 256, 0, st>>>(B, ldb, !tb, N, K, Kp, eb, s, SB);
   count_launch(ctx);
-  dim3 grid((unsigned)cdiv(M, OZ_BM), (unsigned)cdiv(N, OZ_BN));
-  ozaki_kernel<<<grid, OZ_NT, 0, st>>>(SA, SB, ea, eb, M, N, Kp, s, alpha, beta, C, ldc, lower);
+  if (ctx->tensor_route == 1) {
+    CUtensorMap ma, mb;
+    FL_CHECK(ctx, slice_map(&ma, SA, M, Kp, s, TC_M) && slice_map(&mb, SB, N, Kp, s, TC_N),
+             FRACLAP_ERR_CUDA, "ozaki_gemm: tensor map encoding failed");
+    const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
+    FL_CUDA(ctx, cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)cdiv(M, TC_M), (unsigned)cdiv(N, TC_N));
+    ozaki_tc_kernel<<<grid, TC_THREADS, smem, st>>>(ma, mb, ea, eb, M, N, Kp, s, alpha, beta, C, ldc,
+                                                    lower ? 1 : 0, ctx->wait_cycles, ctx->d_status);
+  } else {
+    dim3 grid((unsigned)cdiv(M, OZ_BM), (unsigned)cdiv(N, OZ_BN));
+    ozaki_kernel<<<grid, OZ_NT, 0, st>>>(SA, SB, ea, eb, M, N, Kp, s, alpha, beta, C, ldc, lower);
+  }
   count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   return 0;

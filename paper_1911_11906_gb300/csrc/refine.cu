@@ -90,19 +90,49 @@ __global__ void frob_norms(const double* S, int64_t lds, const double* R, int64_
   }
 }
 
-// y = M x for a symmetric M stored in its lower triangle (diagonal shifted by
-// -shift[i] when shift is given); one thread per row.
-__global__ void symv_lower(const double* M, int64_t ldm, const double* shift, int64_t n,
-                           const double* x, double* y) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double s = 0.0;
-  for (int64_t j = 0; j < n; ++j) {
-    const double m = (j <= i) ? M[i + j * ldm] : M[j + i * ldm];
-    s = fma(m, x[j], s);
+// y += M x for a symmetric M stored in its lower triangle: one 32 x 32 tile
+// (I >= J) per block; the tile contributes L_IJ x_J to y_I and, off the
+// diagonal, L_IJ^T x_I to y_J (atomic adds).  y must be zeroed (or hold the
+// diagonal shift term) beforehand.
+__global__ void symv_lower_tiles(const double* M, int64_t ldm, int64_t n, const double* x, double* y) {
+  __shared__ double t[32][33];
+  // tile index -> (I, J) with I >= J over the lower tile triangle
+  const int64_t q = blockIdx.x;
+  int64_t I = (int64_t)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) / 2 > q) --I;
+  while ((I + 1) * (I + 2) / 2 <= q) ++I;
+  const int64_t J = q - I * (I + 1) / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t gi = I * 32 + tx, gj = J * 32 + r;
+    double v = 0.0;
+    if (gi < n && gj < n && (I != J || tx >= r)) v = M[gi + gj * ldm];
+    t[tx][r] = v;  // t[i][j] = L(I*32+i, J*32+j)
   }
-  if (shift) s -= shift[i] * x[i];
-  y[i] = s;
+  __syncthreads();
+  if (ty == 0) {  // y_I += L_IJ x_J
+    double s = 0.0;
+    for (int j = 0; j < 32; ++j) {
+      const int64_t gj = J * 32 + j;
+      if (gj < n) s = fma(t[tx][j], x[gj], s);
+    }
+    const int64_t gi = I * 32 + tx;
+    if (gi < n) atomicAdd(y + gi, s);
+  } else if (ty == 1) {  // y_J += L_IJ^T x_I (strictly lower part)
+    double s = 0.0;
+    for (int i = 0; i < 32; ++i) {
+      const int64_t gi = I * 32 + i;
+      if (gi < n && (I != J || i > tx)) s = fma(t[i][tx], x[gi], s);
+    }
+    const int64_t gj = J * 32 + tx;
+    if (gj < n) atomicAdd(y + gj, s);
+  }
+}
+
+// y = -shift .* x (or 0).
+__global__ void symv_init(const double* shift, const double* x, int64_t n, double* y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = shift ? -shift[i] * x[i] : 0.0;
 }
 
 // x = y / ||y||, est = ||y|| (one block).
@@ -283,7 +313,7 @@ constexpr int kRefineSlices = 7;
 // inside a cluster instead (its second-order error would not be small).
 constexpr double kUnsafeTau = 1e-2;
 
-__global__ void cluster_jacobi(const double* Sc, int c, double* Q, double* w, int32_t* status) {
+__device__ void cluster_jacobi_body(const double* Sc, int c, double* Q, double* w, int32_t* status) {
   __shared__ double a[kMaxCluster][kMaxCluster + 1];
   __shared__ double q[kMaxCluster][kMaxCluster + 1];
   __shared__ double rot[2];
@@ -364,6 +394,39 @@ __global__ void cluster_jacobi(const double* Sc, int c, double* Q, double* w, in
   if (tid < c) w[tid] = a[perm[tid]][perm[tid]];
 }
 
+// AXc(:, t) = A X(:, src[t]) for the concatenated cluster columns t < T.
+__global__ void spmm_csr_cols(int64_t n, const int64_t* __restrict__ rowptr,
+                              const int32_t* __restrict__ col, const double* __restrict__ val,
+                              const double* X, int64_t ldx, const int* src, int64_t T, double* Y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t p0 = rowptr[i], p1 = rowptr[i + 1];
+  for (int64_t t = blockIdx.y; t < T; t += gridDim.y) {
+    const double* x = X + (int64_t)src[t] * ldx;
+    double s = 0.0;
+    for (int64_t p = p0; p < p1; ++p) s = fma(val[p], x[col[p]], s);
+    Y[i + t * n] = s;
+  }
+}
+
+// X(:, src[t]) = Y(:, t).
+__global__ void scatter_columns(const double* Y, int64_t n, const int* src, int64_t T, double* X,
+                                int64_t ldx) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = blockIdx.y;
+  if (i < n && t < T) X[i + (int64_t)src[t] * ldx] = Y[i + t * n];
+}
+
+// One CTA per cluster: cinfo[3q] = size, cinfo[3q+1] = first sorted position;
+// S_q, Q_q at Sall/Qall + q * 64 * 64 (ld = size).
+__global__ void cluster_jacobi_batched(const double* Sall, const int* cinfo, double* Qall,
+                                       double* lambda, int32_t* status) {
+  const int q = blockIdx.x;
+  const int c = cinfo[3 * q], s0 = cinfo[3 * q + 1];
+  cluster_jacobi_body(Sall + (int64_t)q * kMaxCluster * kMaxCluster, c,
+                      Qall + (int64_t)q * kMaxCluster * kMaxCluster, lambda + s0, status);
+}
+
 // l_j = (x_j^T (A x_j)) / (x_j^T x_j); one block per column.
 __global__ void rayleigh(const double* X, int64_t ldx, const double* AX, int64_t ldax, int64_t n,
                          double* l) {
@@ -399,6 +462,15 @@ __global__ void rayleigh(const double* X, int64_t ldx, const double* AX, int64_t
 // the FP64 dense eigensolver of this library; its workspace is sized for n).
 constexpr int64_t kMaxBigCluster = 65535;
 
+// Scratch of the batched small-cluster step: S_q and Q_q (64 x 64 each) for
+// up to n/2 + 1 clusters, the column map, the cluster table and the GEMM
+// descriptors.
+static int64_t small_cluster_doubles(int64_t n) {
+  const int64_t ns = n / 2 + 1;
+  return 2 * ns * kMaxCluster * kMaxCluster + (n + 64) / 2 + (3 * ns + 64) / 2 + 64 +
+         (int64_t)(2 * ns * sizeof(GemmDescT<double>) + 7) / 8;
+}
+
 size_t refine_ws(const fraclap_ctx* ctx, int64_t n) {
   Arena ar;
   ar.take<double>(n * n);      // AX, then sorted X
@@ -415,7 +487,8 @@ size_t refine_ws(const fraclap_ctx* ctx, int64_t n) {
   ar.take<int>(2 * n + 2);     // cluster list + count
   ar.take<double>(8);          // norms, delta
   const int64_t cmax = std::min<int64_t>(n, kMaxBigCluster);
-  ar.take<double>(n * cmax * 2 + 2 * cmax * cmax + cmax);
+  ar.take<double>(2 * cmax * cmax + cmax);
+  ar.take<double>(small_cluster_doubles(n));
   return ar.off + std::max(cluster_eig_ws(ctx, cmax), ozaki_ws(n, n, n, kRefineSlices));
 }
 
@@ -437,7 +510,8 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
   double* scal = ar->take<double>(8);
   ctx->refine_stats.clear();
   const int64_t cmax = std::min<int64_t>(n, kMaxBigCluster);
-  double* cbuf = ar->take<double>(n * cmax * 2 + 2 * cmax * cmax + cmax);
+  double* cbuf = ar->take<double>(2 * cmax * cmax + cmax);
+  double* sbuf = ar->take<double>(small_cluster_doubles(n));
   Arena car = *ar;  // workspace of the dense eigensolver used on big clusters
   FL_CHECK(ctx, cbuf != nullptr, FRACLAP_ERR_ALLOC, "refine: workspace too small");
   const unsigned rows = (unsigned)cdiv(n, 128);
@@ -480,9 +554,12 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
         const double* shift = which == 0 ? lt : nullptr;
         start_vec<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(xv, n);
         count_launch(ctx);
+        const int64_t nt = cdiv(n, 32);
         for (int pit = 0; pit < 12; ++pit) {
-          symv_lower<<<(unsigned)cdiv(n, 128), 128, 0, st>>>(M, n, shift, n, xv, yv);
+          symv_init<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(shift, xv, n, yv);
+          symv_lower_tiles<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(M, n, n, xv, yv);
           normalize_vec<<<1, 1024, 0, st>>>(yv, n, xv, scal + 4 + which);
+          count_launch(ctx);
           count_launch(ctx);
           count_launch(ctx);
         }
@@ -534,26 +611,71 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
       converged = (hs[5] <= kConvergedR) && (hs[4] <= kConvergedR * na);
     }
     if (ncl > 0) {
-      double* AXc = cbuf;                        // n x c
-      double* Xn = cbuf + n * cmax;              // n x c
-      double* Sc = Xn + n * cmax;                // c x c
-      double* Qc = Sc + cmax * cmax;
+      // clusters up to kMaxCluster: batched (gather A X_c, S_c = X_c^T A X_c,
+      // Jacobi per CTA, X_c Q_c, scatter); larger ones one by one through the
+      // dense FP64 eigensolver.
+      std::vector<int> src, cinfo;
+      std::vector<D64> dS, dQ;
+      int64_t T = 0;
+      double* AXc = R;                      // n x T (R and S are free here)
+      double* Ycat = S;                     // n x T
+      double* Sall = sbuf;                  // nsmall x 64 x 64
+      std::vector<int> big;
       for (int q = 0; q < ncl; ++q) {
+        const int i0 = cl[2 * q], c = cl[2 * q + 1];
+        if (c > kMaxCluster) { big.push_back(q); continue; }
+        const int64_t qi = (int64_t)cinfo.size() / 3;
+        cinfo.push_back(c);
+        cinfo.push_back(i0);
+        cinfo.push_back((int)T);
+        for (int t = 0; t < c; ++t) src.push_back(i0 + t);
+        dS.push_back(D64{c, c, n, X + (int64_t)i0 * ldx, ldx, AXc + T * n, n, Sall + qi * kMaxCluster * kMaxCluster, c,
+                         nullptr, 0, nullptr, 0, 0, 1.0, 0.0});
+        T += c;
+      }
+      const int64_t ns = (int64_t)cinfo.size() / 3;
+      if (ns > 0) {
+        double* Qall = Sall + ns * kMaxCluster * kMaxCluster;
+        for (int64_t qi = 0; qi < ns; ++qi) {
+          const int c = cinfo[3 * qi], i0 = cinfo[3 * qi + 1], off = cinfo[3 * qi + 2];
+          dQ.push_back(D64{n, c, c, X + (int64_t)i0 * ldx, ldx, Qall + qi * kMaxCluster * kMaxCluster, c,
+                           Ycat + (int64_t)off * n, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0});
+        }
+        int* d_src = reinterpret_cast<int*>(Qall + ns * kMaxCluster * kMaxCluster);
+        int* d_cinfo = d_src + ((T + 63) / 64) * 64;
+        D64* d_desc = reinterpret_cast<D64*>(d_cinfo + ((3 * ns + 63) / 64) * 64);
+        FL_CUDA(ctx, cudaMemcpyAsync(d_src, src.data(), sizeof(int) * T, cudaMemcpyHostToDevice, st));
+        FL_CUDA(ctx, cudaMemcpyAsync(d_cinfo, cinfo.data(), sizeof(int) * 3 * ns, cudaMemcpyHostToDevice, st));
+        FL_CUDA(ctx, cudaMemcpyAsync(d_desc, dS.data(), sizeof(D64) * ns, cudaMemcpyHostToDevice, st));
+        FL_CUDA(ctx, cudaMemcpyAsync(d_desc + ns, dQ.data(), sizeof(D64) * ns, cudaMemcpyHostToDevice, st));
+        FL_CHECK(ctx, ns <= 65535 && T <= 65535, FRACLAP_ERR_UNSUPPORTED, "refine: too many clustered columns");
+        spmm_csr_cols<<<dim3(rows, (unsigned)std::min<int64_t>(T, 4096)), 128, 0, st>>>(n, rowptr, col, val, X, ldx,
+                                                                                       d_src, T, AXc);
+        count_launch(ctx);
+        FL_TRY(gemm_batched<double>(ctx, true, false, d_desc, (int)ns, kMaxCluster, kMaxCluster, st));
+        cluster_jacobi_batched<<<(unsigned)ns, 64, 0, st>>>(Sall, d_cinfo, Qall, lambda, ctx->d_status);
+        count_launch(ctx);
+        FL_TRY(gemm_batched<double>(ctx, false, false, d_desc + ns, (int)ns, n, kMaxCluster, st));
+        scatter_columns<<<dim3((unsigned)cdiv(n, 256), (unsigned)T), 256, 0, st>>>(Ycat, n, d_src, T, X, ldx);
+        count_launch(ctx);
+        // the host vectors must outlive the asynchronous copies
+        FL_CUDA(ctx, cudaStreamSynchronize(st));
+      }
+      double* Sc = cbuf;
+      double* Qc = Sc + cmax * cmax;
+      double* AXb = R;
+      double* Xn = S;
+      for (int q : big) {
         const int i0 = cl[2 * q], c = cl[2 * q + 1];
         FL_CHECK(ctx, c <= cmax, FRACLAP_ERR_UNSUPPORTED,
                  "refine: a cluster of %d eigenvalues exceeds %lld", c, (long long)cmax);
         double* Xc = X + (int64_t)i0 * ldx;
-        spmm_csr<<<dim3(rows, (unsigned)c), 128, 0, st>>>(n, rowptr, col, val, Xc, ldx, c, AXc, n);
+        spmm_csr<<<dim3(rows, (unsigned)std::min(c, 4096)), 128, 0, st>>>(n, rowptr, col, val, Xc, ldx, c, AXb, n);
         count_launch(ctx);
         FL_CUDA(ctx, cudaMemsetAsync(Sc, 0, sizeof(double) * c * c, st));
-        FL_TRY(gemm<double>(ctx, true, false, kGemmPlain, D64{c, c, n, Xc, ldx, AXc, n, Sc, c, nullptr, 0, nullptr, 0, 0, 1.0, 1.0}, (int)cdiv(n, 512), st));
-        if (c <= kMaxCluster) {
-          cluster_jacobi<<<1, 64, 0, st>>>(Sc, c, Qc, lambda + i0, ctx->d_status);
-          count_launch(ctx);
-        } else {
-          Arena sub = car;
-          FL_TRY(cluster_eig(ctx, Sc, c, lambda + i0, Qc, &sub, st));
-        }
+        FL_TRY(gemm<double>(ctx, true, false, kGemmPlain, D64{c, c, n, Xc, ldx, AXb, n, Sc, c, nullptr, 0, nullptr, 0, 0, 1.0, 1.0}, (int)cdiv(n, 512), st));
+        Arena sub = car;
+        FL_TRY(cluster_eig(ctx, Sc, c, lambda + i0, Qc, &sub, st));
         FL_TRY(gemm<double>(ctx, false, false, kGemmPlain, D64{n, c, c, Xc, ldx, Qc, c, Xn, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
         FL_CUDA(ctx, cudaMemcpy2DAsync(Xc, ldx * sizeof(double), Xn, n * sizeof(double), n * sizeof(double), c,
                                        cudaMemcpyDeviceToDevice, st));

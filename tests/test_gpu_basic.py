@@ -149,3 +149,22 @@ def test_dgemm_ozaki_fewer_slices_bound():
         got = F.dgemm_ozaki(_colmajor(A), _colmajor(B), slices=s).cpu().numpy()
         scale = np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * 300
         assert np.max(np.abs(got - ref) / scale) <= 2.0 ** (-8 * s + 4)
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 64, 64), (130, 70, 300), (257, 200, 1000), (64, 300, 64)])
+def test_tcgen05_slice_products_match_mma_sync_route(m, n, k):
+    """The tcgen05/TMA route and the mma.sync route compute the same exact
+    slice products: results agree to the last bits, and both match FP64."""
+    F = _F()
+    rng = np.random.default_rng(m * 3 + n * 5 + k)
+    A = rng.standard_normal((k, m))
+    B = rng.standard_normal((k, n))
+    ctx_tc = F.Context(wait_timeout_s=2.0)
+    ctx_ms = F.Context(wait_timeout_s=2.0)
+    ctx_ms.set_tensor_route(0)
+    out = [F.dgemm_ozaki(_colmajor(A), _colmajor(B), trans_a=True, ctx=ctx).cpu().numpy()
+           for ctx in (ctx_tc, ctx_ms)]
+    ref = A.T @ B
+    scale = np.abs(A).max(axis=0)[:, None] * np.abs(B).max(axis=0)[None, :] * k
+    assert np.max(np.abs(out[0] - out[1]) / scale) <= 1e-16
+    assert np.max(np.abs(out[0] - ref) / scale) <= 1e-15
