@@ -143,14 +143,14 @@ REFINE_ITERS = 6
 BAND = {"fp64": 64, "mixed": 64}
 
 
-def ozaki_bf16_flops(n: int, slices: int = 7) -> float:
-    """BF16 tensor flops of one lower-triangular n x n x n residual product:
-    slice pairs with p + q <= s + 1, over the lower-triangle tiles (64 x 64)."""
+def ozaki_bf16_flops(n: int, slices: int = 8) -> float:
+    """BF16 tensor flops one lower-triangular n x n x n residual product issues:
+    the 7-bit slicing for K > 256 uses 8 slices (pairs with p + q <= 9, 36
+    products) over the 128 x 64 CTA tiles that touch the lower triangle."""
     pairs = slices * (slices + 1) // 2
-    t = -(-n // 64)
-    tiles = t * (t + 1) // 2
-    kp = -(-n // 32) * 32
-    return 2.0 * pairs * tiles * 64 * 64 * kp
+    tiles = sum(1 for i in range(-(-n // 128)) for j in range(-(-n // 64)) if i * 128 + 127 >= j * 64)
+    kp = -(-n // 64) * 64
+    return 2.0 * pairs * tiles * 128 * 64 * kp
 
 
 def run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier):
@@ -275,7 +275,7 @@ def run_gpu(args, rank, world, local_rank):
         dur = g_ms / max(g_cnt, 1)
         work = ozaki_bf16_flops(n)
         peak = _measured_peak("bf16_tflops") or 1900.0
-        roof = {"kernel": "ozaki_kernel (residual products of the refinement, BF16 slices on mma.sync)",
+        roof = {"kernel": "ozaki_tc_kernel (residual products of the refinement: tcgen05.mma on TMA-loaded BF16 slices)",
                 "bound": "tensor", "peak": round(peak, 1),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if _measured_peak("bf16_tflops") else "fallback 1.9 PFLOP/s"}
     achieved = work / (dur * 1e-3) / 1e12

@@ -121,7 +121,7 @@ int eig_full(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_t lda,
  * of close eigenvalues, and pairs whose first-order correction would be
  * large, are diagonalised exactly).  refine_iters is the maximum number of
  * iterations; the loop stops after the first iteration that starts with
- * ||I - V^T V||_2 and ||V^T A V - D||_2 / ||A||_2 below 1e-9.  FP32-accurate
+ * ||I - V^T V||_2 and ||V^T A V - D||_2 / ||A||_2 below 3e-9.  FP32-accurate
  * starting vectors at n ~ 10^4 take three or four.
  *
  *  A_dev      double[lda*n] dense, lower triangle read (the FP32 stages).

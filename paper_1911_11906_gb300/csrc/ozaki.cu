@@ -3,15 +3,17 @@
 // 2012), written from the method's mathematics.
 //
 // Every row i of op(A) is scaled by 2^-e_i (e_i: the exponent of its largest
-// entry) and cut into s slices of 8 bits, A = sum_p 2^(e_i - 8p) A_p with A_p
-// integer in [-255, 255] (exact in BF16); likewise every column j of op(B)
-// with 2^f_j.  A product of two slices is an integer below 2^16, so a sum of
-// 256 of them is exact in an FP32 accumulator: the tensor cores compute
-// P_pq = A_p B_q exactly in K-chunks of 256, and the exact chunk sums are
-// added, scaled by 2^-8(p+q), into an FP64 accumulator per output element
-// (K/256 x pairs FP64 additions instead of K FP64 multiply-adds).  Pairs
-// with p + q <= s + 1 are kept; the dropped tail and the slicing truncation
-// are below 2^-8s relative to |row max| |column max| per term.  The result
+// entry) and cut into slices of w bits, A = sum_p 2^(e_i - w p) A_p with A_p
+// integer in (-2^w, 2^w) (exact in BF16 for w <= 8); likewise every column j
+// of op(B) with 2^f_j.  A product of two slices is an integer below 2^2w, so a
+// sum of 2^(24-2w) of them is exact in an FP32 accumulator: the tensor cores
+// compute P_pq = A_p B_q exactly in K-chunks of that length, and the exact
+// chunk sums are added, scaled by 2^-w(p+q), into an FP64 accumulator per
+// output element.  w = 8 (chunks of 256) for short K; otherwise w = 7 (chunks
+// of 1024) with ceil(8s/7) slices, which keeps the 8s bits and needs three
+// times fewer FP64 additions.  Pairs with p + q <= slices + 1 are kept; the
+// dropped tail and the slicing truncation are below about 2^-8s relative to
+// |row max| |column max| per term.  The result
 // C = alpha 2^(e_i + f_j) sum + beta C is formed in FP64.
 //
 // Two tensor-core kernels compute the slice products: the sm_103a one uses
@@ -30,7 +32,7 @@
 namespace fraclap {
 namespace {
 
-constexpr int OZ_BM = 64, OZ_BN = 64, OZ_BK = 32, OZ_NT = 128, OZ_CHUNK = 256;
+constexpr int OZ_BM = 64, OZ_BN = 64, OZ_BK = 32, OZ_NT = 128;
 constexpr int OZ_KPAD = 64;  // slice rows padded to a multiple of 64 (one TMA box)
 constexpr int OZ_LDS = OZ_BK / 2 + 4;  // shared row stride in 32-bit words (padded)
 
@@ -59,7 +61,7 @@ __global__ void row_exponents(const double* A, int64_t lda, bool trans, int64_t 
 // Slices of op(A) (M x K): S[p][i][k] (k contiguous, Kp >= K, zero padded).
 // One thread per (i, k); i fastest when A is not transposed (coalesced reads).
 __global__ void make_slices(const double* A, int64_t lda, bool trans, int64_t M, int64_t K,
-                            int64_t Kp, const int* ex, int s, __nv_bfloat16* S) {
+                            int64_t Kp, const int* ex, int s, int bits, __nv_bfloat16* S) {
   const int64_t total = M * Kp;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -68,7 +70,7 @@ __global__ void make_slices(const double* A, int64_t lda, bool trans, int64_t M,
     double x = 0.0;
     if (k < K) x = ldexp(trans ? A[k + i * lda] : A[i + k * lda], -ex[i]);
     for (int p = 0; p < s; ++p) {
-      const double y = x * 256.0;
+      const double y = ldexp(x, bits);
       const double q = trunc(y);
       S[((int64_t)p * M + i) * Kp + k] = __float2bfloat16_rn((float)q);
       x = y - q;
@@ -88,7 +90,8 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 __global__ void __launch_bounds__(OZ_NT)
 ozaki_kernel(const __nv_bfloat16* __restrict__ SA, const __nv_bfloat16* __restrict__ SB,
              const int* __restrict__ ea, const int* __restrict__ eb, int64_t M, int64_t N,
-             int64_t Kp, int s, double alpha, double beta, double* C, int64_t ldc, bool lower) {
+             int64_t Kp, int s, int bits, int64_t chunk, double alpha, double beta, double* C,
+             int64_t ldc, bool lower) {
   __shared__ uint32_t As[OZ_BM][OZ_LDS];
   __shared__ uint32_t Bs[OZ_BN][OZ_LDS];
   const int64_t m0 = (int64_t)blockIdx.x * OZ_BM, n0 = (int64_t)blockIdx.y * OZ_BN;
@@ -109,15 +112,15 @@ ozaki_kernel(const __nv_bfloat16* __restrict__ SA, const __nv_bfloat16* __restri
     for (int q = 0; p + q < s; ++q) {  // slices p, q (0-based): p + q <= s - 1
       const __nv_bfloat16* Ap = SA + (int64_t)p * M * Kp;
       const __nv_bfloat16* Bq = SB + (int64_t)q * N * Kp;
-      const double scale = ldexp(1.0, -8 * (p + q + 2));
-      for (int64_t c0 = 0; c0 < Kp; c0 += OZ_CHUNK) {
+      const double scale = ldexp(1.0, -bits * (p + q + 2));
+      for (int64_t c0 = 0; c0 < Kp; c0 += chunk) {
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
           for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-        const int64_t cend = (c0 + OZ_CHUNK < Kp) ? c0 + OZ_CHUNK : Kp;
+        const int64_t cend = (c0 + chunk < Kp) ? c0 + chunk : Kp;
         for (int64_t k0 = c0; k0 < cend; k0 += OZ_BK) {
           // 64 rows x 32 bf16 = 64 x 16 words per operand; 128 threads x 8 words each
 #pragma unroll
@@ -271,7 +274,8 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __global__ void __launch_bounds__(TC_THREADS, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const int* __restrict__ ea, const int* __restrict__ eb, int64_t M, int64_t N, int64_t Kp,
-                int s, double alpha, double beta, double* C, int64_t ldc, int lower, long long limit,
+                int s, int bits, int64_t chunk, double alpha, double beta, double* C, int64_t ldc,
+                int lower, long long limit,
                 int32_t* status) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -282,7 +286,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.x * TC_M, n0 = (int64_t)blockIdx.y * TC_N;
   if (lower && m0 + TC_M - 1 < n0) return;  // whole CTA: tile above the diagonal
-  const int nchunk = (int)((Kp + OZ_CHUNK - 1) / OZ_CHUNK);
+  const int nchunk = (int)((Kp + chunk - 1) / chunk);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < TC_STAGES; ++i) {
@@ -318,8 +322,8 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       for (int p = 0; p < s && ok; ++p)
         for (int q = 0; p + q < s && ok; ++q)
           for (int c = 0; c < nchunk && ok; ++c) {
-            const int64_t c0 = (int64_t)c * OZ_CHUNK;
-            const int nkb = (int)(((Kp - c0) < OZ_CHUNK ? (Kp - c0) : OZ_CHUNK) / TC_KB);
+            const int64_t c0 = (int64_t)c * chunk;
+            const int nkb = (int)(((Kp - c0) < chunk ? (Kp - c0) : chunk) / TC_KB);
             for (int kb = 0; kb < nkb; ++kb, ++it) {
               const int st = it % TC_STAGES;
               if (!mbar_wait(&empty_bar[st], ((it / TC_STAGES) & 1) ^ 1, limit) || *(volatile int*)&abort_sh) {
@@ -345,20 +349,20 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      int it = 0, chunk = 0;
+      int it = 0, chunk_i = 0;
       bool ok = true;
       for (int p = 0; p < s && ok; ++p)
         for (int q = 0; p + q < s && ok; ++q)
-          for (int c = 0; c < nchunk && ok; ++c, ++chunk) {
-            const int buf = chunk & 1;
-            if (!mbar_wait(&acc_empty[buf], ((chunk >> 1) & 1) ^ 1, limit) || *(volatile int*)&abort_sh) {
+          for (int c = 0; c < nchunk && ok; ++c, ++chunk_i) {
+            const int buf = chunk_i & 1;
+            if (!mbar_wait(&acc_empty[buf], ((chunk_i >> 1) & 1) ^ 1, limit) || *(volatile int*)&abort_sh) {
               ok = false;
               break;
             }
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(buf * TC_N);
-            const int64_t c0 = (int64_t)c * OZ_CHUNK;
-            const int nkb = (int)(((Kp - c0) < OZ_CHUNK ? (Kp - c0) : OZ_CHUNK) / TC_KB);
+            const int64_t c0 = (int64_t)c * chunk;
+            const int nkb = (int)(((Kp - c0) < chunk ? (Kp - c0) : chunk) / TC_KB);
             for (int kb = 0; kb < nkb; ++kb, ++it) {
               const int st = it % TC_STAGES;
               if (!mbar_wait(&full_bar[st], (it / TC_STAGES) & 1, limit) || *(volatile int*)&abort_sh) {
@@ -390,14 +394,14 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     double sum[TC_N];
 #pragma unroll
     for (int j = 0; j < TC_N; ++j) sum[j] = 0.0;
-    int chunk = 0;
+    int chunk_i = 0;
     bool ok = true;
     for (int p = 0; p < s && ok; ++p)
       for (int q = 0; p + q < s && ok; ++q) {
-        const double scale = ldexp(1.0, -8 * (p + q + 2));
-        for (int c = 0; c < nchunk; ++c, ++chunk) {
-          const int buf = chunk & 1;
-          if (!mbar_wait(&acc_full[buf], (chunk >> 1) & 1, limit) || *(volatile int*)&abort_sh) {
+        const double scale = ldexp(1.0, -bits * (p + q + 2));
+        for (int c = 0; c < nchunk; ++c, ++chunk_i) {
+          const int buf = chunk_i & 1;
+          if (!mbar_wait(&acc_full[buf], (chunk_i >> 1) & 1, limit) || *(volatile int*)&abort_sh) {
             ok = false;
             break;
           }
@@ -474,6 +478,7 @@ bool slice_map(CUtensorMap* map, const __nv_bfloat16* S, int64_t rows, int64_t K
 
 size_t ozaki_ws(int64_t M, int64_t N, int64_t K, int s) {
   const int64_t Kp = cdiv(std::max<int64_t>(K, 1), OZ_KPAD) * OZ_KPAD;
+  s = (8 * s + 6) / 7;  // room for the 7-bit slicing
   Arena ar;
   ar.take<__nv_bfloat16>((int64_t)s * M * Kp);
   ar.take<__nv_bfloat16>((int64_t)s * N * Kp);
@@ -491,33 +496,42 @@ int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t
   FL_CHECK(ctx, s >= 1 && s <= 8, FRACLAP_ERR_INVALID_ARG, "ozaki_gemm: slices must be 1..8");
   FL_CHECK(ctx, cdiv(N, OZ_BN) <= 65535, FRACLAP_ERR_UNSUPPORTED, "ozaki_gemm: N too large");
   const int64_t Kp = cdiv(std::max<int64_t>(K, 1), OZ_KPAD) * OZ_KPAD;
-  __nv_bfloat16* SA = ar->take<__nv_bfloat16>((int64_t)s * M * Kp);
-  __nv_bfloat16* SB = ar->take<__nv_bfloat16>((int64_t)s * N * Kp);
+  const int smax = (8 * s + 6) / 7;
+  __nv_bfloat16* SA = ar->take<__nv_bfloat16>((int64_t)smax * M * Kp);
+  __nv_bfloat16* SB = ar->take<__nv_bfloat16>((int64_t)smax * N * Kp);
   int* ea = ar->take<int>(M);
   int* eb = ar->take<int>(N);
   FL_CHECK(ctx, eb != nullptr, FRACLAP_ERR_ALLOC, "ozaki_gemm: workspace too small");
   // op(A) rows: trans -> A stored K x M; op(B) columns = rows of op(B)^T
+  // slice width: 8 bits (exact chunks of 256) for short K, else 7 bits (exact
+  // chunks of 1024) with one more slice for the same 8s bits: 3x fewer folds.
+  int bits = 8, sl = s;
+  if (K > 256) {
+    bits = 7;
+    sl = (8 * s + 6) / 7;
+  }
+  const int64_t chunk = (int64_t)1 << (24 - 2 * bits);
   row_exponents<<<(unsigned)M, 256, 0, st>>>(A, lda, ta, K, ea);
   count_launch(ctx);
   row_exponents<<<(unsigned)N, 256, 0, st>>>(B, ldb, !tb, K, eb);
   count_launch(ctx);
   const unsigned gs = (unsigned)std::min<int64_t>(cdiv(std::max(M, N) * Kp, 256), 152 * 32);
-  make_slices<<<gs, 256, 0, st>>>(A, lda, ta, M, K, Kp, ea, s, SA);
+  make_slices<<<gs, 256, 0, st>>>(A, lda, ta, M, K, Kp, ea, sl, bits, SA);
   count_launch(ctx);
-  make_slices<<<gs, 256, 0, st>>>(B, ldb, !tb, N, K, Kp, eb, s, SB);
+  make_slices<<<gs, 256, 0, st>>>(B, ldb, !tb, N, K, Kp, eb, sl, bits, SB);
   count_launch(ctx);
   if (ctx->tensor_route == 1) {
     CUtensorMap ma, mb;
-    FL_CHECK(ctx, slice_map(&ma, SA, M, Kp, s, TC_M) && slice_map(&mb, SB, N, Kp, s, TC_N),
+    FL_CHECK(ctx, slice_map(&ma, SA, M, Kp, sl, TC_M) && slice_map(&mb, SB, N, Kp, sl, TC_N),
              FRACLAP_ERR_CUDA, "ozaki_gemm: tensor map encoding failed");
     const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
     FL_CUDA(ctx, cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)cdiv(M, TC_M), (unsigned)cdiv(N, TC_N));
-    ozaki_tc_kernel<<<grid, TC_THREADS, smem, st>>>(ma, mb, ea, eb, M, N, Kp, s, alpha, beta, C, ldc,
-                                                    lower ? 1 : 0, ctx->wait_cycles, ctx->d_status);
+    ozaki_tc_kernel<<<grid, TC_THREADS, smem, st>>>(ma, mb, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C,
+                                                    ldc, lower ? 1 : 0, ctx->wait_cycles, ctx->d_status);
   } else {
     dim3 grid((unsigned)cdiv(M, OZ_BM), (unsigned)cdiv(N, OZ_BN));
-    ozaki_kernel<<<grid, OZ_NT, 0, st>>>(SA, SB, ea, eb, M, N, Kp, s, alpha, beta, C, ldc, lower);
+    ozaki_kernel<<<grid, OZ_NT, 0, st>>>(SA, SB, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc, lower);
   }
   count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());

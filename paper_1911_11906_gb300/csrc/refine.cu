@@ -306,7 +306,7 @@ __global__ void copy_columns(const double* Xs, int64_t n, double* X, int64_t ldx
 constexpr int kMaxCluster = 64;
 // Stop after the iteration that starts with ||R||_2 and ||S - D||_2 / ||A||_2 below this
 // (its quadratic step lands at rounding level).
-constexpr double kConvergedR = 1e-9;
+constexpr double kConvergedR = 3e-9;
 // BF16 slices per operand in the refinement's residual products (7: FP64).
 constexpr int kRefineSlices = 7;
 // A pair whose first-order coefficient exceeds this is diagonalised exactly

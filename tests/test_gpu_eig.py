@@ -148,7 +148,7 @@ def test_eig_full_mixed_refined_vs_oracle(which, b, iters):
     _check_decomposition(D, lam_o, lam, V)
     stats = ctx.refine_stats()
     assert 1 <= len(stats) <= iters
-    assert stats[-1]["norm2_R"] <= 1e-9 or len(stats) == iters
+    assert stats[-1]["norm2_R"] <= 3e-9 or len(stats) == iters
     U_o = O.frac_apply(V_o, lam_o, p.F, p.pair_f, p.pair_alpha)
     U = O.frac_apply(V, lam, p.F, p.pair_f, p.pair_alpha)
     err = max(np.linalg.norm(U[:, j] - U_o[:, j]) / np.linalg.norm(U_o[:, j]) for j in range(U.shape[1]))
