@@ -228,7 +228,12 @@ enum {
   FRACLAP_STAGE_APPLY = 6,          /* frac_apply */
   FRACLAP_STAGE_REFINE = 7,         /* Ogita-Aishima refinement (eig_full_mixed) */
   FRACLAP_STAGE_RESIDUAL_GEMM = 8,  /* its tensor-core residual products (inside REFINE) */
-  FRACLAP_STAGE_COUNT = 9
+  FRACLAP_STAGE_REFINE_NORMS = 9,   /* A V, Ritz values, 2-norm estimates (inside REFINE) */
+  FRACLAP_STAGE_REFINE_UPDATE = 10, /* cluster detection, correction, V += V E (inside REFINE) */
+  FRACLAP_STAGE_REFINE_SORT = 11,   /* ordering of the columns (inside REFINE) */
+  FRACLAP_STAGE_REFINE_CLUSTERS = 12, /* exact diagonalisation of clusters up to 64 (inside REFINE) */
+  FRACLAP_STAGE_REFINE_BIG_CLUSTERS = 13, /* larger clusters, dense FP64 solver (inside REFINE) */
+  FRACLAP_STAGE_COUNT = 14
 };
 /* With enable != 0, every later stage records a CUDA event pair on its stream. */
 int fraclap_set_profiling(fraclap_ctx* ctx, int enable);
@@ -243,6 +248,11 @@ int fraclap_stage_times(fraclap_ctx* ctx, double* ms_out, int64_t* count_out, in
 int fraclap_refine_stats(const fraclap_ctx* ctx, double* out, int max_values);
 /* Number of kernels the context has launched so far. */
 long long fraclap_launch_count(const fraclap_ctx* ctx);
+
+/* Refinement safeguard of eig_full_mixed: a pair whose first-order
+ * correction coefficient exceeds tau (default 3e-3) is treated as part of a
+ * cluster and diagonalised exactly; 0 < tau <= 1. */
+int fraclap_set_refine_tau(fraclap_ctx* ctx, double tau);
 
 /* Tensor-core route of the BF16 slice products: 1 (default) = tcgen05.mma
  * with TMA-loaded operands and tensor-memory accumulators; 0 = mma.sync

@@ -38,6 +38,7 @@ SIGNATURES = {
     "fraclap_launch_count": (ctypes.c_longlong, [_p]),
     "fraclap_refine_stats": (_i32, [_p, _p, _i32]),
     "fraclap_set_tensor_route": (_i32, [_p, _i32]),
+    "fraclap_set_refine_tau": (_i32, [_p, _dbl]),
     "fraclap_dgemm_ozaki_workspace_bytes": (_sz, [_i64, _i64, _i64, _i32]),
     "fraclap_dgemm_ozaki": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64,
                                    _i32, _p, _sz, _p]),
@@ -115,7 +116,8 @@ class Context:
             raise FraclapError(rc, msg)
 
     STAGES = ("assemble", "band_reduction", "bulge_chasing", "tridiag_dc", "back_q2", "back_q1", "apply",
-              "refine", "residual_gemm")
+              "refine", "residual_gemm", "refine_norms", "refine_update", "refine_sort", "refine_clusters",
+              "refine_big_clusters")
 
     def set_profiling(self, enable: bool = True):
         self.check(self.lib.fraclap_set_profiling(self.handle, int(enable)))
@@ -137,6 +139,10 @@ class Context:
         nv = self.lib.fraclap_refine_stats(self.handle, buf, 512)
         f = self.REFINE_FIELDS
         return [dict(zip(f, buf[i:i + len(f)])) for i in range(0, min(nv, 512), len(f))]
+
+    def set_refine_tau(self, tau: float):
+        """Refinement safeguard: pairs with a first-order coefficient above tau are clustered."""
+        self.check(self.lib.fraclap_set_refine_tau(self.handle, float(tau)))
 
     def set_tensor_route(self, route: int):
         """1: tcgen05 + TMA slice products (default); 0: mma.sync."""

@@ -433,3 +433,9 @@ extern "C" int fraclap_set_tensor_route(fraclap_ctx* ctx, int route) {
   ctx->tensor_route = route;
   return 0;
 }
+
+extern "C" int fraclap_set_refine_tau(fraclap_ctx* ctx, double tau) {
+  if (!ctx || !(tau > 0.0) || tau > 1.0) return FRACLAP_ERR_INVALID_ARG;
+  ctx->refine_tau = tau;
+  return 0;
+}

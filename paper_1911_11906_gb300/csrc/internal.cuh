@@ -18,6 +18,7 @@ struct fraclap_ctx {
   int leaf_size = 32;
   double wait_timeout_s = 10.0;
   int tensor_route = 1;          // slice products: 1 = tcgen05 + TMA, 0 = mma.sync
+  double refine_tau = 3e-3;      // first-order coefficient above which a pair is clustered
   long long wait_cycles = 0;     // wait_timeout_s in SM clock cycles (upper bound)
   int32_t* d_status = nullptr;   // device status word (0 = ok, else a FRACLAP_ERR_*)
   unsigned* d_barrier = nullptr; // grid-barrier state for cooperative kernels
@@ -72,7 +73,12 @@ enum Stage : int {
   kStageApply = 6,
   kStageRefine = 7,
   kStageResidualGemm = 8,
-  kStageCount = 9
+  kStageRefineNorms = 9,      // A X, power iterations, threshold
+  kStageRefineUpdate = 10,    // unsafe pairs, correction, X += X E
+  kStageRefineSort = 11,      // ranks and column permutation
+  kStageRefineClusters = 12,  // exact diagonalisation of the clusters (up to 64)
+  kStageRefineBigClusters = 13,  // clusters above 64 (dense FP64 solver)
+  kStageCount = 14
 };
 
 // Records CUDA events around a stage on `st` when profiling is on.
@@ -94,6 +100,34 @@ struct StageTimer {
       cudaEventDestroy(e0);
     }
   }
+};
+
+// Consecutive spans on one stream: start(id) closes the previous span.
+struct StageSpan {
+  fraclap_ctx* ctx;
+  cudaStream_t st;
+  int stage = -1;
+  cudaEvent_t e0 = nullptr;
+  StageSpan(fraclap_ctx* c, cudaStream_t s) : ctx(c), st(s) {}
+  void start(int id) {
+    stop();
+    if (!ctx->profiling) return;
+    stage = id;
+    if (cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, st);
+    else e0 = nullptr;
+  }
+  void stop() {
+    if (!e0) return;
+    cudaEvent_t e1;
+    if (cudaEventCreate(&e1) == cudaSuccess) {
+      cudaEventRecord(e1, st);
+      ctx->stage_events.push_back({stage, e0, e1});
+    } else {
+      cudaEventDestroy(e0);
+    }
+    e0 = nullptr;
+  }
+  ~StageSpan() { stop(); }
 };
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -309,9 +309,6 @@ constexpr int kMaxCluster = 64;
 constexpr double kConvergedR = 3e-9;
 // BF16 slices per operand in the refinement's residual products (7: FP64).
 constexpr int kRefineSlices = 7;
-// A pair whose first-order coefficient exceeds this is diagonalised exactly
-// inside a cluster instead (its second-order error would not be small).
-constexpr double kUnsafeTau = 1e-2;
 
 __device__ void cluster_jacobi_body(const double* Sc, int c, double* Q, double* w, int32_t* status) {
   __shared__ double a[kMaxCluster][kMaxCluster + 1];
@@ -521,10 +518,13 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
   using D64 = GemmDescT<double>;
   using D32 = GemmDescT<float>;
   bool converged = false;
+  StageSpan span(ctx, st);
   for (int it = 0; it < iters && !converged; ++it) {
     // AX = A X
+    span.start(kStageRefineNorms);
     spmm_csr<<<dim3(rows, (unsigned)std::min<int64_t>(n, 4096)), 128, 0, st>>>(n, rowptr, col, val, X, ldx, n, AX, n);
     count_launch(ctx);
+    span.stop();
     // R = I - X^T X, S = X^T (A X): lower triangles, FP64-accurate products
     // from BF16 tensor-core slices (the slices live in the scratch arena)
     {
@@ -539,6 +539,7 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
       Arena oz = *ar;
       FL_TRY(ozaki_gemm(ctx, true, false, n, n, n, 1.0, X, ldx, AX, n, 0.0, S, n, kRefineSlices, true, &oz, st));
     }
+    span.start(kStageRefineNorms);
     ritz_values<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(S, n, R, n, n, lt);
     count_launch(ctx);
     FL_CUDA(ctx, cudaMemsetAsync(scal, 0, 8 * sizeof(double), st));
@@ -567,12 +568,13 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
     }
     cluster_threshold<<<1, 1, 0, st>>>(scal, scal + 4, nA, delta);
     count_launch(ctx);
+    span.start(kStageRefineUpdate);
     // clusters from unsafe pairs, in sorted order
     ranks<<<(unsigned)cdiv(n, 128), 128, 0, st>>>(lt, n, rank);
     count_launch(ctx);
     init_reach<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(reach, n);
     count_launch(ctx);
-    unsafe_spans<<<flat, 256, 0, st>>>(S, n, R, n, lt, rank, delta, kUnsafeTau, n, reach);
+    unsafe_spans<<<flat, 256, 0, st>>>(S, n, R, n, lt, rank, delta, ctx->refine_tau, n, reach);
     count_launch(ctx);
     merge_spans<<<1, 1, 0, st>>>(reach, n, cid, clist + 1, clist);
     count_launch(ctx);
@@ -582,6 +584,7 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
     FL_TRY(gemm<float>(ctx, false, false, kGemmPlain, D32{n, n, n, X32, n, E, n, P, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
     add_correction<<<flat, 256, 0, st>>>(X, ldx, P, n);
     count_launch(ctx);
+    span.start(kStageRefineSort);
     // sort the columns by l
     FL_CHECK(ctx, n <= 65535, FRACLAP_ERR_UNSUPPORTED, "refine: n too large");
     permute_columns<<<dim3((unsigned)cdiv(n, 256), (unsigned)n), 256, 0, st>>>(X, ldx, rank, n, AX, lt, ls);
@@ -589,6 +592,7 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
     copy_columns<<<flat, 256, 0, st>>>(AX, n, X, ldx);
     count_launch(ctx);
     FL_CUDA(ctx, cudaMemcpyAsync(lambda, ls, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    span.stop();
     int ncl = 0;
     double hs[8];
     FL_CUDA(ctx, cudaMemcpyAsync(&ncl, clist, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -610,6 +614,7 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
       // quadratic step leaves them at rounding level
       converged = (hs[5] <= kConvergedR) && (hs[4] <= kConvergedR * na);
     }
+    span.start(kStageRefineClusters);
     if (ncl > 0) {
       // clusters up to kMaxCluster: batched (gather A X_c, S_c = X_c^T A X_c,
       // Jacobi per CTA, X_c Q_c, scatter); larger ones one by one through the
@@ -665,6 +670,7 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
       double* Qc = Sc + cmax * cmax;
       double* AXb = R;
       double* Xn = S;
+      if (!big.empty()) span.start(kStageRefineBigClusters);
       for (int q : big) {
         const int i0 = cl[2 * q], c = cl[2 * q + 1];
         FL_CHECK(ctx, c <= cmax, FRACLAP_ERR_UNSUPPORTED,
@@ -683,6 +689,7 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
     }
     FL_CUDA(ctx, cudaGetLastError());
   }
+  span.stop();
   if (iters > 0) {  // eigenvalues: Rayleigh quotients of the refined vectors, ascending
     spmm_csr<<<dim3(rows, (unsigned)std::min<int64_t>(n, 4096)), 128, 0, st>>>(n, rowptr, col, val, X, ldx, n, AX, n);
     count_launch(ctx);
