@@ -27,7 +27,6 @@
 namespace fraclap {
 namespace {
 
-constexpr int SB_NT = 256;
 
 __device__ __forceinline__ int64_t sb_nsteps(int64_t s, int64_t n, int b) {
   return (n - 2 - s) / b + 1;  // valid for s <= n - 2
@@ -46,28 +45,76 @@ struct SbArgs {
   long long limit;
 };
 
-template <class T>
-__global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sm = reinterpret_cast<T*>(sm_raw);
-  const int b = a.b, ldb = 2 * b;
-  const int64_t n = a.n;
-  T* xv = sm;                 // b
-  T* F = xv + 64;             // b x b  (F[t + q*b])
-  T* D = F + 64 * 64;         // b x b  full symmetric (D[t + u*b])
-  T* E = D + 64 * 64;         // b x b  (E[t + u*b])
-  T* pw = E + 64 * 64;        // b
-  T* wq = pw + 64;            // b
-  T* ey = wq + 64;            // b
-  __shared__ double s_coef[4];
+// Step of one sweep: thread (t, g) = (tid % B, tid / B) owns row t of the
+// step's blocks and the columns u = g + NG i (i < B / NG) of each: the column
+// block [x | F] (u = 0 is x, u >= 1 the block F to its right), the diagonal
+// block D (symmetric, both triangles) and the block E below it, all in
+// registers.  Sums over t (F^T v) are butterfly reduce-scatters inside a warp,
+// plus one shared-memory add when a row range spans two warps; sums over u
+// (D v, E v) are per-thread partials added across the NG column groups in
+// shared memory.  The block E of step k is [x | F] of step k + 1 (same rows,
+// columns shifted by b), so it stays in the same registers and step k + 1
+// writes it back.
+template <class T, int C, int W>
+__device__ __forceinline__ T sb_reduce_scatter(T (&v)[C], int lane, int* idx) {
+  constexpr int LOGC = (C >= 16) ? 4 : (C >= 8) ? 3 : (C >= 4) ? 2 : (C >= 2) ? 1 : 0;
+  static_assert((1 << LOGC) == C && 2 * C <= W, "column count per thread");
+  int base = 0;
+#pragma unroll
+  for (int j = 0; j < LOGC; ++j) {
+    const int half = C >> (j + 1);
+    const int o = W >> (j + 1);
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int q = 0; q < C / 2; ++q) {
+      if (q < half) {
+        const T send = up ? v[q] : v[q + half];
+        const T keep = up ? v[q + half] : v[q];
+        v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    if (up) base += half;
+  }
+  T r = v[0];
+#pragma unroll
+  for (int o = W / (2 * C); o >= 1; o /= 2) r += __shfl_xor_sync(0xffffffffu, r, o);
+  *idx = base;
+  return r;
+}
+
+template <int B, int NG>
+struct SbShape {
+  static constexpr int C = B / NG;                       // columns per thread
+  static constexpr int NT = (B * NG < 32) ? 32 : B * NG;  // threads
+  static constexpr int W = (B < 32) ? B : 32;            // lanes of one row range in a warp
+  static constexpr int H = B / W;                        // warps one row range spans
+  static constexpr int NW = NT / 32;
+};
+
+template <class T, int B, int NG>
+__global__ void __launch_bounds__(SbShape<B, NG>::NT) sb2st_kernel(SbArgs<T> a) {
+  using Sh = SbShape<B, NG>;
+  constexpr int C = Sh::C, W = Sh::W, H = Sh::H, NW = Sh::NW, LDS = B + 1;
+  __shared__ T Ds[B * LDS];     // transpose of D's lower triangle
+  __shared__ T xs[B];           // the column x
+  __shared__ T red_p[NG][B], red_e[NG][B];
+  __shared__ T wpart[H][B];
+  __shared__ T kpart[NW];
+  __shared__ T wfull[B], eyfull[B], wqfull[B];  // w = p - K v, tau E v, tau F^T v
+  __shared__ double s_hh[3];    // beta, tau, 1 / v0
   __shared__ int s_abort;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool active = tid < B * NG;
+  const int t = tid % B, g = active ? tid / B : 0;
+  const int64_t n = a.n;
+  constexpr int ldb = 2 * B;
   T* band = a.band;
 #define BAND(i, j) band[((i) - (j)) + (int64_t)(j) * ldb]
 
+  T XF[C];
   for (int64_t s = blockIdx.x; s < n - 1; s += gridDim.x) {
-    const int64_t ns = sb_nsteps(s, n, b);
-    const int64_t ns_prev = (s > 0) ? sb_nsteps(s - 1, n, b) : 0;
+    const int64_t ns = sb_nsteps(s, n, B);
+    const int64_t ns_prev = (s > 0) ? sb_nsteps(s - 1, n, B) : 0;
     for (int64_t k = 0; k < ns; ++k) {
       // ---- wait for sweep s-1 to have completed step k+2 ----
       if (tid == 0) {
@@ -84,141 +131,146 @@ __global__ void __launch_bounds__(SB_NT) sb2st_kernel(SbArgs<T> a) {
             }
             __nanosleep(32);
           }
-          __threadfence();
         }
         s_abort = !ok;
       }
       __syncthreads();
       if (s_abort) return;
 
-      const int64_t r0 = s + 1 + k * b;
-      const int L = (int)((n - r0 < b) ? n - r0 : b);
+      const int64_t r0 = s + 1 + k * B;
+      const int L = (int)((n - r0 < B) ? n - r0 : B);
       const int64_t r1 = r0 + L - 1;
-      const int64_t c = (k == 0) ? s : r0 - b;
-      const int nf = (int)(r0 - 1 - c);
-      const int Lb = (int)((n - 1 - r1 < b) ? n - 1 - r1 : b);
+      const int64_t c = (k == 0) ? s : r0 - B;
+      const int nf = (int)(r0 - 1 - c);  // 0 at step 0, b - 1 after
+      const int Lb = (int)((n - 1 - r1 < B) ? n - 1 - r1 : B);
 
-      // ---- load ----
-      for (int t = tid; t < L; t += SB_NT) xv[t] = __ldcg(&BAND(r0 + t, c));
-      for (int p = tid; p < L * nf; p += SB_NT) {
-        const int t = p % L, q = p / L;
-        F[t + q * b] = __ldcg(&BAND(r0 + t, c + 1 + q));
+      // ---- load (all of a thread's loads in flight together) ----
+      if (k == 0) {
+#pragma unroll
+        for (int i = 0; i < C; ++i) XF[i] = T(0);
+        if (active && g == 0 && t < L) XF[0] = __ldcg(&BAND(r0 + t, c));
       }
-      for (int p = tid; p < L * L; p += SB_NT) {
-        const int t = p % L, u = p / L;
-        if (t >= u) {
-          const T v = __ldcg(&BAND(r0 + t, r0 + u));
-          D[t + u * b] = v;
-          D[u + t * b] = v;
-        }
+      T Dr[C], Er[C];
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const int u = g + NG * i;
+        Dr[i] = (active && t < L && u <= t) ? __ldcg(&BAND(r0 + t, r0 + u)) : T(0);
+        Er[i] = (active && t < Lb && u < L) ? __ldcg(&BAND(r1 + 1 + t, r0 + u)) : T(0);
       }
-      for (int p = tid; p < Lb * L; p += SB_NT) {
-        const int t = p % Lb, u = p / Lb;
-        E[t + u * b] = __ldcg(&BAND(r1 + 1 + t, r0 + u));
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const int u = g + NG * i;
+        if (active && u <= t) Ds[u + t * LDS] = Dr[i];
       }
+      if (active && g == 0) xs[t] = XF[0];
       __syncthreads();
-      // ---- Householder vector from x (warp 0), norms and scaling in FP64 ----
-      if (tid < 32) {
+      // ---- Householder scalars (warp 0; norms in FP64) ----
+      if (warp == 0) {
         double tail = 0.0;
-        for (int t = 1 + tid; t < L; t += 32) tail += (double)xv[t] * (double)xv[t];
+        for (int j = 1 + lane; j < B; j += 32) tail += (double)xs[j] * (double)xs[j];
         tail = warp_sum(tail);
-        const double x0 = xv[0];
-        double beta = x0, v0 = 1.0, tu = 0.0;
-        if (tail > 0.0) {
-          const double alpha = sqrt(x0 * x0 + tail);
-          beta = (x0 >= 0.0) ? -alpha : alpha;
-          v0 = x0 - beta;
-          tu = (beta - x0) / beta;
-        }
-        if (tid == 0) {
-          s_coef[0] = beta;
-          s_coef[1] = tu;
-          s_coef[2] = v0;
-        }
-        __syncwarp();
-        const double inv = 1.0 / v0;
-        for (int t = 1 + tid; t < L; t += 32) xv[t] = (tu == 0.0) ? T(0) : (T)((double)xv[t] * inv);
-        if (tid == 0) xv[0] = T(1);
-      }
-      __syncthreads();
-      const double beta = s_coef[0], tu = s_coef[1];
-      const T tuT = (T)tu;
-      T* rv = a.refl + ((int64_t)s * a.kmax + k) * b;
-      for (int t = tid; t < b; t += SB_NT) rv[t] = (t < L) ? xv[t] : T(0);
-      if (tid == 0) a.rtau[s * a.kmax + k] = tu;
-      if (tu != 0.0) {
-        // ---- wq = tau F^T v, pw = tau D v, y = tau E v: 4 threads per dot ----
-        {
-          const int part = tid & 3;
-          const int ntask = nf + L + Lb;
-          // warp-uniform trip count: every lane reaches the shuffles
-          for (int base = 0; base < ntask; base += SB_NT / 4) {
-            const int task = base + (tid >> 2);
-            T acc = T(0);
-            if (task >= ntask) {
-            } else if (task < nf) {
-              const T* col = F + task * b;
-              for (int t = part; t < L; t += 4) acc += xv[t] * col[t];
-            } else if (task < nf + L) {
-              const int t = task - nf;
-              for (int u = part; u < L; u += 4) acc += D[t + u * b] * xv[u];
-            } else {
-              const int t = task - nf - L;
-              for (int u = part; u < L; u += 4) acc += E[t + u * b] * xv[u];
-            }
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            if (part == 0 && task < ntask) {
-              if (task < nf) wq[task] = tuT * acc;
-              else if (task < nf + L) pw[task - nf] = tuT * acc;
-              else ey[task - nf - L] = tuT * acc;
-            }
+        if (lane == 0) {
+          const double x0 = (double)xs[0];
+          double beta = x0, v0 = 1.0, tu = 0.0;
+          if (tail > 0.0) {
+            const double alpha = sqrt(x0 * x0 + tail);
+            beta = (x0 >= 0.0) ? -alpha : alpha;
+            v0 = x0 - beta;
+            tu = (beta - x0) / beta;
           }
+          s_hh[0] = beta;
+          s_hh[1] = tu;
+          s_hh[2] = (tu == 0.0) ? 0.0 : 1.0 / v0;
         }
-        __syncthreads();
-        for (int p = tid; p < L * nf; p += SB_NT) {
-          const int t = p % L, q = p / L;
-          F[t + q * b] -= xv[t] * wq[q];
-        }
-        for (int p = tid; p < Lb * L; p += SB_NT) {
-          const int t = p % Lb, u = p / Lb;
-          E[t + u * b] -= ey[t] * xv[u];
-        }
-        if (tid < 32) {  // K = tau/2 p^T v
-          double pv = 0.0;
-          for (int t = tid; t < L; t += 32) pv += (double)pw[t] * (double)xv[t];
-          pv = warp_sum(pv);
-          if (tid == 0) s_coef[3] = 0.5 * tu * pv;
-        }
-        __syncthreads();
-        const T K = (T)s_coef[3];
-        for (int t = tid; t < L; t += SB_NT) pw[t] -= K * xv[t];  // w = p - K v
-        __syncthreads();
-        for (int p = tid; p < L * L; p += SB_NT) {
-          const int t = p % L, u = p / L;
-          if (t >= u) D[t + u * b] -= xv[t] * pw[u] + pw[t] * xv[u];
-        }
-        __syncthreads();
-        // ---- store ----
-        for (int t = tid; t < L; t += SB_NT) __stcg(&BAND(r0 + t, c), (t == 0) ? (T)beta : T(0));
-        for (int p = tid; p < L * nf; p += SB_NT) {
-          const int t = p % L, q = p / L;
-          __stcg(&BAND(r0 + t, c + 1 + q), F[t + q * b]);
-        }
-        for (int p = tid; p < L * L; p += SB_NT) {
-          const int t = p % L, u = p / L;
-          if (t >= u) __stcg(&BAND(r0 + t, r0 + u), D[t + u * b]);
-        }
-        for (int p = tid; p < Lb * L; p += SB_NT) {
-          const int t = p % Lb, u = p / Lb;
-          __stcg(&BAND(r1 + 1 + t, r0 + u), E[t + u * b]);
-        }
+      }
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const int u = g + NG * i;
+        if (active && u > t) Dr[i] = Ds[t + u * LDS];  // upper triangle from the transpose
       }
       __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        st_release_gpu(a.progress + s, (int)(k + 1));
+      const double tu = s_hh[1];
+      const T inv = (T)s_hh[2];
+      const T vt = (t == 0) ? T(1) : xs[t] * inv;  // v, with v(0) = 1
+      T vu[C];
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const int u = g + NG * i;
+        vu[i] = (u == 0) ? T(1) : xs[u] * inv;
       }
+      if (active && g == 0) a.refl[((int64_t)s * a.kmax + k) * B + t] = vt;
+      if (tid == 0) a.rtau[s * a.kmax + k] = tu;
+      // ---- partial sums: F^T v (over rows), D v and E v (over columns), v^T D v ----
+      {
+        T pv[C];
+#pragma unroll
+        for (int i = 0; i < C; ++i) pv[i] = vt * XF[i];
+        int idx;
+        const T cs = sb_reduce_scatter<T, C, W>(pv, lane, &idx);
+        if (active && (lane & (W / C - 1)) == 0) wpart[(t / W) % H][g + NG * idx] = cs;
+      }
+      T pp = T(0), ep = T(0);
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        pp += Dr[i] * vu[i];
+        ep += Er[i] * vu[i];
+      }
+      if (active) {
+        red_p[g][t] = pp;
+        red_e[g][t] = ep;
+      }
+      {
+        T kk = active ? vt * pp : T(0);
+#pragma unroll
+        for (int o = 16; o >= 1; o /= 2) kk += __shfl_xor_sync(0xffffffffu, kk, o);
+        if (lane == 0) kpart[warp] = kk;
+      }
+      __syncthreads();
+      // ---- full sums, once per row / column ----
+      if (tid < B) {
+        const T tuT = (T)tu;
+        T ksum = T(0);
+#pragma unroll
+        for (int q = 0; q < NW; ++q) ksum += kpart[q];
+        const T K = T(0.5) * tuT * tuT * ksum;  // tau/2 p^T v with p = tau D v
+        const T vj = (tid == 0) ? T(1) : xs[tid] * inv;
+        T ps = T(0), es = T(0), cs = T(0);
+#pragma unroll
+        for (int q = 0; q < NG; ++q) {
+          ps += red_p[q][tid];
+          es += red_e[q][tid];
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h) cs += wpart[h][tid];
+        wfull[tid] = tuT * ps - K * vj;
+        eyfull[tid] = tuT * es;
+        wqfull[tid] = tuT * cs;
+      }
+      __syncthreads();
+      // ---- rank-one and rank-two updates in registers ----
+      const T wt = wfull[t], eyt = eyfull[t];
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const int u = g + NG * i;
+        XF[i] -= vt * wqfull[u];
+        if (u <= t) Dr[i] -= vt * wfull[u] + wt * vu[i];  // only the stored triangle
+        Er[i] -= eyt * vu[i];
+      }
+      // ---- store x (annihilated), F and D's lower triangle; E moves on ----
+      if (active && t < L) {
+        const T beta = (T)s_hh[0];
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+          const int u = g + NG * i;
+          if (u == 0) __stcg(&BAND(r0 + t, c), (t == 0) ? beta : T(0));
+          else if (u <= nf) __stcg(&BAND(r0 + t, c + u), XF[i]);
+          if (u <= t) __stcg(&BAND(r0 + t, r0 + u), Dr[i]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < C; ++i) XF[i] = Er[i];
+      __syncthreads();
+      if (tid == 0) st_release_gpu(a.progress + s, (int)(k + 1));  // orders the CTA's stores (after the barrier)
     }
   }
 #undef BAND
@@ -390,6 +442,20 @@ int stage2_take(Arena* ar, int64_t n, int b, Stage2T<T>* s) {
   return 0;
 }
 
+template <class T, int B, int NG>
+int sb2st_launch(fraclap_ctx* ctx, SbArgs<T> a, cudaStream_t st) {
+  constexpr int NT = SbShape<B, NG>::NT;
+  int per_sm = 0;
+  FL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sb2st_kernel<T, B, NG>, NT, 0));
+  FL_CHECK(ctx, per_sm >= 1, FRACLAP_ERR_UNSUPPORTED, "sb2st: kernel does not fit on an SM");
+  int64_t G = (int64_t)ctx->sm_count * per_sm;
+  if (G > a.n - 1) G = a.n - 1;
+  void* args[] = {&a};
+  count_launch(ctx);
+  FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)sb2st_kernel<T, B, NG>, dim3((unsigned)G), dim3(NT), args, 0, st));
+  return 0;
+}
+
 template <class T>
 int sb2st_run(fraclap_ctx* ctx, T* band, int64_t n, int b, double* d, double* e, Stage2T<T>* s,
               cudaStream_t st) {
@@ -397,16 +463,16 @@ int sb2st_run(fraclap_ctx* ctx, T* band, int64_t n, int b, double* d, double* e,
     FL_CUDA(ctx, cudaMemsetAsync(s->progress, 0, sizeof(int) * (n + 1), st));
     FL_CUDA(ctx, cudaMemsetAsync(s->rtau, 0, sizeof(double) * (n - 1) * s->kmax, st));
     SbArgs<T> a{band, n, b, s->kmax, s->refl, s->rtau, s->progress, ctx->d_status, ctx->wait_cycles};
-    const size_t smem = sizeof(T) * (64 + 3 * 64 * 64 + 3 * 64);
-    FL_CUDA(ctx, cudaFuncSetAttribute(sb2st_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    FL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sb2st_kernel<T>, SB_NT, smem));
-    FL_CHECK(ctx, per_sm >= 1, FRACLAP_ERR_UNSUPPORTED, "sb2st: kernel does not fit on an SM");
-    int64_t G = (int64_t)ctx->sm_count * per_sm;
-    if (G > n - 1) G = n - 1;
-    void* args[] = {&a};
-    count_launch(ctx);
-    FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)sb2st_kernel<T>, dim3((unsigned)G), dim3(SB_NT), args, smem, st));
+    int rc = 0;
+    switch (b) {
+      case 4: rc = sb2st_launch<T, 4, 4>(ctx, a, st); break;
+      case 8: rc = sb2st_launch<T, 8, 4>(ctx, a, st); break;
+      case 16: rc = sb2st_launch<T, 16, 4>(ctx, a, st); break;
+      case 32: rc = sb2st_launch<T, 32, 4>(ctx, a, st); break;
+      case 64: rc = sb2st_launch<T, 64, 4>(ctx, a, st); break;
+      default: FL_CHECK(ctx, false, FRACLAP_ERR_UNSUPPORTED, "sb2st: band width %d", b);
+    }
+    if (rc) return rc;
   }
   if (n >= 1) {
     band_diagonals<T><<<(unsigned)cdiv(n, 256), 256, 0, st>>>(band, 2 * b, n, d, e);
