@@ -60,20 +60,37 @@ __global__ void row_exponents(const double* A, int64_t lda, bool trans, int64_t 
 
 // Slices of op(A) (M x K): S[p][i][k] (k contiguous, Kp >= K, zero padded).
 // One thread per (i, k); i fastest when A is not transposed (coalesced reads).
+// Slice p is the signed integer trunc(x 2^(w(p+1))) - 2^w trunc(x 2^(w p))
+// of x = a 2^-e (|x| < 1): the w-bit digits of |x| with the sign of x.  When
+// all s w bits fit in 64, |x| 2^(w s) is truncated once to an unsigned
+// integer (exact: a power-of-two scaling, then a truncating conversion) and
+// the digits are read off with shifts; otherwise the digits are peeled in
+// FP64, which gives the same digits.
 __global__ void make_slices(const double* A, int64_t lda, bool trans, int64_t M, int64_t K,
                             int64_t Kp, const int* ex, int s, int bits, __nv_bfloat16* S) {
   const int64_t total = M * Kp;
+  const int tb = bits * s;
+  const unsigned long long mask = (1ull << bits) - 1ull;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     int64_t i, k;
     if (trans) { k = t % Kp; i = t / Kp; } else { i = t % M; k = t / M; }
-    double x = 0.0;
-    if (k < K) x = ldexp(trans ? A[k + i * lda] : A[i + k * lda], -ex[i]);
-    for (int p = 0; p < s; ++p) {
-      const double y = ldexp(x, bits);
-      const double q = trunc(y);
-      S[((int64_t)p * M + i) * Kp + k] = __float2bfloat16_rn((float)q);
-      x = y - q;
+    const double a = (k < K) ? (trans ? A[k + i * lda] : A[i + k * lda]) : 0.0;
+    if (tb <= 64) {
+      const unsigned long long u = __double2ull_rz(ldexp(fabs(a), tb - ex[i]));
+      const float sg = (a < 0.0) ? -1.0f : 1.0f;
+      for (int p = 0; p < s; ++p) {
+        const unsigned long long dgt = (u >> (bits * (s - 1 - p))) & mask;
+        S[((int64_t)p * M + i) * Kp + k] = __float2bfloat16_rn(sg * (float)dgt);
+      }
+    } else {
+      double x = ldexp(a, -ex[i]);
+      for (int p = 0; p < s; ++p) {
+        const double y = ldexp(x, bits);
+        const double q = trunc(y);
+        S[((int64_t)p * M + i) * Kp + k] = __float2bfloat16_rn((float)q);
+        x = y - q;
+      }
     }
   }
 }
@@ -183,15 +200,18 @@ ozaki_kernel(const __nv_bfloat16* __restrict__ SA, const __nv_bfloat16* __restri
 
 
 // ----------------------------------------------------------------------------
-// tcgen05 route: CTA tile 128 (rows of op(A)) x 64 (columns of op(B)).
-// Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 2-5:
-// epilogue (TMEM lanes 32 (w % 4) ..), each thread one output row.
+// tcgen05 route: CTA tile 128 (rows of op(A)) x 128 (columns of op(B)).
+// Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 2-9:
+// epilogue, two warps per TMEM lane quarter (lanes 32 (w % 4) ..), each
+// thread one output row and 64 of the 128 columns.  Six 32 KB stages keep
+// enough bytes in flight to cover the L2 latency.
 // ----------------------------------------------------------------------------
-constexpr int TC_M = 128, TC_N = 64, TC_KB = 64, TC_STAGES = 4;
+constexpr int TC_M = 128, TC_N = 128, TC_KB = 64, TC_STAGES = 6;
 constexpr int TC_A_BYTES = TC_M * TC_KB * 2, TC_B_BYTES = TC_N * TC_KB * 2;
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
-constexpr int TC_THREADS = 192;
-constexpr uint32_t TC_TMEM_COLS = 128;  // two 64-column FP32 accumulators
+constexpr int TC_EPI_WARPS = 8, TC_EPI_COLS = TC_N * 4 / TC_EPI_WARPS;
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
+constexpr uint32_t TC_TMEM_COLS = 2 * TC_N;  // two FP32 accumulators
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -248,7 +268,7 @@ __device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
   d |= (uint64_t)2 << 61;            // 128-byte swizzle
   return d;
 }
-// kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, M 128, N 64.
+// kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, M 128, N 128.
 constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                               ((uint32_t)(TC_M >> 4) << 24);
 __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
@@ -269,6 +289,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
                : "r"(taddr)
                : "memory");
 }
+// 2^e for e in [-1022, 1023], from its bit pattern.
+__device__ __forceinline__ double pow2i(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -295,7 +317,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 4);
+      mbar_init(&acc_empty[i], TC_EPI_WARPS);
     }
     mbar_init(&done_bar, 1);
     abort_sh = 0;
@@ -319,9 +341,10 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int p = 0; p < s && ok; ++p)
-        for (int q = 0; p + q < s && ok; ++q)
+      for (int dg = 0; dg < s && ok; ++dg)
+        for (int p = 0; p <= dg && ok; ++p)
           for (int c = 0; c < nchunk && ok; ++c) {
+            const int q = dg - p;
             const int64_t c0 = (int64_t)c * chunk;
             const int nkb = (int)(((Kp - c0) < chunk ? (Kp - c0) : chunk) / TC_KB);
             for (int kb = 0; kb < nkb; ++kb, ++it) {
@@ -351,8 +374,8 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     if (lane == 0) {
       int it = 0, chunk_i = 0;
       bool ok = true;
-      for (int p = 0; p < s && ok; ++p)
-        for (int q = 0; p + q < s && ok; ++q)
+      for (int dg = 0; dg < s && ok; ++dg)
+        for (int p = 0; p <= dg && ok; ++p)
           for (int c = 0; c < nchunk && ok; ++c, ++chunk_i) {
             const int buf = chunk_i & 1;
             if (!mbar_wait(&acc_empty[buf], ((chunk_i >> 1) & 1) ^ 1, limit) || *(volatile int*)&abort_sh) {
@@ -388,17 +411,53 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       mbar_wait(&done_bar, 0, limit);
     }
   } else {
-    // ---------------- epilogue: FP64 folding ----------------
-    const int lg = warp & 3;                 // TMEM lane group of this warp
-    const int64_t row = m0 + lg * 32 + lane;  // output row of this thread
-    double sum[TC_N];
+    // ---------------- epilogue: exact integer sums, FP64 once per diagonal ----------------
+    // Pairs are visited by diagonal p + q, which share one scale.  A chunk
+    // sum is an integer below 2^24 (exact in FP32), so it converts exactly
+    // to int32; up to 127 of them add exactly in an int32 accumulator, which
+    // is scaled (exactly, by a power of two) and added into C in FP64 at the
+    // end of the diagonal (or after 127 chunks).
+    const int lg = warp & 3;                          // TMEM lane quarter of this warp
+    const int cbase = ((warp - 2) >> 2) * TC_EPI_COLS;  // this warp's columns of the tile
+    const int64_t row = m0 + lg * 32 + lane;          // output row of this thread
+    const int er = (row < M) ? ea[row] : 0;
+    int acc[TC_EPI_COLS];
 #pragma unroll
-    for (int j = 0; j < TC_N; ++j) sum[j] = 0.0;
+    for (int j = 0; j < TC_EPI_COLS; ++j) acc[j] = 0;
+    bool first = true;
+    auto fold = [&](int dg) {
+      const int sh = bits * (dg + 2);
+      if (row < M) {
+        // opaque copies of the base pointers: the per-column addresses are
+        // formed here, not hoisted out of the diagonal loop into registers
+        const int* ebp;
+        double* cb;
+        asm volatile("mov.b64 %0, %1;" : "=l"(ebp) : "l"(eb + n0 + cbase));
+        asm volatile("mov.b64 %0, %1;" : "=l"(cb) : "l"(C + row + (n0 + cbase) * ldc));
+#pragma unroll
+        for (int j = 0; j < TC_EPI_COLS; ++j) {
+          const int64_t col = n0 + cbase + j;
+          if (col < N && !(lower && row < col)) {
+            // acc 2^e in two exact power-of-two steps (each factor normal);
+            // beyond |e| = 2044 the result is 0 or infinite either way
+            int e = er + ebp[j] - sh;
+            e = (e < -2044) ? -2044 : (e > 2044 ? 2044 : e);
+            const int e1 = e / 2;
+            const double v = alpha * (((double)acc[j] * pow2i(e1)) * pow2i(e - e1));
+            double* cp = cb + j * ldc;
+            *cp = first ? ((beta == 0.0) ? v : v + beta * *cp) : *cp + v;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < TC_EPI_COLS; ++j) acc[j] = 0;
+      first = false;
+    };
     int chunk_i = 0;
     bool ok = true;
-    for (int p = 0; p < s && ok; ++p)
-      for (int q = 0; p + q < s && ok; ++q) {
-        const double scale = ldexp(1.0, -bits * (p + q + 2));
+    for (int dg = 0; dg < s && ok; ++dg) {
+      int pending = 0;
+      for (int p = 0; p <= dg && ok; ++p) {
         for (int c = 0; c < nchunk; ++c, ++chunk_i) {
           const int buf = chunk_i & 1;
           if (!mbar_wait(&acc_full[buf], (chunk_i >> 1) & 1, limit) || *(volatile int*)&abort_sh) {
@@ -406,33 +465,29 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             break;
           }
           tc_fence_after();
-          const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * TC_N);
+          const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(buf * TC_N + cbase);
 #pragma unroll
-          for (int j0 = 0; j0 < TC_N; j0 += 16) {
+          for (int j0 = 0; j0 < TC_EPI_COLS; j0 += 16) {
             uint32_t r[16];
             tmem_ld16(taddr + j0, r);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) sum[j0 + j] = fma((double)__uint_as_float(r[j]), scale, sum[j0 + j]);
+            for (int j = 0; j < 16; ++j) acc[j0 + j] += __float2int_rz(__uint_as_float(r[j]));
           }
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[buf]);
+          if (++pending == 127) {
+            fold(dg);
+            pending = 0;
+          }
         }
       }
+      if (ok) fold(dg);
+    }
     if (!ok) {
       if (lane == 0) atomicCAS(status, 0, FRACLAP_ERR_TIMEOUT);
       abort_sh = 1;
-    } else if (row < M) {
-      const int er = ea[row];
-#pragma unroll
-      for (int j = 0; j < TC_N; ++j) {
-        const int64_t col = n0 + j;
-        if (col >= N || (lower && row < col)) continue;
-        const double v = ldexp(sum[j], er + eb[col]);
-        double* cp = C + row + col * ldc;
-        *cp = (beta == 0.0) ? alpha * v : alpha * v + beta * *cp;
-      }
     }
   }
   tc_fence_before();

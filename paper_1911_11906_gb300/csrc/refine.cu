@@ -311,84 +311,227 @@ constexpr double kConvergedR = 3e-9;
 constexpr int kRefineSlices = 7;
 
 __device__ void cluster_jacobi_body(const double* Sc, int c, double* Q, double* w, int32_t* status) {
+  // Parallel-order Jacobi: each round applies c/2 disjoint rotations at
+  // once (round-robin pairing; for odd c one index sits out each round), a
+  // sweep is c - 1 (c even) or c rounds and visits every pair once.
   __shared__ double a[kMaxCluster][kMaxCluster + 1];
   __shared__ double q[kMaxCluster][kMaxCluster + 1];
-  __shared__ double rot[2];
+  __shared__ double rc[kMaxCluster / 2], rs[kMaxCluster / 2];
+  __shared__ int rp[kMaxCluster / 2], rq[kMaxCluster / 2];
+  __shared__ double red[2][32];
   __shared__ int s_done;
-  const int tid = threadIdx.x;
-  for (int p = tid; p < c * c; p += blockDim.x) {
+  __shared__ int perm[kMaxCluster];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int p = tid; p < c * c; p += nt) {
     const int i = p % c, j = p / c;
     a[i][j] = 0.5 * (Sc[i + j * c] + Sc[j + i * c]);
     q[i][j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
+  const int m = c + (c & 1);  // players; index c is a bye when c is odd
+  const int np = m / 2;
   for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0, fro = 0.0;
+    for (int p = tid; p < c * c; p += nt) {
+      const int i = p % c, j = p / c;
+      const double v = a[i][j] * a[i][j];
+      fro += v;
+      if (i != j) off += v;
+    }
+    off = warp_sum(off);
+    fro = warp_sum(fro);
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = off;
+      red[1][tid >> 5] = fro;
+    }
+    __syncthreads();
     if (tid == 0) {
-      double off = 0.0, fro = 0.0;
-      for (int i = 0; i < c; ++i)
-        for (int j = 0; j < c; ++j) {
-          fro += a[i][j] * a[i][j];
-          if (i != j) off += a[i][j] * a[i][j];
-        }
-      s_done = (off <= 1e-30 * fro) || fro == 0.0;
+      double o = 0.0, f = 0.0;
+      for (int u = 0; u < nt / 32; ++u) {
+        o += red[0][u];
+        f += red[1][u];
+      }
+      s_done = (o <= 1e-30 * f) || f == 0.0;
     }
     __syncthreads();
     if (s_done) break;
-    for (int pi = 0; pi + 1 < c; ++pi)
-      for (int qi = pi + 1; qi < c; ++qi) {
+    for (int r = 0; r + 1 < m; ++r) {
+      if (tid < np) {
+        int p, qq;
         if (tid == 0) {
-          const double apq = a[pi][qi];
-          double cs = 1.0, sn = 0.0;
-          if (fabs(apq) > 1e-18 * (fabs(a[pi][pi]) + fabs(a[qi][qi]))) {
-            const double theta = (a[qi][qi] - a[pi][pi]) / (2.0 * apq);
+          p = r;
+          qq = m - 1;
+        } else {
+          p = (r + tid) % (m - 1);
+          qq = (r - tid + (m - 1)) % (m - 1);
+        }
+        if (p > qq) {
+          const int tmp = p;
+          p = qq;
+          qq = tmp;
+        }
+        double cs = 1.0, sn = 0.0;
+        if (qq < c) {
+          const double apq = a[p][qq];
+          if (fabs(apq) > 1e-18 * (fabs(a[p][p]) + fabs(a[qq][qq]))) {
+            const double theta = (a[qq][qq] - a[p][p]) / (2.0 * apq);
             const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
             cs = 1.0 / sqrt(t * t + 1.0);
             sn = t * cs;
           }
-          rot[0] = cs;
-          rot[1] = sn;
         }
-        __syncthreads();
-        const double cs = rot[0], sn = rot[1];
-        if (sn != 0.0) {
-          if (tid < c) {  // columns pi, qi
-            const double xp = a[tid][pi], xq = a[tid][qi];
-            a[tid][pi] = cs * xp - sn * xq;
-            a[tid][qi] = sn * xp + cs * xq;
-            const double vp = q[tid][pi], vq = q[tid][qi];
-            q[tid][pi] = cs * vp - sn * vq;
-            q[tid][qi] = sn * vp + cs * vq;
-          }
-          __syncthreads();
-          if (tid < c) {  // rows pi, qi
-            const double xp = a[pi][tid], xq = a[qi][tid];
-            a[pi][tid] = cs * xp - sn * xq;
-            a[qi][tid] = sn * xp + cs * xq;
-          }
-        }
-        __syncthreads();
+        rp[tid] = p;
+        rq[tid] = qq;
+        rc[tid] = cs;
+        rs[tid] = sn;
       }
+      __syncthreads();
+      for (int e = tid; e < np * c; e += nt) {  // columns p, q of A and of Q
+        const int k = e / c, i = e % c;
+        const double sn = rs[k];
+        if (sn != 0.0) {
+          const int p = rp[k], qq = rq[k];
+          const double cs = rc[k];
+          const double xp = a[i][p], xq = a[i][qq];
+          a[i][p] = cs * xp - sn * xq;
+          a[i][qq] = sn * xp + cs * xq;
+          const double vp = q[i][p], vq = q[i][qq];
+          q[i][p] = cs * vp - sn * vq;
+          q[i][qq] = sn * vp + cs * vq;
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < np * c; e += nt) {  // rows p, q of A
+        const int k = e / c, j = e % c;
+        const double sn = rs[k];
+        if (sn != 0.0) {
+          const int p = rp[k], qq = rq[k];
+          const double cs = rc[k];
+          const double xp = a[p][j], xq = a[qq][j];
+          a[p][j] = cs * xp - sn * xq;
+          a[qq][j] = sn * xp + cs * xq;
+        }
+      }
+      __syncthreads();
+    }
     if (sweep == 49 && tid == 0) raise_status(status, FRACLAP_ERR_NO_CONVERGENCE);
   }
   // ascending order (selection by thread 0), then write out
-  __shared__ int perm[kMaxCluster];
   if (tid == 0) {
     for (int i = 0; i < c; ++i) perm[i] = i;
     for (int i = 0; i + 1 < c; ++i) {
-      int m = i;
+      int mm = i;
       for (int j = i + 1; j < c; ++j)
-        if (a[perm[j]][perm[j]] < a[perm[m]][perm[m]]) m = j;
+        if (a[perm[j]][perm[j]] < a[perm[mm]][perm[mm]]) mm = j;
       const int t = perm[i];
-      perm[i] = perm[m];
-      perm[m] = t;
+      perm[i] = perm[mm];
+      perm[mm] = t;
     }
   }
   __syncthreads();
-  for (int p = tid; p < c * c; p += blockDim.x) {
+  for (int p = tid; p < c * c; p += nt) {
     const int i = p % c, j = p / c;
     Q[i + j * c] = q[i][perm[j]];
   }
   if (tid < c) w[tid] = a[perm[tid]][perm[tid]];
+}
+
+// S_q += X_q^T (A X_q) over the row range of blockIdx.y (of gridDim.y), for
+// every small cluster q (cinfo: size, first column, offset of its columns in
+// AXc).  One CTA per (cluster, row range); rows are staged 32 at a time and
+// the work is n c^2 per cluster.  S_q (ld c) must be zero on entry.
+constexpr int kGramThreads = 256;
+__global__ void __launch_bounds__(kGramThreads) cluster_gram(const double* X, int64_t ldx, const double* AXc,
+                                                             int64_t n, const int* cinfo, double* Sall) {
+  constexpr int RB = 32, NT = kGramThreads, MO = kMaxCluster * kMaxCluster / NT;
+  __shared__ double xs[RB][kMaxCluster + 1], ys[RB][kMaxCluster + 1];
+  __shared__ double red[NT];
+  const int q = blockIdx.x, tid = threadIdx.x;
+  const int c = cinfo[3 * q], i0 = cinfo[3 * q + 1], off = cinfo[3 * q + 2];
+  const int P = c * c;
+  const int groups = (P >= NT) ? 1 : NT / P;
+  const int64_t rows = (n + gridDim.y - 1) / gridDim.y;
+  const int64_t rbeg = (int64_t)blockIdx.y * rows;
+  const int64_t rend = (rbeg + rows < n) ? rbeg + rows : n;
+  double acc[MO];
+#pragma unroll
+  for (int mo = 0; mo < MO; ++mo) acc[mo] = 0.0;
+  for (int64_t r0 = rbeg; r0 < rend; r0 += RB) {
+    for (int e = tid; e < RB * c; e += NT) {
+      const int rr = e % RB, cc = e / RB;
+      const int64_t r = r0 + rr;
+      xs[rr][cc] = (r < rend) ? X[r + (int64_t)(i0 + cc) * ldx] : 0.0;
+      ys[rr][cc] = (r < rend) ? AXc[r + (int64_t)(off + cc) * n] : 0.0;
+    }
+    __syncthreads();
+    if (groups > 1) {
+      if (tid < groups * P) {
+        const int o = tid % P, gr = tid / P, i = o % c, j = o / c;
+        double sum = acc[0];
+        for (int rr = gr; rr < RB; rr += groups) sum = fma(xs[rr][i], ys[rr][j], sum);
+        acc[0] = sum;
+      }
+    } else {
+#pragma unroll
+      for (int mo = 0; mo < MO; ++mo) {
+        const int o = tid + NT * mo;
+        if (o < P) {
+          const int i = o % c, j = o / c;
+          double sum = acc[mo];
+#pragma unroll 8
+          for (int rr = 0; rr < RB; ++rr) sum = fma(xs[rr][i], ys[rr][j], sum);
+          acc[mo] = sum;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  double* S = Sall + (int64_t)q * kMaxCluster * kMaxCluster;
+  if (groups > 1) {
+    red[tid] = (tid < groups * P) ? acc[0] : 0.0;
+    __syncthreads();
+    if (tid < P) {
+      double sum = 0.0;
+      for (int gr = 0; gr < groups; ++gr) sum += red[tid + gr * P];
+      atomicAdd(S + tid, sum);  // o = i + j c
+    }
+  } else {
+#pragma unroll
+    for (int mo = 0; mo < MO; ++mo) {
+      const int o = tid + NT * mo;
+      if (o < P) atomicAdd(S + o, acc[mo]);
+    }
+  }
+}
+
+// X_q <- X_q Q_q in place for every small cluster q; one CTA per (64 rows,
+// cluster): the rows are staged in shared memory, so each thread reads only
+// staged values before it writes its outputs.
+__global__ void __launch_bounds__(256) cluster_rotate(double* X, int64_t ldx, int64_t n, const int* cinfo,
+                                                      const double* Qall) {
+  constexpr int RB = 64;
+  __shared__ double xs[RB][kMaxCluster + 1];
+  __shared__ double qs[kMaxCluster][kMaxCluster + 1];
+  const int q = blockIdx.y, tid = threadIdx.x;
+  const int c = cinfo[3 * q], i0 = cinfo[3 * q + 1];
+  const int64_t r0 = (int64_t)blockIdx.x * RB;
+  const double* Qq = Qall + (int64_t)q * kMaxCluster * kMaxCluster;
+  for (int e = tid; e < RB * c; e += 256) {
+    const int rr = e % RB, cc = e / RB;
+    const int64_t r = r0 + rr;
+    xs[rr][cc] = (r < n) ? X[r + (int64_t)(i0 + cc) * ldx] : 0.0;
+  }
+  for (int e = tid; e < c * c; e += 256) qs[e % c][e / c] = Qq[e];
+  __syncthreads();
+  const int rr = tid % RB, part = tid / RB;
+  const int64_t r = r0 + rr;
+  if (r < n) {
+    for (int j = part; j < c; j += 256 / RB) {
+      double sum = 0.0;
+      for (int i = 0; i < c; ++i) sum = fma(xs[rr][i], qs[i][j], sum);
+      X[r + (int64_t)(i0 + j) * ldx] = sum;
+    }
+  }
 }
 
 // AXc(:, t) = A X(:, src[t]) for the concatenated cluster columns t < T.
@@ -404,14 +547,6 @@ __global__ void spmm_csr_cols(int64_t n, const int64_t* __restrict__ rowptr,
     for (int64_t p = p0; p < p1; ++p) s = fma(val[p], x[col[p]], s);
     Y[i + t * n] = s;
   }
-}
-
-// X(:, src[t]) = Y(:, t).
-__global__ void scatter_columns(const double* Y, int64_t n, const int* src, int64_t T, double* X,
-                                int64_t ldx) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t t = blockIdx.y;
-  if (i < n && t < T) X[i + (int64_t)src[t] * ldx] = Y[i + t * n];
 }
 
 // One CTA per cluster: cinfo[3q] = size, cinfo[3q+1] = first sorted position;
@@ -460,12 +595,10 @@ __global__ void rayleigh(const double* X, int64_t ldx, const double* AX, int64_t
 constexpr int64_t kMaxBigCluster = 65535;
 
 // Scratch of the batched small-cluster step: S_q and Q_q (64 x 64 each) for
-// up to n/2 + 1 clusters, the column map, the cluster table and the GEMM
-// descriptors.
+// up to n/2 + 1 clusters, the column map and the cluster table.
 static int64_t small_cluster_doubles(int64_t n) {
   const int64_t ns = n / 2 + 1;
-  return 2 * ns * kMaxCluster * kMaxCluster + (n + 64) / 2 + (3 * ns + 64) / 2 + 64 +
-         (int64_t)(2 * ns * sizeof(GemmDescT<double>) + 7) / 8;
+  return 2 * ns * kMaxCluster * kMaxCluster + (n + 64) / 2 + (3 * ns + 64) / 2 + 64;
 }
 
 size_t refine_ws(const fraclap_ctx* ctx, int64_t n) {
@@ -620,48 +753,36 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
       // Jacobi per CTA, X_c Q_c, scatter); larger ones one by one through the
       // dense FP64 eigensolver.
       std::vector<int> src, cinfo;
-      std::vector<D64> dS, dQ;
       int64_t T = 0;
       double* AXc = R;                      // n x T (R and S are free here)
-      double* Ycat = S;                     // n x T
       double* Sall = sbuf;                  // nsmall x 64 x 64
       std::vector<int> big;
       for (int q = 0; q < ncl; ++q) {
         const int i0 = cl[2 * q], c = cl[2 * q + 1];
         if (c > kMaxCluster) { big.push_back(q); continue; }
-        const int64_t qi = (int64_t)cinfo.size() / 3;
         cinfo.push_back(c);
         cinfo.push_back(i0);
         cinfo.push_back((int)T);
         for (int t = 0; t < c; ++t) src.push_back(i0 + t);
-        dS.push_back(D64{c, c, n, X + (int64_t)i0 * ldx, ldx, AXc + T * n, n, Sall + qi * kMaxCluster * kMaxCluster, c,
-                         nullptr, 0, nullptr, 0, 0, 1.0, 0.0});
         T += c;
       }
       const int64_t ns = (int64_t)cinfo.size() / 3;
       if (ns > 0) {
         double* Qall = Sall + ns * kMaxCluster * kMaxCluster;
-        for (int64_t qi = 0; qi < ns; ++qi) {
-          const int c = cinfo[3 * qi], i0 = cinfo[3 * qi + 1], off = cinfo[3 * qi + 2];
-          dQ.push_back(D64{n, c, c, X + (int64_t)i0 * ldx, ldx, Qall + qi * kMaxCluster * kMaxCluster, c,
-                           Ycat + (int64_t)off * n, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0});
-        }
         int* d_src = reinterpret_cast<int*>(Qall + ns * kMaxCluster * kMaxCluster);
         int* d_cinfo = d_src + ((T + 63) / 64) * 64;
-        D64* d_desc = reinterpret_cast<D64*>(d_cinfo + ((3 * ns + 63) / 64) * 64);
         FL_CUDA(ctx, cudaMemcpyAsync(d_src, src.data(), sizeof(int) * T, cudaMemcpyHostToDevice, st));
         FL_CUDA(ctx, cudaMemcpyAsync(d_cinfo, cinfo.data(), sizeof(int) * 3 * ns, cudaMemcpyHostToDevice, st));
-        FL_CUDA(ctx, cudaMemcpyAsync(d_desc, dS.data(), sizeof(D64) * ns, cudaMemcpyHostToDevice, st));
-        FL_CUDA(ctx, cudaMemcpyAsync(d_desc + ns, dQ.data(), sizeof(D64) * ns, cudaMemcpyHostToDevice, st));
         FL_CHECK(ctx, ns <= 65535 && T <= 65535, FRACLAP_ERR_UNSUPPORTED, "refine: too many clustered columns");
         spmm_csr_cols<<<dim3(rows, (unsigned)std::min<int64_t>(T, 4096)), 128, 0, st>>>(n, rowptr, col, val, X, ldx,
                                                                                        d_src, T, AXc);
         count_launch(ctx);
-        FL_TRY(gemm_batched<double>(ctx, true, false, d_desc, (int)ns, kMaxCluster, kMaxCluster, st));
-        cluster_jacobi_batched<<<(unsigned)ns, 64, 0, st>>>(Sall, d_cinfo, Qall, lambda, ctx->d_status);
+        FL_CUDA(ctx, cudaMemsetAsync(Sall, 0, sizeof(double) * ns * kMaxCluster * kMaxCluster, st));
+        cluster_gram<<<dim3((unsigned)ns, 4), kGramThreads, 0, st>>>(X, ldx, AXc, n, d_cinfo, Sall);
         count_launch(ctx);
-        FL_TRY(gemm_batched<double>(ctx, false, false, d_desc + ns, (int)ns, n, kMaxCluster, st));
-        scatter_columns<<<dim3((unsigned)cdiv(n, 256), (unsigned)T), 256, 0, st>>>(Ycat, n, d_src, T, X, ldx);
+        cluster_jacobi_batched<<<(unsigned)ns, 256, 0, st>>>(Sall, d_cinfo, Qall, lambda, ctx->d_status);
+        count_launch(ctx);
+        cluster_rotate<<<dim3((unsigned)cdiv(n, 64), (unsigned)ns), 256, 0, st>>>(X, ldx, n, d_cinfo, Qall);
         count_launch(ctx);
         // the host vectors must outlive the asynchronous copies
         FL_CUDA(ctx, cudaStreamSynchronize(st));
