@@ -250,7 +250,7 @@ int fraclap_refine_stats(const fraclap_ctx* ctx, double* out, int max_values);
 long long fraclap_launch_count(const fraclap_ctx* ctx);
 
 /* Refinement safeguard of eig_full_mixed: a pair whose first-order
- * correction coefficient exceeds tau (default 3e-3) is treated as part of a
+ * correction coefficient exceeds tau (default 1e-3) is treated as part of a
  * cluster and diagonalised exactly; 0 < tau <= 1. */
 int fraclap_set_refine_tau(fraclap_ctx* ctx, double tau);
 

@@ -18,7 +18,7 @@ struct fraclap_ctx {
   int leaf_size = 32;
   double wait_timeout_s = 10.0;
   int tensor_route = 1;          // slice products: 1 = tcgen05 + TMA, 0 = mma.sync
-  double refine_tau = 3e-3;      // first-order coefficient above which a pair is clustered
+  double refine_tau = 1e-3;      // first-order coefficient above which a pair is clustered
   long long wait_cycles = 0;     // wait_timeout_s in SM clock cycles (upper bound)
   int32_t* d_status = nullptr;   // device status word (0 = ok, else a FRACLAP_ERR_*)
   unsigned* d_barrier = nullptr; // grid-barrier state for cooperative kernels

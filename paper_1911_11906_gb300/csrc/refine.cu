@@ -310,12 +310,16 @@ constexpr double kConvergedR = 3e-9;
 // BF16 slices per operand in the refinement's residual products (7: FP64).
 constexpr int kRefineSlices = 7;
 
-__device__ void cluster_jacobi_body(const double* Sc, int c, double* Q, double* w, int32_t* status) {
-  // Parallel-order Jacobi: each round applies c/2 disjoint rotations at
-  // once (round-robin pairing; for odd c one index sits out each round), a
-  // sweep is c - 1 (c even) or c rounds and visits every pair once.
+__device__ void cluster_jacobi_body(const double* Sc, const double* Bc, int c, double* Q, double* w,
+                                    int32_t* status) {
+  // Rayleigh-Ritz on the pencil (S, B), B = X_c^T X_c: B = L L^T (Cholesky),
+  // C = L^-1 S L^-T, C = Y diag(mu) Y^T by parallel-order Jacobi (each round
+  // applies c/2 disjoint rotations at once, round-robin pairing; for odd c
+  // one index sits out each round), and Q = L^-T Y, so that X_c Q has
+  // orthonormal columns even though X_c is orthonormal only to first order.
   __shared__ double a[kMaxCluster][kMaxCluster + 1];
   __shared__ double q[kMaxCluster][kMaxCluster + 1];
+  __shared__ double l[kMaxCluster][kMaxCluster + 1];
   __shared__ double rc[kMaxCluster / 2], rs[kMaxCluster / 2];
   __shared__ int rp[kMaxCluster / 2], rq[kMaxCluster / 2];
   __shared__ double red[2][32];
@@ -325,6 +329,51 @@ __device__ void cluster_jacobi_body(const double* Sc, int c, double* Q, double* 
   for (int p = tid; p < c * c; p += nt) {
     const int i = p % c, j = p / c;
     a[i][j] = 0.5 * (Sc[i + j * c] + Sc[j + i * c]);
+    l[i][j] = 0.5 * (Bc[i + j * c] + Bc[j + i * c]);
+  }
+  __syncthreads();
+  // Cholesky, column by column, in place in the lower triangle of l
+  for (int j = 0; j < c; ++j) {
+    if (tid == 0) {
+      double d = l[j][j];
+      for (int k = 0; k < j; ++k) d -= l[j][k] * l[j][k];
+      if (!(d > 0.0)) {
+        raise_status(status, FRACLAP_ERR_NO_CONVERGENCE);
+        d = 1.0;
+      }
+      l[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < c; i += nt) {
+      double v = l[i][j];
+      for (int k = 0; k < j; ++k) v -= l[i][k] * l[j][k];
+      l[i][j] = v / l[j][j];
+    }
+    __syncthreads();
+  }
+  // W = L^-1 S (in place in a, one column per thread)
+  for (int m = tid; m < c; m += nt)
+    for (int i = 0; i < c; ++i) {
+      double v = a[i][m];
+      for (int k = 0; k < i; ++k) v -= l[i][k] * a[k][m];
+      a[i][m] = v / l[i][i];
+    }
+  __syncthreads();
+  // C = L^-1 W^T (into q), then a = C symmetrised and q = I
+  for (int m = tid; m < c; m += nt)
+    for (int i = 0; i < c; ++i) {
+      double v = a[m][i];
+      for (int k = 0; k < i; ++k) v -= l[i][k] * q[k][m];
+      q[i][m] = v / l[i][i];
+    }
+  __syncthreads();
+  for (int p = tid; p < c * c; p += nt) {
+    const int i = p % c, j = p / c;
+    a[i][j] = 0.5 * (q[i][j] + q[j][i]);
+  }
+  __syncthreads();
+  for (int p = tid; p < c * c; p += nt) {
+    const int i = p % c, j = p / c;
     q[i][j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
@@ -416,6 +465,14 @@ __device__ void cluster_jacobi_body(const double* Sc, int c, double* Q, double* 
     }
     if (sweep == 49 && tid == 0) raise_status(status, FRACLAP_ERR_NO_CONVERGENCE);
   }
+  // Q = L^-T Y (in place in q, one column per thread)
+  for (int m = tid; m < c; m += nt)
+    for (int i = c - 1; i >= 0; --i) {
+      double v = q[i][m];
+      for (int k = i + 1; k < c; ++k) v -= l[k][i] * q[k][m];
+      q[i][m] = v / l[i][i];
+    }
+  __syncthreads();
   // ascending order (selection by thread 0), then write out
   if (tid == 0) {
     for (int i = 0; i < c; ++i) perm[i] = i;
@@ -436,13 +493,15 @@ __device__ void cluster_jacobi_body(const double* Sc, int c, double* Q, double* 
   if (tid < c) w[tid] = a[perm[tid]][perm[tid]];
 }
 
-// S_q += X_q^T (A X_q) over the row range of blockIdx.y (of gridDim.y), for
-// every small cluster q (cinfo: size, first column, offset of its columns in
-// AXc).  One CTA per (cluster, row range); rows are staged 32 at a time and
-// the work is n c^2 per cluster.  S_q (ld c) must be zero on entry.
+// S_q += X_q^T (A X_q) and B_q += X_q^T X_q over the row range of
+// blockIdx.y (of gridDim.y), for every small cluster q (cinfo: size, first
+// column, offset of its columns in AXc).  One CTA per (cluster, row range);
+// rows are staged 32 at a time and the work is n c^2 per cluster.  S_q and
+// B_q (ld c) must be zero on entry.
 constexpr int kGramThreads = 256;
 __global__ void __launch_bounds__(kGramThreads) cluster_gram(const double* X, int64_t ldx, const double* AXc,
-                                                             int64_t n, const int* cinfo, double* Sall) {
+                                                             int64_t n, const int* cinfo, double* Sall,
+                                                             double* Ball) {
   constexpr int RB = 32, NT = kGramThreads, MO = kMaxCluster * kMaxCluster / NT;
   __shared__ double xs[RB][kMaxCluster + 1], ys[RB][kMaxCluster + 1];
   __shared__ double red[NT];
@@ -453,9 +512,12 @@ __global__ void __launch_bounds__(kGramThreads) cluster_gram(const double* X, in
   const int64_t rows = (n + gridDim.y - 1) / gridDim.y;
   const int64_t rbeg = (int64_t)blockIdx.y * rows;
   const int64_t rend = (rbeg + rows < n) ? rbeg + rows : n;
-  double acc[MO];
+  double acc[MO], accb[MO];
 #pragma unroll
-  for (int mo = 0; mo < MO; ++mo) acc[mo] = 0.0;
+  for (int mo = 0; mo < MO; ++mo) {
+    acc[mo] = 0.0;
+    accb[mo] = 0.0;
+  }
   for (int64_t r0 = rbeg; r0 < rend; r0 += RB) {
     for (int e = tid; e < RB * c; e += NT) {
       const int rr = e % RB, cc = e / RB;
@@ -467,9 +529,13 @@ __global__ void __launch_bounds__(kGramThreads) cluster_gram(const double* X, in
     if (groups > 1) {
       if (tid < groups * P) {
         const int o = tid % P, gr = tid / P, i = o % c, j = o / c;
-        double sum = acc[0];
-        for (int rr = gr; rr < RB; rr += groups) sum = fma(xs[rr][i], ys[rr][j], sum);
+        double sum = acc[0], sumb = accb[0];
+        for (int rr = gr; rr < RB; rr += groups) {
+          sum = fma(xs[rr][i], ys[rr][j], sum);
+          sumb = fma(xs[rr][i], xs[rr][j], sumb);
+        }
         acc[0] = sum;
+        accb[0] = sumb;
       }
     } else {
 #pragma unroll
@@ -477,29 +543,40 @@ __global__ void __launch_bounds__(kGramThreads) cluster_gram(const double* X, in
         const int o = tid + NT * mo;
         if (o < P) {
           const int i = o % c, j = o / c;
-          double sum = acc[mo];
+          double sum = acc[mo], sumb = accb[mo];
 #pragma unroll 8
-          for (int rr = 0; rr < RB; ++rr) sum = fma(xs[rr][i], ys[rr][j], sum);
+          for (int rr = 0; rr < RB; ++rr) {
+            sum = fma(xs[rr][i], ys[rr][j], sum);
+            sumb = fma(xs[rr][i], xs[rr][j], sumb);
+          }
           acc[mo] = sum;
+          accb[mo] = sumb;
         }
       }
     }
     __syncthreads();
   }
   double* S = Sall + (int64_t)q * kMaxCluster * kMaxCluster;
+  double* Bq = Ball + (int64_t)q * kMaxCluster * kMaxCluster;
   if (groups > 1) {
-    red[tid] = (tid < groups * P) ? acc[0] : 0.0;
-    __syncthreads();
-    if (tid < P) {
-      double sum = 0.0;
-      for (int gr = 0; gr < groups; ++gr) sum += red[tid + gr * P];
-      atomicAdd(S + tid, sum);  // o = i + j c
+    for (int which = 0; which < 2; ++which) {
+      red[tid] = (tid < groups * P) ? (which ? accb[0] : acc[0]) : 0.0;
+      __syncthreads();
+      if (tid < P) {
+        double sum = 0.0;
+        for (int gr = 0; gr < groups; ++gr) sum += red[tid + gr * P];
+        atomicAdd((which ? Bq : S) + tid, sum);  // o = i + j c
+      }
+      __syncthreads();
     }
   } else {
 #pragma unroll
     for (int mo = 0; mo < MO; ++mo) {
       const int o = tid + NT * mo;
-      if (o < P) atomicAdd(S + o, acc[mo]);
+      if (o < P) {
+        atomicAdd(S + o, acc[mo]);
+        atomicAdd(Bq + o, accb[mo]);
+      }
     }
   }
 }
@@ -550,13 +627,30 @@ __global__ void spmm_csr_cols(int64_t n, const int64_t* __restrict__ rowptr,
 }
 
 // One CTA per cluster: cinfo[3q] = size, cinfo[3q+1] = first sorted position;
-// S_q, Q_q at Sall/Qall + q * 64 * 64 (ld = size).
-__global__ void cluster_jacobi_batched(const double* Sall, const int* cinfo, double* Qall,
+// S_q, B_q, Q_q at Sall/Ball/Qall + q * 64 * 64 (ld = size).
+__global__ void cluster_jacobi_batched(const double* Sall, const double* Ball, const int* cinfo, double* Qall,
                                        double* lambda, int32_t* status) {
   const int q = blockIdx.x;
   const int c = cinfo[3 * q], s0 = cinfo[3 * q + 1];
-  cluster_jacobi_body(Sall + (int64_t)q * kMaxCluster * kMaxCluster, c,
-                      Qall + (int64_t)q * kMaxCluster * kMaxCluster, lambda + s0, status);
+  const int64_t o = (int64_t)q * kMaxCluster * kMaxCluster;
+  cluster_jacobi_body(Sall + o, Ball + o, c, Qall + o, lambda + s0, status);
+}
+
+// Pencil (S, I + G) to first order in G = B - I: C = S - (G S + S G) / 2
+// (from the product P = G S), Q = Y - G Y / 2 (from P = G Y).  c x c, ld c.
+__global__ void pencil_first_order(const double* S, const double* P, int64_t c, double* Cout) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= c * c) return;
+  const int64_t i = t % c, j = t / c;
+  Cout[t] = 0.5 * (S[i + j * c] + S[j + i * c]) - 0.5 * (P[i + j * c] + P[j + i * c]);
+}
+__global__ void vectors_first_order(double* Y, const double* P, int64_t c) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < c * c) Y[t] -= 0.5 * P[t];
+}
+__global__ void minus_identity(double* G, int64_t c) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < c) G[i + i * c] -= 1.0;
 }
 
 // l_j = (x_j^T (A x_j)) / (x_j^T x_j); one block per column.
@@ -594,11 +688,11 @@ __global__ void rayleigh(const double* X, int64_t ldx, const double* AX, int64_t
 // the FP64 dense eigensolver of this library; its workspace is sized for n).
 constexpr int64_t kMaxBigCluster = 65535;
 
-// Scratch of the batched small-cluster step: S_q and Q_q (64 x 64 each) for
+// Scratch of the batched small-cluster step: S_q, B_q and Q_q (64 x 64 each) for
 // up to n/2 + 1 clusters, the column map and the cluster table.
 static int64_t small_cluster_doubles(int64_t n) {
   const int64_t ns = n / 2 + 1;
-  return 2 * ns * kMaxCluster * kMaxCluster + (n + 64) / 2 + (3 * ns + 64) / 2 + 64;
+  return 3 * ns * kMaxCluster * kMaxCluster + (n + 64) / 2 + (3 * ns + 64) / 2 + 64;
 }
 
 size_t refine_ws(const fraclap_ctx* ctx, int64_t n) {
@@ -617,7 +711,7 @@ size_t refine_ws(const fraclap_ctx* ctx, int64_t n) {
   ar.take<int>(2 * n + 2);     // cluster list + count
   ar.take<double>(8);          // norms, delta
   const int64_t cmax = std::min<int64_t>(n, kMaxBigCluster);
-  ar.take<double>(2 * cmax * cmax + cmax);
+  ar.take<double>(4 * cmax * cmax + cmax);
   ar.take<double>(small_cluster_doubles(n));
   return ar.off + std::max(cluster_eig_ws(ctx, cmax), ozaki_ws(n, n, n, kRefineSlices));
 }
@@ -640,7 +734,7 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
   double* scal = ar->take<double>(8);
   ctx->refine_stats.clear();
   const int64_t cmax = std::min<int64_t>(n, kMaxBigCluster);
-  double* cbuf = ar->take<double>(2 * cmax * cmax + cmax);
+  double* cbuf = ar->take<double>(4 * cmax * cmax + cmax);
   double* sbuf = ar->take<double>(small_cluster_doubles(n));
   Arena car = *ar;  // workspace of the dense eigensolver used on big clusters
   FL_CHECK(ctx, cbuf != nullptr, FRACLAP_ERR_ALLOC, "refine: workspace too small");
@@ -768,7 +862,8 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
       }
       const int64_t ns = (int64_t)cinfo.size() / 3;
       if (ns > 0) {
-        double* Qall = Sall + ns * kMaxCluster * kMaxCluster;
+        double* Ball = Sall + ns * kMaxCluster * kMaxCluster;
+        double* Qall = Ball + ns * kMaxCluster * kMaxCluster;
         int* d_src = reinterpret_cast<int*>(Qall + ns * kMaxCluster * kMaxCluster);
         int* d_cinfo = d_src + ((T + 63) / 64) * 64;
         FL_CUDA(ctx, cudaMemcpyAsync(d_src, src.data(), sizeof(int) * T, cudaMemcpyHostToDevice, st));
@@ -777,18 +872,23 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
         spmm_csr_cols<<<dim3(rows, (unsigned)std::min<int64_t>(T, 4096)), 128, 0, st>>>(n, rowptr, col, val, X, ldx,
                                                                                        d_src, T, AXc);
         count_launch(ctx);
-        FL_CUDA(ctx, cudaMemsetAsync(Sall, 0, sizeof(double) * ns * kMaxCluster * kMaxCluster, st));
-        cluster_gram<<<dim3((unsigned)ns, 4), kGramThreads, 0, st>>>(X, ldx, AXc, n, d_cinfo, Sall);
+        FL_CUDA(ctx, cudaMemsetAsync(Sall, 0, sizeof(double) * 2 * ns * kMaxCluster * kMaxCluster, st));
+        cluster_gram<<<dim3((unsigned)ns, 4), kGramThreads, 0, st>>>(X, ldx, AXc, n, d_cinfo, Sall, Ball);
         count_launch(ctx);
-        cluster_jacobi_batched<<<(unsigned)ns, 256, 0, st>>>(Sall, d_cinfo, Qall, lambda, ctx->d_status);
+        cluster_jacobi_batched<<<(unsigned)ns, 256, 0, st>>>(Sall, Ball, d_cinfo, Qall, lambda, ctx->d_status);
         count_launch(ctx);
         cluster_rotate<<<dim3((unsigned)cdiv(n, 64), (unsigned)ns), 256, 0, st>>>(X, ldx, n, d_cinfo, Qall);
         count_launch(ctx);
         // the host vectors must outlive the asynchronous copies
         FL_CUDA(ctx, cudaStreamSynchronize(st));
       }
+      // Big clusters: the pencil (S_c, B_c), B_c = X_c^T X_c = I + G, to
+      // first order in G (the basis is orthonormal to second order in the
+      // first-order coefficients), through the dense FP64 eigensolver.
       double* Sc = cbuf;
       double* Qc = Sc + cmax * cmax;
+      double* Gc = Qc + cmax * cmax;
+      double* Pc = Gc + cmax * cmax;
       double* AXb = R;
       double* Xn = S;
       if (!big.empty()) span.start(kStageRefineBigClusters);
@@ -797,13 +897,25 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
         FL_CHECK(ctx, c <= cmax, FRACLAP_ERR_UNSUPPORTED,
                  "refine: a cluster of %d eigenvalues exceeds %lld", c, (long long)cmax);
         double* Xc = X + (int64_t)i0 * ldx;
+        const unsigned cg = (unsigned)cdiv((int64_t)c * c, 256);
+        const int ksplit = (int)cdiv(n, 512);
         spmm_csr<<<dim3(rows, (unsigned)std::min(c, 4096)), 128, 0, st>>>(n, rowptr, col, val, Xc, ldx, c, AXb, n);
         count_launch(ctx);
         FL_CUDA(ctx, cudaMemsetAsync(Sc, 0, sizeof(double) * c * c, st));
-        FL_TRY(gemm<double>(ctx, true, false, kGemmPlain, D64{c, c, n, Xc, ldx, AXb, n, Sc, c, nullptr, 0, nullptr, 0, 0, 1.0, 1.0}, (int)cdiv(n, 512), st));
+        FL_CUDA(ctx, cudaMemsetAsync(Gc, 0, sizeof(double) * c * c, st));
+        FL_TRY(gemm<double>(ctx, true, false, kGemmPlain, D64{c, c, n, Xc, ldx, AXb, n, Sc, c, nullptr, 0, nullptr, 0, 0, 1.0, 1.0}, ksplit, st));
+        FL_TRY(gemm<double>(ctx, true, false, kGemmPlain, D64{c, c, n, Xc, ldx, Xc, ldx, Gc, c, nullptr, 0, nullptr, 0, 0, 1.0, 1.0}, ksplit, st));
+        minus_identity<<<(unsigned)cdiv(c, 256), 256, 0, st>>>(Gc, c);
+        count_launch(ctx);
+        FL_TRY(gemm<double>(ctx, false, false, kGemmPlain, D64{c, c, c, Gc, c, Sc, c, Pc, c, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
+        pencil_first_order<<<cg, 256, 0, st>>>(Sc, Pc, c, Qc);
+        count_launch(ctx);
         Arena sub = car;
-        FL_TRY(cluster_eig(ctx, Sc, c, lambda + i0, Qc, &sub, st));
-        FL_TRY(gemm<double>(ctx, false, false, kGemmPlain, D64{n, c, c, Xc, ldx, Qc, c, Xn, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
+        FL_TRY(cluster_eig(ctx, Qc, c, lambda + i0, Sc, &sub, st));  // Y into Sc
+        FL_TRY(gemm<double>(ctx, false, false, kGemmPlain, D64{c, c, c, Gc, c, Sc, c, Pc, c, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
+        vectors_first_order<<<cg, 256, 0, st>>>(Sc, Pc, c);
+        count_launch(ctx);
+        FL_TRY(gemm<double>(ctx, false, false, kGemmPlain, D64{n, c, c, Xc, ldx, Sc, c, Xn, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
         FL_CUDA(ctx, cudaMemcpy2DAsync(Xc, ldx * sizeof(double), Xn, n * sizeof(double), n * sizeof(double), c,
                                        cudaMemcpyDeviceToDevice, st));
       }
