@@ -144,13 +144,17 @@ BAND = {"fp64": 64, "mixed": 64}
 
 
 def ozaki_bf16_flops(n: int, slices: int = 8) -> float:
-    """BF16 tensor flops one lower-triangular n x n x n residual product issues:
-    the 7-bit slicing for K > 256 uses 8 slices (pairs with p + q <= 9, 36
-    products) over the 128 x 64 CTA tiles that touch the lower triangle."""
+    """Algorithmic BF16 tensor flops of one lower-triangular n x n x n
+    residual product: the 7-bit slicing for K > 256 uses 8 slices, pairs
+    with p + q < 8 (36 products), each 2 n flops per lower-triangle entry."""
     pairs = slices * (slices + 1) // 2
-    tiles = sum(1 for i in range(-(-n // 128)) for j in range(-(-n // 64)) if i * 128 + 127 >= j * 64)
-    kp = -(-n // 64) * 64
-    return 2.0 * pairs * tiles * 128 * 64 * kp
+    return 2.0 * pairs * n * (n * (n + 1) // 2)
+
+
+# DRAM bytes per BF16 flop of ozaki_tc_kernel, from one ncu capture of the
+# 4096^3 product (12.87 GB read + 1.06 GB written for 36 x 2 x 4096^3 flop);
+# its tile re-streaming grows in proportion to the flops.
+OZAKI_DRAM_BYTES_PER_FLOP = (12.866905e9 + 1.060005e9) / (36 * 2.0 * 4096 ** 3)
 
 
 def run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier):
@@ -267,20 +271,23 @@ def run_gpu(args, rank, world, local_rank):
         q2_ms, q2_cnt = stages["back_q2"]
         dur = q2_ms / max(q2_cnt, 1)
         work = q2_flops(n, b)
+        traffic = None
         roof = {"kernel": "q2t_apply_kernel (back-transformation by the bulge-chasing reflectors, FP64)",
                 "bound": "alu", "peak": round(FP64_PEAK_TFLOPS, 4),
                 "peak_source": "derived FP64 peak (152 SMs x 2.07 GHz x 2 DFMA/clk x 2); no FP64 figure in MEASURED_PEAKS.json"}
     else:
-        g_ms, g_cnt = stages["residual_gemm"]
+        g_ms, g_cnt = stages["slice_products"]
         dur = g_ms / max(g_cnt, 1)
         work = ozaki_bf16_flops(n)
+        traffic = OZAKI_DRAM_BYTES_PER_FLOP * work
         peak = _measured_peak("bf16_tflops") or 1900.0
         roof = {"kernel": "ozaki_tc_kernel (residual products of the refinement: tcgen05.mma on TMA-loaded BF16 slices)",
                 "bound": "tensor", "peak": round(peak, 1),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if _measured_peak("bf16_tflops") else "fallback 1.9 PFLOP/s"}
     achieved = work / (dur * 1e-3) / 1e12
     roof.update({"achieved": round(achieved, 4), "unit": "TFLOP/s", "frac": round(achieved / roof["peak"], 5),
-                 "traffic": None, "flops_per_launch": work, "ms_per_launch": round(dur, 3)})
+                 "traffic": (round(traffic) if traffic else None), "flops_per_launch": work,
+                 "ms_per_launch": round(dur, 3)})
     eig_stages = ("band_reduction", "bulge_chasing", "tridiag_dc", "back_q2", "back_q1", "refine")
     solves = k * world
     line = {
@@ -422,6 +429,27 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_product_only(args):
+    """The refinement's residual product X^T X (lower triangle, 7 slices) on a
+    seeded N x N matrix, alone: a small case for kernel captures."""
+    import torch
+    import paper_1911_11906_gb300 as F
+    n = args.product_only
+    g = torch.Generator(device="cpu").manual_seed(0)
+    X = (torch.randn(n, n, generator=g, dtype=torch.float64) / n ** 0.5).cuda()
+    C = torch.empty(n, n, dtype=torch.float64, device="cuda").t()
+    ctx = F.Context()
+    for it in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        F.dgemm_ozaki(X.t(), X.t(), trans_a=True, C=C, ctx=ctx)
+        e1.record()
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            print(json.dumps({"product": f"{n}x{n}x{n}", "slices": 7, "ms": round(e0.elapsed_time(e1), 3)}),
+                  flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -431,7 +459,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="both", choices=["both", "fp64", "mixed"],
                     help="eigendecomposition route(s) to time; the headline is the fastest that meets the FP64 bar")
+    ap.add_argument("--product-only", type=int, default=0, metavar="N",
+                    help="profiling aid: run only FP64-accurate slice products N x N x N (R = X^T X "
+                         "shape), --steps times after --warmup, and print their CUDA-event times")
     args = ap.parse_args()
+    if args.product_only > 0:
+        run_product_only(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

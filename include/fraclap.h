@@ -233,7 +233,8 @@ enum {
   FRACLAP_STAGE_REFINE_SORT = 11,   /* ordering of the columns (inside REFINE) */
   FRACLAP_STAGE_REFINE_CLUSTERS = 12, /* exact diagonalisation of clusters up to 64 (inside REFINE) */
   FRACLAP_STAGE_REFINE_BIG_CLUSTERS = 13, /* larger clusters, dense FP64 solver (inside REFINE) */
-  FRACLAP_STAGE_COUNT = 14
+  FRACLAP_STAGE_SLICE_PRODUCTS = 14, /* the tensor-core kernel of each FP64-accurate product alone */
+  FRACLAP_STAGE_COUNT = 15
 };
 /* With enable != 0, every later stage records a CUDA event pair on its stream. */
 int fraclap_set_profiling(fraclap_ctx* ctx, int enable);

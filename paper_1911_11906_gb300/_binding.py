@@ -117,7 +117,7 @@ class Context:
 
     STAGES = ("assemble", "band_reduction", "bulge_chasing", "tridiag_dc", "back_q2", "back_q1", "apply",
               "refine", "residual_gemm", "refine_norms", "refine_update", "refine_sort", "refine_clusters",
-              "refine_big_clusters")
+              "refine_big_clusters", "slice_products")
 
     def set_profiling(self, enable: bool = True):
         self.check(self.lib.fraclap_set_profiling(self.handle, int(enable)))

@@ -78,7 +78,8 @@ enum Stage : int {
   kStageRefineSort = 11,      // ranks and column permutation
   kStageRefineClusters = 12,  // exact diagonalisation of the clusters (up to 64)
   kStageRefineBigClusters = 13,  // clusters above 64 (dense FP64 solver)
-  kStageCount = 14
+  kStageSliceProducts = 14,   // the slice-product kernel of an FP64-accurate product
+  kStageCount = 15
 };
 
 // Records CUDA events around a stage on `st` when profiling is on.

@@ -575,6 +575,7 @@ int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t
   count_launch(ctx);
   make_slices<<<gs, 256, 0, st>>>(B, ldb, !tb, N, K, Kp, eb, sl, bits, SB);
   count_launch(ctx);
+  StageTimer tm(ctx, kStageSliceProducts, st);
   if (ctx->tensor_route == 1) {
     CUtensorMap ma, mb;
     FL_CHECK(ctx, slice_map(&ma, SA, M, Kp, sl, TC_M) && slice_map(&mb, SB, N, Kp, sl, TC_N),
