@@ -49,6 +49,8 @@ struct DcBuf {
   int* kept;      // n: [lo, lo+K): sorted positions of survivors; [lo+K, hi): deflated
   double* dd;     // n: survivors' D
   double* zz;     // n: survivors' z
+  T* ddt;         // n: survivors' D in the working precision (secular equation)
+  T* zzt;         // n: survivors' z in the working precision
   double* tau;    // n: root offsets
   int* org;       // n: root origins (index into dd)
   double* zhat;   // n
@@ -244,7 +246,10 @@ __global__ void dc_merge_prep(DcBuf<T> B, const double* e, const double* lambda,
   // deflation
   double dmax = 0.0;
   for (int64_t i = 0; i < nm; ++i) dmax = fmax(dmax, fabs(Dp[i]));
-  const double tol = 8.0 * kEps * fmax(dmax, rho);
+  // deflation at the working precision's rounding level (FP32 merges
+  // deflate at 8 eps_32: their results are only FP32-accurate anyway)
+  const double eps_t = (sizeof(T) == 4) ? 1.1920928955078125e-07 : kEps;
+  const double tol = 8.0 * eps_t * fmax(dmax, rho);
   int* kept = B.kept + lo;
   int64_t nrot = 0, K = 0, ndef = 0;
   int64_t prev = -1;
@@ -276,8 +281,13 @@ __global__ void dc_merge_prep(DcBuf<T> B, const double* e, const double* lambda,
   for (int64_t i = 0; i < nm; ++i)
     if (!flag[i]) {
       kept[K] = (int)i;
-      B.dd[lo + K] = Dp[i];
-      B.zz[lo + K] = zp[i];
+      // the poles and weights as the working precision holds them, so that
+      // the roots (found in T) and the Gu-Eisenstat weights and vectors
+      // (formed in FP64 from dd, zz) see the same secular equation
+      B.ddt[lo + K] = (T)Dp[i];
+      B.zzt[lo + K] = (T)zp[i];
+      B.dd[lo + K] = (double)(T)Dp[i];
+      B.zz[lo + K] = (double)(T)zp[i];
       ++K;
     }
   for (int64_t i = 0; i < nm; ++i)
@@ -327,57 +337,83 @@ __global__ void dc_gather(DcBuf<T> B, const T* Z, int64_t ldz, int64_t nmax) {
   }
 }
 
-// Secular equation roots; thread = root.
+// Secular equation 1 + rho sum_j z_j^2 / (d_j - lambda) = 0: one warp per
+// root, the lanes splitting the sums over the poles (butterfly sums, so every
+// lane holds the same totals and takes the same branches).  Root i lies in
+// (d_i, d_{i+1}) (the last one in (d_{K-1}, d_{K-1} + rho |z|^2)); it is kept
+// as an offset tau from its nearer pole d_org.  Each step fits the two
+// neighbouring poles exactly and the rest by the tangent rational model, and
+// a bisection bracket guards it.  The terms are formed in the merge's working
+// precision T and summed in FP64.  Stop when |f| is at the rounding level of
+// its terms (8 eps_T (1 + |psi| + |phi|): psi and phi are sums of terms of
+// one sign), when the bracket has closed to the rounding level of tau, or
+// when a step no longer moves tau.
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int kSecWarps = 4;  // roots per 128-thread block
+
 template <class T>
-__global__ void dc_secular(DcBuf<T> B, int32_t* status) {
+__global__ void __launch_bounds__(32 * kSecWarps) dc_secular(DcBuf<T> B, int32_t* status) {
   const MergeInfo inf = B.info[blockIdx.y];
   const int64_t K = inf.K;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= K) return;
-  const double* dd = B.dd + inf.lo;
-  const double* zz = B.zz + inf.lo;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * kSecWarps + (threadIdx.x >> 5);
+  if (i >= K) return;  // warp-uniform
+  const double eps = (sizeof(T) == 4) ? 1.1920928955078125e-07 : kEps;
+  const T* dd = B.ddt + inf.lo;
+  const T* zz = B.zzt + inf.lo;
   const double rho = inf.rho;
-  double lo_t, hi_t;
+  T lo_t, hi_t;
   int64_t orgi;
   if (i < K - 1) {
-    const double half = 0.5 * (dd[i + 1] - dd[i]);
-    double f = 1.0;
-    for (int64_t j = 0; j < K; ++j) f += rho * zz[j] * zz[j] / ((dd[j] - dd[i]) - half);
-    if (f >= 0.0) { orgi = i; lo_t = 0.0; hi_t = half; }
-    else { orgi = i + 1; lo_t = -half; hi_t = 0.0; }
+    const T half = T(0.5) * (dd[i + 1] - dd[i]);
+    double f = 0.0;
+    for (int64_t j = lane; j < K; j += 32) f += (double)(zz[j] * zz[j] / ((dd[j] - dd[i]) - half));
+    f = 1.0 + rho * warp_allsum(f);
+    if (f >= 0.0) { orgi = i; lo_t = T(0); hi_t = half; }
+    else { orgi = i + 1; lo_t = -half; hi_t = T(0); }
   } else {
-    double s = 0.0;
-    for (int64_t j = 0; j < K; ++j) s += zz[j] * zz[j];
-    orgi = i; lo_t = 0.0; hi_t = rho * s;
+    double s2 = 0.0;
+    for (int64_t j = lane; j < K; j += 32) s2 += (double)zz[j] * (double)zz[j];
+    orgi = i; lo_t = T(0); hi_t = (T)(rho * warp_allsum(s2));
   }
-  const double dorg = dd[orgi];
-  const double a = dd[i] - dorg;
-  const double bpole = (i < K - 1) ? dd[i + 1] - dorg : 0.0;
-  double tau = 0.5 * (lo_t + hi_t);
+  const T dorg = dd[orgi];
+  const T a = dd[i] - dorg;
+  const T bpole = (i < K - 1) ? dd[i + 1] - dorg : T(0);
+  T tau = T(0.5) * (lo_t + hi_t);
   int it = 0;
   for (; it < 200; ++it) {
     double psi = 0.0, phi = 0.0, dpsi = 0.0, dphi = 0.0;
-    for (int64_t j = 0; j < K; ++j) {
-      const double den = (dd[j] - dorg) - tau;
-      const double t = zz[j] * zz[j] / den;
-      if (j <= i) { psi += t; dpsi += t / den; }
-      else { phi += t; dphi += t / den; }
+    for (int64_t j = lane; j < K; j += 32) {
+      const T den = (dd[j] - dorg) - tau;
+      const T t = zz[j] * zz[j] / den;
+      if (j <= i) { psi += (double)t; dpsi += (double)(t / den); }
+      else { phi += (double)t; dphi += (double)(t / den); }
     }
-    psi *= rho; phi *= rho; dpsi *= rho; dphi *= rho;
+    psi = rho * warp_allsum(psi);
+    phi = rho * warp_allsum(phi);
+    dpsi = rho * warp_allsum(dpsi);
+    dphi = rho * warp_allsum(dphi);
     const double f = 1.0 + psi + phi;
     if (f > 0.0) hi_t = tau; else lo_t = tau;
-    if (fabs(f) <= 8.0 * kEps * (double)K * (1.0 + fabs(psi) + fabs(phi))) break;
-    if (hi_t - lo_t <= 4.0 * kEps * fmax(fabs(lo_t), fabs(hi_t))) break;
+    if (fabs(f) <= 8.0 * eps * (1.0 + fabs(psi) + fabs(phi))) break;
+    if ((double)(hi_t - lo_t) <= 4.0 * eps * fmax(fabs((double)lo_t), fabs((double)hi_t))) break;
     double x;
+    const double at = (double)a - (double)tau;
     if (i < K - 1) {
-      const double q1 = dpsi * (a - tau) * (a - tau), p1 = psi - dpsi * (a - tau);
-      const double q2 = dphi * (bpole - tau) * (bpole - tau), p2 = phi - dphi * (bpole - tau);
+      const double bt = (double)bpole - (double)tau;
+      const double q1 = dpsi * at * at, p1 = psi - dpsi * at;
+      const double q2 = dphi * bt * bt, p2 = phi - dphi * bt;
       const double C = 1.0 + p1 + p2;
-      // C (a - x)(b - x) + q1 (b - x) + q2 (a - x) = 0
-      const double A2 = C, B2 = -(C * (a + bpole) + q1 + q2), C2 = C * a * bpole + q1 * bpole + q2 * a;
-      x = 0.5 * (lo_t + hi_t);
+      // in x - tau: C (at - y)(bt - y) + q1 (bt - y) + q2 (at - y) = 0, y = x - tau
+      const double A2 = C, B2 = -(C * (at + bt) + q1 + q2), C2 = C * at * bt + q1 * bt + q2 * at;
+      double y = 0.5 * ((double)lo_t + (double)hi_t) - (double)tau;
       if (A2 == 0.0) {
-        if (B2 != 0.0) x = -C2 / B2;
+        if (B2 != 0.0) y = -C2 / B2;
       } else {
         const double disc = fmax(B2 * B2 - 4.0 * A2 * C2, 0.0);
         const double sq = sqrt(disc);
@@ -391,20 +427,27 @@ __global__ void dc_secular(DcBuf<T> B, int32_t* status) {
           r1 = 2.0 * C2 / t;
           r2 = t / (2.0 * A2);
         }
-        if (r1 > lo_t && r1 < hi_t) x = r1;
-        else if (r2 > lo_t && r2 < hi_t) x = r2;
+        const double lo_y = (double)lo_t - (double)tau, hi_y = (double)hi_t - (double)tau;
+        if (r1 > lo_y && r1 < hi_y) y = r1;
+        else if (r2 > lo_y && r2 < hi_y) y = r2;
       }
+      x = (double)tau + y;
     } else {
-      const double q1 = dpsi * (a - tau) * (a - tau), p1 = psi - dpsi * (a - tau);
+      const double q1 = dpsi * at * at, p1 = psi - dpsi * at;
       const double C = 1.0 + p1 + phi;
-      x = (C != 0.0) ? a + q1 / C : 0.5 * (lo_t + hi_t);
+      x = (C != 0.0) ? (double)tau + (at + q1 / C) : 0.5 * ((double)lo_t + (double)hi_t);
     }
-    if (!(x > lo_t && x < hi_t)) x = 0.5 * (lo_t + hi_t);
-    tau = x;
+    T xn = (T)x;
+    if (!(xn > lo_t && xn < hi_t)) xn = T(0.5) * (lo_t + hi_t);
+    const bool stalled = fabs((double)xn - (double)tau) <= 2.0 * eps * fabs((double)tau);
+    tau = xn;
+    if (stalled) break;
   }
-  if (it >= 200) raise_status(status, FRACLAP_ERR_NO_CONVERGENCE);
-  B.tau[inf.lo + i] = tau;
-  B.org[inf.lo + i] = (int)orgi;
+  if (lane == 0) {
+    if (it >= 200) raise_status(status, FRACLAP_ERR_NO_CONVERGENCE);
+    B.tau[inf.lo + i] = (double)tau;
+    B.org[inf.lo + i] = (int)orgi;
+  }
 }
 
 // Gu-Eisenstat: zhat_i^2 = (lam_{K-1} - d_i)/rho * prod_{j<K-1} (lam_j - d_i)/(d_j' - d_i).
@@ -544,6 +587,8 @@ int take_bufs(Arena* ar, int64_t n, int L, DcBuf<T>* B) {
   B->kept = ar->take<int>(n);
   B->dd = ar->take<double>(n);
   B->zz = ar->take<double>(n);
+  B->ddt = ar->take<T>(n);
+  B->zzt = ar->take<T>(n);
   B->tau = ar->take<double>(n);
   B->org = ar->take<int>(n);
   B->zhat = ar->take<double>(n);
@@ -599,7 +644,8 @@ int stedc_run(fraclap_ctx* ctx, const double* d, const double* e, int64_t n, dou
     const dim3 rows((unsigned)cdiv(nmax, 128), (unsigned)nmerge);
     dc_gather<T><<<rows, 128, 0, st>>>(B, Z, ldz, nmax);
     count_launch(ctx);
-    dc_secular<T><<<rows, 128, 0, st>>>(B, ctx->d_status);
+    dc_secular<T><<<dim3((unsigned)cdiv(nmax, kSecWarps), (unsigned)nmerge), 32 * kSecWarps, 0, st>>>(
+        B, ctx->d_status);
     count_launch(ctx);
     dc_zhat<T><<<rows, 128, 0, st>>>(B);
     count_launch(ctx);
