@@ -4,7 +4,8 @@
 // (compact WY) by a cooperative kernel: the panel's rows are split over the
 // CTAs and stay in shared memory, and each Householder column costs one
 // grid-wide reduction (the dot products of the pivot column with every later
-// column, from which the reflector and its effect on the panel follow).  The
+// column, added by FP64 atomics, from which the reflector and its effect on
+// the panel follow).  The
 // trailing matrix is then updated as A22 <- Q^T A22 Q = A22 - W V^T - V W^T
 // with X = A22 (V T), W = X - 1/2 V (T^T V^T X), through the GEMM engine
 // (symmetric A22 read from its lower triangle; lower-triangular rank-2b
@@ -44,7 +45,9 @@ panel_qr_kernel(T* P, int64_t ldp, int64_t m, int bw, T* Vout, int64_t ldv,
   const int nref = (m < bw) ? (int)m : bw;
   const int stride = 2 * bw;
   for (int c = 0; c < nref; ++c) {
-    double* part = partials + (size_t)(c & 1) * G * stride + (size_t)blockIdx.x * stride;
+    // column sums over all CTAs: FP64 atomics into one of three buffers
+    // (zeroed two columns ahead, after the barrier that ends its last use)
+    double* acc = partials + (size_t)(c % 3) * stride;
     // partial dot products over this CTA's rows r >= c
     const int64_t r0 = (c > rb) ? c - rb : 0;  // first local row with global row >= c
     for (int j = c + warp; j < bw; j += nwarp) {
@@ -55,18 +58,16 @@ panel_qr_kernel(T* P, int64_t ldp, int64_t m, int bw, T* Vout, int64_t ldv,
         s += (double)S[r + c * ld] * (double)S[r + j * ld];
       }
       s = warp_sum(s);
-      if (lane == 0) part[j] = s;
+      if (lane == 0 && s != 0.0) atomicAdd(acc + j, s);
     }
-    for (int j = c + tid; j < bw; j += PQR_NT)
-      part[bw + j] = (c >= rb && c < re) ? (double)S[(c - rb) + j * ld] : 0.0;
+    if (c >= rb && c < re)
+      for (int j = c + tid; j < bw; j += PQR_NT) acc[bw + j] = (double)S[(c - rb) + j * ld];
     if (!grid_barrier(bar, G, limit, status)) return;
-    // every CTA reduces the partials in the same order (identical results)
+    if (blockIdx.x == 0)
+      for (int t = tid; t < stride; t += PQR_NT) partials[(size_t)((c + 2) % 3) * stride + t] = 0.0;
     for (int t = tid; t < 2 * (bw - c); t += PQR_NT) {
       const int slot = (t < bw - c) ? c + t : bw + c + (t - (bw - c));
-      const double* base = partials + (size_t)(c & 1) * G * stride;
-      double s = 0.0;
-      for (unsigned b = 0; b < G; ++b) s += __ldcg(base + (size_t)b * stride + slot);
-      red[(t < bw - c) ? t : 64 + (t - (bw - c))] = s;
+      red[(t < bw - c) ? t : 64 + (t - (bw - c))] = __ldcg(acc + slot);
     }
     __syncthreads();
     if (tid == 0) {
@@ -186,7 +187,7 @@ int stage1_take(Arena* ar, int64_t n, int b, int G, Stage1T<T>* s) {
   s->Y = ar->take<T>((int64_t)b * b);
   s->Mm = ar->take<T>((int64_t)b * b);
   s->gram = ar->take<double>((int64_t)b * b);
-  s->partials = ar->take<double>(2 * (int64_t)G * 2 * b);
+  s->partials = ar->take<double>(3 * 2 * (int64_t)b);
   return 0;
 }
 
@@ -218,6 +219,7 @@ int sy2sb_run(fraclap_ctx* ctx, T* Aw, int64_t n, int64_t lda, int b, T* band, S
     const int G = panel_grid(ctx, m, b, sizeof(T), &rows_per_cta, &smem);
     FL_CHECK(ctx, smem <= 180 * 1024, FRACLAP_ERR_UNSUPPORTED, "sy2sb: panel too tall (%lld)", (long long)m);
     FL_CUDA(ctx, cudaMemsetAsync(s->gram, 0, sizeof(double) * b * b, st));
+    FL_CUDA(ctx, cudaMemsetAsync(s->partials, 0, sizeof(double) * 3 * 2 * b, st));
     FL_CUDA(ctx, cudaMemsetAsync(ctx->d_barrier, 0, 2 * sizeof(unsigned), st));
     {
       double* tau = s->tau + p * b;
