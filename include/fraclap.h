@@ -214,6 +214,21 @@ int fraclap_dgemm(fraclap_ctx* ctx, int trans_a, int trans_b, int64_t m, int64_t
                   double alpha, const double* A_dev, int64_t lda, const double* B_dev,
                   int64_t ldb, double beta, double* C_dev, int64_t ldc, fraclap_stream_t stream);
 
+/* C = alpha * op(A) * op(B) + beta * C in FP32 (column-major), the engine of
+ * the FP32 stages of eig_full_mixed.  route 1: tensor cores, three TF32
+ * products A_hi B_hi + A_hi B_lo + A_lo B_hi of the operands split as
+ * x = tf32(x) + tf32(x - tf32(x)) (FP32-level accuracy; taken when m >= 128,
+ * n >= 64, k >= 64, else the SIMT kernel); route 0: FP32 FMA kernel.
+ * form 0: plain; 1: A symmetric, only its lower triangle read (trans_a = 0,
+ * m = k); 2: only the lower triangle of C (i >= j) is written.
+ * work_dev: device scratch of fraclap_sgemm_workspace_bytes(m, n, k) bytes
+ * (256-byte aligned; NULL: the context allocates it). */
+size_t fraclap_sgemm_workspace_bytes(int64_t m, int64_t n, int64_t k);
+int fraclap_sgemm(fraclap_ctx* ctx, int trans_a, int trans_b, int form, int64_t m, int64_t n, int64_t k,
+                  float alpha, const float* A_dev, int64_t lda, const float* B_dev, int64_t ldb,
+                  float beta, float* C_dev, int64_t ldc, int route, void* work_dev, size_t work_bytes,
+                  fraclap_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; it reports per-phase wall
  * times, Table I, and these give the same view of this library).

@@ -20,6 +20,7 @@ from ._binding import (  # noqa: F401
     tridiagonalize,
     tridiag_eig,
     dgemm,
+    sgemm,
     dgemm_ozaki,
     solve,
     default_context,

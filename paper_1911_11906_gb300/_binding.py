@@ -43,6 +43,9 @@ SIGNATURES = {
     "fraclap_dgemm_ozaki": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64,
                                    _i32, _p, _sz, _p]),
     "fraclap_dgemm": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64, _p]),
+    "fraclap_sgemm_workspace_bytes": (ctypes.c_size_t, [_i64, _i64, _i64]),
+    "fraclap_sgemm": (_i32, [_p, _i32, _i32, _i32, _i64, _i64, _i64, ctypes.c_float, _p, _i64, _p, _i64,
+                             ctypes.c_float, _p, _i64, _i32, _p, ctypes.c_size_t, _p]),
 }
 
 
@@ -326,6 +329,34 @@ def dgemm(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, alpha=
     st = ctypes.c_void_p(_stream(stream))
     ctx.check(ctx.lib.fraclap_dgemm(ctx.handle, int(trans_a), int(trans_b), m, n, k, float(alpha), _ptr(A),
                                     _ld(A), _ptr(B), _ld(B), float(beta), _ptr(C), _ld(C), st))
+    ctx.sync(stream)
+    return C
+
+
+def sgemm(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, alpha=1.0, beta=0.0,
+          C: torch.Tensor | None = None, form: int = 0, route: int = 1, ctx: Context | None = None,
+          stream=None) -> torch.Tensor:
+    """C = alpha op(A) op(B) + beta C in FP32: route 1 on the tensor cores (three TF32
+    products), route 0 on the FP32 FMA kernel.  form 1: A symmetric (lower triangle read);
+    form 2: only the lower triangle of C written."""
+    ctx = ctx or default_context()
+    for t, name in ((A, "A"), (B, "B")):
+        if t.dtype != torch.float32 or not t.is_cuda:
+            raise TypeError(f"{name} must be a float32 CUDA tensor")
+    A = A if A.stride(0) == 1 else A.t().contiguous().t()
+    B = B if B.stride(0) == 1 else B.t().contiguous().t()
+    m = A.shape[1] if trans_a else A.shape[0]
+    k = A.shape[0] if trans_a else A.shape[1]
+    n = B.shape[0] if trans_b else B.shape[1]
+    if C is None:
+        C = torch.zeros((n, m), dtype=torch.float32, device=A.device).t()
+        beta = 0.0
+    ws = ctx.lib.fraclap_sgemm_workspace_bytes(m, n, k)
+    work = torch.empty(ws, dtype=torch.uint8, device=A.device)
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.fraclap_sgemm(ctx.handle, int(trans_a), int(trans_b), int(form), m, n, k, float(alpha),
+                                    _ptr(A), _ld(A), _ptr(B), _ld(B), float(beta), _ptr(C), _ld(C), int(route),
+                                    _ptr(work), ws, st))
     ctx.sync(stream)
     return C
 

@@ -19,6 +19,8 @@ struct fraclap_ctx {
   double wait_timeout_s = 10.0;
   int tensor_route = 1;          // slice products: 1 = tcgen05 + TMA, 0 = mma.sync
   double refine_tau = 1e-3;      // first-order coefficient above which a pair is clustered
+  void* tc_scratch = nullptr;    // split operands of the TF32 tensor-core route of FP32 GEMMs
+  size_t tc_scratch_bytes = 0;   // (set by the caller of the FP32 stages, null otherwise)
   long long wait_cycles = 0;     // wait_timeout_s in SM clock cycles (upper bound)
   int32_t* d_status = nullptr;   // device status word (0 = ok, else a FRACLAP_ERR_*)
   unsigned* d_barrier = nullptr; // grid-barrier state for cooperative kernels
@@ -185,6 +187,13 @@ using GemmDesc = GemmDescT<double>;
 template <class T>
 int gemm(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDescT<T>& d, int split_k,
          cudaStream_t st);
+// FP32 GEMM on the tensor cores (three TF32 products, FP32-level accuracy),
+// through the split-operand scratch in ctx->tc_scratch; gemm<float> takes
+// this route when tf32_route_fits (modes Plain, SymA, LowerC; M >= 128,
+// N >= 64, K + K2 >= 64, no split-K, tensor route 1, scratch large enough).
+size_t tf32_split_bytes(int64_t M, int64_t N, int64_t K);
+bool tf32_route_fits(const fraclap_ctx* ctx, GemmMode mode, const GemmDescT<float>& d, int split_k);
+int gemm_tf32x3(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDescT<float>& d, cudaStream_t st);
 // Batched over a device array of descriptors; grid covers max_m x max_n tiles,
 // tiles outside a descriptor's M x N exit.  Descriptors with M, N or K <= 0
 // are skipped.

@@ -168,3 +168,42 @@ def test_tcgen05_slice_products_match_mma_sync_route(m, n, k):
     scale = np.abs(A).max(axis=0)[:, None] * np.abs(B).max(axis=0)[None, :] * k
     assert np.max(np.abs(out[0] - out[1]) / scale) <= 1e-16
     assert np.max(np.abs(out[0] - ref) / scale) <= 1e-15
+
+
+def _f32_colmajor(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32).T)).cuda().t()
+
+
+@pytest.mark.parametrize("route", [1, 0])
+@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("m,n,k", [(128, 64, 64), (130, 70, 300), (300, 257, 1000), (1000, 129, 64), (64, 40, 30)])
+def test_sgemm_fp32_accurate(route, form, ta, tb, m, n, k):
+    """FP32 GEMM (tensor-core route: three TF32 products; FMA route) against an
+    FP64 product of the same FP32 inputs, relative to sum_k |a_ik| |b_kj|."""
+    F = _F()
+    if form == 1:
+        if ta or m != k:
+            pytest.skip("symmetric A is square and untransposed")
+    rng = np.random.default_rng(m * 7 + n * 3 + k + form)
+    A = rng.standard_normal((k, m) if ta else (m, k)).astype(np.float32)
+    if form == 1:
+        A = np.tril(A) + np.tril(A, -1).T  # only the lower triangle is read
+        A_stored = np.tril(A) + 1e3 * np.triu(np.ones_like(A), 1)  # garbage above
+    else:
+        A_stored = A
+    B = rng.standard_normal((n, k) if tb else (k, n)).astype(np.float32)
+    C0 = rng.standard_normal((m, n)).astype(np.float32)
+    opA = (A.T if ta else A).astype(np.float64)
+    opB = (B.T if tb else B).astype(np.float64)
+    ref = 0.5 * opA @ opB - 2.0 * C0.astype(np.float64)
+    scale = 0.5 * np.abs(opA) @ np.abs(opB) + 2.0 * np.abs(C0.astype(np.float64))
+    C = _f32_colmajor(C0)
+    F.sgemm(_f32_colmajor(A_stored), _f32_colmajor(B), trans_a=ta, trans_b=tb, alpha=0.5, beta=-2.0, C=C,
+            form=form, route=route)
+    got = C.cpu().numpy().astype(np.float64)
+    if form == 2:
+        low = np.tril(np.ones((m, n), bool))
+        assert np.array_equal(got[~low], C0.astype(np.float64)[~low])  # untouched above the diagonal
+        got, ref, scale = got[low], ref[low], scale[low]
+    assert np.max(np.abs(got - ref) / scale) <= 4e-6
