@@ -240,7 +240,9 @@ int sy2sb_run(fraclap_ctx* ctx, T* Aw, int64_t n, int64_t lda, int b, T* band, S
     // XT = V T  (m x b)
     FL_TRY(gemm<T>(ctx, false, false, kGemmPlain, D{m, b, b, V, m, Tf, b, s->XT, m, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
     // X = A22 XT (A22 symmetric, lower triangle)
-    FL_TRY(gemm<T>(ctx, false, false, kGemmSymA, D{m, b, m, A22, lda, s->XT, m, s->X, m, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
+    // (b columns only: split over the long dimension so that the grid fills the GPU)
+    FL_CUDA(ctx, cudaMemsetAsync(s->X, 0, sizeof(T) * m * b, st));
+    FL_TRY(gemm<T>(ctx, false, false, kGemmSymA, D{m, b, m, A22, lda, s->XT, m, s->X, m, nullptr, 0, nullptr, 0, 0, 1.0, 1.0}, (int)std::min<int64_t>(cdiv(m, 1024), 16), st));
     // Y = V^T X  (b x b), split over the long dimension
     FL_CUDA(ctx, cudaMemsetAsync(s->Y, 0, sizeof(T) * b * b, st));
     FL_TRY(gemm<T>(ctx, true, false, kGemmPlain, D{b, b, m, V, m, s->X, m, s->Y, b, nullptr, 0, nullptr, 0, 0, 1.0, 1.0}, (int)cdiv(m, 256), st));
@@ -271,8 +273,9 @@ int q1_apply_run(fraclap_ctx* ctx, const Stage1T<T>* s, int64_t n, int b, T* Z, 
     const T* V = s->Vstore + voff;
     const T* Tf = s->Tstore + p * b * b;
     T* Zr = Z + (j0 + b);
-    // W1 = V^T Zr  (b x ncols)
-    FL_TRY(gemm<T>(ctx, true, false, kGemmPlain, D{b, ncols, m, V, m, Zr, ldz, W1, b, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
+    // W1 = V^T Zr  (b x ncols), split over the long dimension m
+    FL_CUDA(ctx, cudaMemsetAsync(W1, 0, sizeof(T) * b * ncols, st));
+    FL_TRY(gemm<T>(ctx, true, false, kGemmPlain, D{b, ncols, m, V, m, Zr, ldz, W1, b, nullptr, 0, nullptr, 0, 0, 1.0, 1.0}, (int)std::min<int64_t>(cdiv(m, 1024), 16), st));
     // W2 = T W1
     FL_TRY(gemm<T>(ctx, false, false, kGemmPlain, D{b, ncols, b, Tf, b, W1, b, W2, b, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
     // Zr -= V W2
