@@ -230,6 +230,46 @@ int fraclap_sgemm(fraclap_ctx* ctx, int trans_a, int trans_b, int form, int64_t 
                   fraclap_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * fraclap_solve_batched — many independent problems (masked grids of their
+ * own size, forcings and orders) in one call: for each problem the
+ * eigendecomposition (as eig_full, or eig_full_mixed when the problem
+ * carries its CSR; band width 32) of its dense A into
+ * lambda_dev / V_dev and, when k > 0, the spectral apply of its k pairs into
+ * U_dev (as frac_apply; Sec. II eq. poisson_solution).  The problems are
+ * spread over `workers` concurrent streams (0: 16), each with its own share
+ * of the SMs and a context-owned workspace sized for its largest problem;
+ * the caller's stream waits for all of them.  probs is a host array; every
+ * pointer in it is a device pointer owned by the caller, and distinct
+ * problems must not share outputs.  Device errors reach the context's status
+ * word (fraclap_sync); argument errors name the problem.
+ * ---------------------------------------------------------------------- */
+typedef struct fraclap_problem {
+  int64_t n;
+  const double* A_dev;        /* n x n, column-major, lower triangle read */
+  int64_t lda;
+  double* lambda_dev;         /* n, ascending */
+  double* V_dev;              /* n x n eigenvectors */
+  int64_t ldv;
+  const double* F_dev;        /* n x m forcings (may be NULL when k = 0) */
+  int64_t ldf;
+  int64_t m;
+  const int32_t* pair_f_dev;  /* k forcing columns */
+  const double* pair_alpha_dev; /* k orders */
+  int64_t k;
+  double* U_dev;              /* n x k solutions */
+  int64_t ldu;
+  /* optional CSR of the same A (as fd_assemble writes it): when rowptr_dev is
+   * not NULL the problem takes the mixed route of eig_full_mixed with
+   * refine_iters refinement iterations (1..8) instead of the FP64 route */
+  const int64_t* rowptr_dev;
+  const int32_t* col_dev;
+  const double* val_dev;
+  int refine_iters;
+} fraclap_problem;
+int fraclap_solve_batched(fraclap_ctx* ctx, const fraclap_problem* probs, int count, int workers,
+                          fraclap_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; it reports per-phase wall
  * times, Table I, and these give the same view of this library).
  * ---------------------------------------------------------------------- */

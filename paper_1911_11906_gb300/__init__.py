@@ -23,5 +23,6 @@ from ._binding import (  # noqa: F401
     sgemm,
     dgemm_ozaki,
     solve,
+    solve_batched,
     default_context,
 )

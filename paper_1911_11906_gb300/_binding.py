@@ -44,6 +44,7 @@ SIGNATURES = {
                                    _i32, _p, _sz, _p]),
     "fraclap_dgemm": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64, _p]),
     "fraclap_sgemm_workspace_bytes": (ctypes.c_size_t, [_i64, _i64, _i64]),
+    "fraclap_solve_batched": (_i32, [_p, _p, _i32, _i32, _p]),
     "fraclap_sgemm": (_i32, [_p, _i32, _i32, _i32, _i64, _i64, _i64, ctypes.c_float, _p, _i64, _p, _i64,
                              ctypes.c_float, _p, _i64, _i32, _p, ctypes.c_size_t, _p]),
 }
@@ -359,6 +360,59 @@ def sgemm(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, alpha=
                                     _ptr(work), ws, st))
     ctx.sync(stream)
     return C
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("A_dev", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("lambda_dev", ctypes.c_void_p), ("V_dev", ctypes.c_void_p), ("ldv", ctypes.c_int64),
+                ("F_dev", ctypes.c_void_p), ("ldf", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("pair_f_dev", ctypes.c_void_p), ("pair_alpha_dev", ctypes.c_void_p), ("k", ctypes.c_int64),
+                ("U_dev", ctypes.c_void_p), ("ldu", ctypes.c_int64),
+                ("rowptr_dev", ctypes.c_void_p), ("col_dev", ctypes.c_void_p), ("val_dev", ctypes.c_void_p),
+                ("refine_iters", ctypes.c_int)]
+
+
+def solve_batched(problems, workers: int = 0, ctx: Context | None = None, stream=None) -> list:
+    """Eigendecomposition (FP64 route) and spectral apply of many independent problems in
+    one call.  problems: list of dicts with "A" (n x n float64 CUDA tensor) and optionally
+    "F" (n x m), "pair_f", "pair_alpha" (k pairs), and "rowptr", "col", "val" (the CSR of A:
+    the mixed route, with "refine_iters", default 6).  Returns per problem (lam, V, U or None)."""
+    ctx = ctx or default_context()
+    arr = (_Problem * max(len(problems), 1))()
+    keep, out = [], []
+    for i, pr in enumerate(problems):
+        A = _f64_colmajor(pr["A"], "A") if pr["A"].numel() else pr["A"]
+        n = int(pr["A"].shape[0])
+        dev = pr["A"].device
+        lam = torch.empty(n, dtype=torch.float64, device=dev)
+        V = empty_colmajor(n, n, dev)
+        U = None
+        k = 0
+        if pr.get("pair_f") is not None and len(pr["pair_f"]) and n:
+            Fm = _f64_colmajor(pr["F"], "F")
+            pf = torch.as_tensor(np.asarray(pr["pair_f"], dtype=np.int32)).to(dev)
+            pa = torch.as_tensor(np.asarray(pr["pair_alpha"], dtype=np.float64)).to(dev)
+            k = int(pf.numel())
+            U = empty_colmajor(n, k, dev)
+            keep += [Fm, pf, pa]
+            arr[i].F_dev, arr[i].ldf, arr[i].m = Fm.data_ptr(), _ld(Fm), Fm.shape[1]
+            arr[i].pair_f_dev, arr[i].pair_alpha_dev = pf.data_ptr(), pa.data_ptr()
+            arr[i].U_dev, arr[i].ldu = U.data_ptr(), _ld(U)
+        arr[i].n, arr[i].k = n, k
+        if pr.get("rowptr") is not None and n:
+            keep += [pr["rowptr"], pr["col"], pr["val"]]
+            arr[i].rowptr_dev, arr[i].col_dev, arr[i].val_dev = (pr["rowptr"].data_ptr(), pr["col"].data_ptr(),
+                                                                 pr["val"].data_ptr())
+            arr[i].refine_iters = int(pr.get("refine_iters", 6))
+        if n:
+            keep.append(A)
+            arr[i].A_dev, arr[i].lda = A.data_ptr(), _ld(A)
+            arr[i].lambda_dev, arr[i].V_dev, arr[i].ldv = lam.data_ptr(), V.data_ptr(), _ld(V)
+        out.append((lam, V, U))
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.fraclap_solve_batched(ctx.handle, arr, len(problems), int(workers), st))
+    ctx.sync(stream)
+    return out
 
 
 def dgemm_ozaki(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, alpha=1.0, beta=0.0,

@@ -253,6 +253,10 @@ extern "C" int fraclap_create(fraclap_ctx** out, const fraclap_opts* opts) {
 extern "C" void fraclap_destroy(fraclap_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
+  for (fraclap_ctx* w : ctx->workers) fraclap_destroy(w);
+  for (cudaStream_t s : ctx->worker_streams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : ctx->worker_events) cudaEventDestroy(e);
+  if (ctx->batch_start) cudaEventDestroy(ctx->batch_start);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_barrier) cudaFree(ctx->d_barrier);

@@ -34,6 +34,12 @@ struct fraclap_ctx {
   // per refinement iteration: delta, ||S-D||_2 est, ||R||_2 est, ||S-D||_F,
   // ||R||_F, ||A||_2 bound, clusters, largest cluster
   std::vector<double> refine_stats;
+  // workers of the batched solver (created on first use): sub-contexts with
+  // a share of the SMs, their streams and completion events
+  std::vector<fraclap_ctx*> workers;
+  std::vector<cudaStream_t> worker_streams;
+  std::vector<cudaEvent_t> worker_events;
+  cudaEvent_t batch_start = nullptr;
 };
 
 namespace fraclap {

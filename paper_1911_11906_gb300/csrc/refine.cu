@@ -2,21 +2,28 @@
 // (T. Ogita, K. Aishima, JJIAM 35, 2018; clustered eigenvalues: JJIAM 36,
 // 2019), written from the method's mathematics.  One iteration, with X the
 // current approximate eigenvector matrix (FP64, n x n):
-//   R = I - X^T X,  S = X^T A X                 (FP64, lower triangles)
+//   R = I - X^T X,  S = X^T A X   (FP64-accurate products on the tensor
+//                                  cores, lower triangles)
 //   l_i = s_ii / (1 - r_ii)
-//   delta = 2 (||S - diag(l)||_F + ||A||_2 ||R||_F)
-//   E_ij = (s_ij + l_j r_ij) / (l_j - l_i)   if |l_j - l_i| > delta
-//        = r_ij / 2                           otherwise (and on the diagonal)
-//   X <- X + X E                               (the product in FP32: E is small)
-// then the columns are sorted by l, and every cluster is diagonalised exactly:
-// S_c = X_c^T A X_c (FP64), Jacobi on S_c, X_c <- X_c Q_c.  A cluster is a run
-// of sorted positions joined by "unsafe" pairs: |l_j - l_i| <= delta (the
-// method's own test), or a first-order coefficient |E_ij| above 1e-2, whose
-// second-order error would spoil the quadratic convergence when the starting
-// vectors are only FP32-accurate (this safeguard is ours).  Using the lower triangles of R and S as symmetric
-// matrices keeps E_ij + E_ji = r_ij, so orthogonality improves to first order
-// exactly.  A enters only through products with its CSR form (5/7 nonzeros
-// per row).
+//   delta = 2 (||S - diag(l)||_2 + ||A||_2 ||R||_2)   (2-norms by power
+//          iteration, x2, capped by the Frobenius norms; ||A||_2 <= Gershgorin)
+//   E_ij = (s_ij + l_j r_ij) / (l_j - l_i)   off the clusters
+//        = r_ij / 2                           inside them and on the diagonal
+//   X <- X + X E                               (X E in FP32 precision: its
+//                                              error is removed next time)
+// then the columns are sorted by l, and every cluster is diagonalised on the
+// pencil (X_c^T A X_c, X_c^T X_c): after the first-order update X_c is
+// orthonormal only to second order in the outer coefficients, and the plain
+// problem of X_c^T A X_c would leave mixing of order l |X_c^T X_c - I| / gap.
+// A cluster is a run of sorted positions joined by "unsafe" pairs:
+// |l_j - l_i| <= delta (the method's own test), or a first-order coefficient
+// above the context's threshold (1e-3 by default), whose second-order error
+// would spoil the quadratic convergence when the starting vectors are only
+// FP32-accurate (this safeguard is ours).  Using the lower triangles of R and
+// S as symmetric matrices keeps E_ij + E_ji = r_ij, so orthogonality improves
+// to first order exactly.  A enters only through products with its CSR form
+// (5/7 nonzeros per row).  The eigenvalues returned are the Rayleigh
+// quotients of the refined vectors.
 #include <string.h>
 
 #include <algorithm>
@@ -826,8 +833,10 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
     FL_CUDA(ctx, cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
     FL_CUDA(ctx, cudaStreamSynchronize(st));
     std::vector<int> cl(2 * (size_t)std::max(ncl, 0));
-    if (ncl > 0)
-      FL_CUDA(ctx, cudaMemcpy(cl.data(), clist + 1, sizeof(int) * 2 * ncl, cudaMemcpyDeviceToHost));
+    if (ncl > 0) {  // on the caller's stream: other streams keep running
+      FL_CUDA(ctx, cudaMemcpyAsync(cl.data(), clist + 1, sizeof(int) * 2 * ncl, cudaMemcpyDeviceToHost, st));
+      FL_CUDA(ctx, cudaStreamSynchronize(st));
+    }
     {
       unsigned long long nab;
       memcpy(&nab, &hs[2], sizeof(nab));

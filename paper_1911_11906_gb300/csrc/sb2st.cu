@@ -513,7 +513,7 @@ int q2_apply_run(fraclap_ctx* ctx, const Stage2T<T>* s, int64_t n, int b, T* Z, 
   FL_Q2T(8, 2)
   FL_Q2T(16, 4)
   FL_Q2T(32, 8)
-  FL_Q2T(64, 8)
+  FL_Q2T(64, 4)
 #undef FL_Q2T
   FL_CHECK(ctx, cpw != 0, FRACLAP_ERR_UNSUPPORTED, "q2 back-transformation: band width %d not in {4, 8, 16, 32, 64}", b);
   FL_CUDA(ctx, cudaGetLastError());

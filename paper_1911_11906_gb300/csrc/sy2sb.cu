@@ -16,6 +16,7 @@ namespace fraclap {
 namespace {
 
 constexpr int PQR_NT = 256;
+constexpr int kPanelSmemMax = 180 * 1024;  // largest panel slice one CTA holds
 
 // Cooperative panel QR.  P: m x bw panel (ld ldp) in the working matrix.
 // On exit P holds R on and above its diagonal (the band block) and the
@@ -217,7 +218,7 @@ int sy2sb_run(fraclap_ctx* ctx, T* Aw, int64_t n, int64_t lda, int b, T* band, S
     int64_t rows_per_cta;
     size_t smem;
     const int G = panel_grid(ctx, m, b, sizeof(T), &rows_per_cta, &smem);
-    FL_CHECK(ctx, smem <= 180 * 1024, FRACLAP_ERR_UNSUPPORTED, "sy2sb: panel too tall (%lld)", (long long)m);
+    FL_CHECK(ctx, smem <= (size_t)kPanelSmemMax, FRACLAP_ERR_UNSUPPORTED, "sy2sb: panel too tall (%lld)", (long long)m);
     FL_CUDA(ctx, cudaMemsetAsync(s->gram, 0, sizeof(double) * b * b, st));
     FL_CUDA(ctx, cudaMemsetAsync(s->partials, 0, sizeof(double) * 3 * 2 * b, st));
     FL_CUDA(ctx, cudaMemsetAsync(ctx->d_barrier, 0, 2 * sizeof(unsigned), st));
@@ -231,7 +232,9 @@ int sy2sb_run(fraclap_ctx* ctx, T* Aw, int64_t n, int64_t lda, int b, T* band, S
       long long limit = ctx->wait_cycles;
       int32_t* status = ctx->d_status;
       void* args[] = {&P, &ldp, &mm, &bw, &V, &ldv, &tau, &Tf, &partials, &gram, &bar, &limit, &status, &rows_per_cta};
-      FL_CUDA(ctx, cudaFuncSetAttribute(panel_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      // the permitted maximum, not this panel's size: the attribute belongs to
+      // the function, and concurrent callers on other streams share it
+      FL_CUDA(ctx, cudaFuncSetAttribute(panel_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmemMax));
       count_launch(ctx);
       FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)panel_qr_kernel<T>, dim3(G), dim3(PQR_NT), args, smem, st));
     }

@@ -1,0 +1,126 @@
+"""GPU parity at the benchmark's full size: the 128 x 128 six-ellipse grid
+(n = 8810, 16 forcings x 8 orders), both eigensolver routes, with the
+launch configuration of the benchmark (band width 64, refinement cap 6).
+
+The oracle cannot decompose n = 8810 inside a test, so the checks are the
+ones it can compute one by one or that hold at any size: every alpha = 2
+solution against the oracle's banded direct solve, eigenvalue brackets at
++-1e-11 from the oracle's inertia counts at sampled indices, the trace
+identity sum(lambda) = 4 n / h^2, orthogonality of sampled columns, and
+residuals A v - lambda v of sampled columns (A from the oracle's assembly).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1911_11906_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _bracketed(A, lam, i, rel=1e-11):
+    """An exact eigenvalue with index i lies within rel |lam_i| of lam_i (inertia
+    counts of the oracle's banded LDL^T, which does not pivot)."""
+    return O.count_below(A, lam[i] * (1 - rel)) <= i < O.count_below(A, lam[i] * (1 + rel))
+
+
+def _bracket_indices(lam, want, diag):
+    """Indices to bracket, skipping eigenvalues at the diagonal value 2 dim / h^2:
+    there A - sigma I has a vanishing diagonal (on a bipartite grid graph that
+    value is often a multiple eigenvalue) and the unpivoted LDL^T of the inertia
+    count breaks down."""
+    return [i for i in want if abs(lam[i] - diag) > 1e-8 * diag]
+
+
+@pytest.fixture(scope="module")
+def workload():
+    p = I.ellipse_problem()
+    _, A = O.assemble(p.mask, p.h)
+    refs = {j: O.band_solve(A, p.F[:, p.pair_f[j]]) for j in np.nonzero(p.pair_alpha == 2.0)[0]}
+    return p, A, refs
+
+
+@pytest.mark.parametrize("route", ["mixed", "fp64"])
+def test_full_size_workload(workload, route):
+    import paper_1911_11906_gb300 as F
+    p, A, refs = workload
+    assert p.n == 8810
+    ctx = F.Context(band_width=64)
+    mask = torch.from_numpy(p.mask).cuda()
+    asm = F.fd_assemble(mask, p.h, ctx=ctx)
+    if route == "mixed":
+        lam, V = F.eig_full_mixed(asm["A"], asm["rowptr"], asm["col"], asm["val"], refine_iters=6, ctx=ctx)
+    else:
+        lam, V = F.eig_full(asm["A"], ctx=ctx)
+    Fd = torch.from_numpy(np.ascontiguousarray(p.F.T)).cuda().t()
+    U = F.frac_apply(V, lam, Fd, p.pair_f, p.pair_alpha, ctx=ctx).cpu().numpy()
+    lam_h = lam.cpu().numpy()
+    assert np.all(np.diff(lam_h) >= 0)
+    for j, ref in refs.items():
+        assert np.linalg.norm(U[:, j] - ref) <= 1e-10 * np.linalg.norm(ref)
+    rng = np.random.default_rng(8810)
+    want = sorted(rng.choice(p.n, size=12, replace=False).tolist()) + [0, p.n - 1]
+    for i in _bracket_indices(lam_h, want, 4.0 / p.h ** 2):
+        assert _bracketed(A, lam_h, i), i
+    tr = 4 * p.n / p.h ** 2
+    assert abs(lam_h.sum() - tr) <= 1e-12 * tr
+    cols = np.sort(rng.choice(p.n, size=32, replace=False))
+    Vc = V[:, torch.from_numpy(cols).cuda()]
+    G = (V.t() @ Vc).cpu().numpy()
+    G[cols, np.arange(cols.size)] -= 1.0
+    assert np.abs(G).max() <= 1e-12
+    Vc = Vc.cpu().numpy()
+    nA = 8.0 / p.h ** 2
+    for t, i in enumerate(cols):
+        r = O.spmv(A, Vc[:, t]) - lam_h[i] * Vc[:, t]
+        assert np.linalg.norm(r) <= 1e-12 * nA
+
+
+def test_batched_problems_match_oracle():
+    """Many uneven masked grids in one call (FP64 route, or the mixed route for
+    every third problem): every
+    alpha = 2 solution against the oracle's direct solve, eigenvalues of the
+    small problems against the oracle's full decomposition, brackets from
+    inertia counts and the trace for the others; an empty problem and a
+    decomposition-only problem ride along."""
+    import paper_1911_11906_gb300 as F
+    probs = I.batched_problems(32)
+    items = []
+    for j, p in enumerate(probs):
+        _, A = O.assemble(p.mask, p.h)
+        D = torch.from_numpy(np.ascontiguousarray(A.dense().T)).cuda().t()
+        item = {"A": D}
+        if j % 3 == 1:  # these take the mixed route (FP32 stages + refinement)
+            item.update(rowptr=torch.from_numpy(A.rowptr).cuda(), col=torch.from_numpy(A.col).cuda(),
+                        val=torch.from_numpy(A.val).cuda(), refine_iters=6)
+        if j != 5:  # problem 5: decomposition only
+            item.update(F=torch.from_numpy(np.ascontiguousarray(p.F.T)).cuda().t(), pair_f=p.pair_f,
+                        pair_alpha=p.pair_alpha)
+        items.append((p, A, item))
+    batch = [it for _, _, it in items]
+    batch.insert(7, {"A": torch.empty((0, 0), dtype=torch.float64, device="cuda")})
+    ctx = F.Context()
+    out = F.solve_batched(batch, workers=8, ctx=ctx)
+    out.pop(7)
+    assert len(out) == len(items)
+    for j, ((p, A, it), (lam, V, U)) in enumerate(zip(items, out)):
+        lam_h = lam.cpu().numpy()
+        assert np.all(np.diff(lam_h) >= 0)
+        tr = 4 * p.n / p.h ** 2
+        assert abs(lam_h.sum() - tr) <= 1e-12 * tr
+        if p.n <= 700:
+            lam_o, _ = O.eig_full(A.dense())
+            assert np.max(np.abs(lam_h - lam_o) / lam_o) <= 1e-11
+        else:
+            for i in _bracket_indices(lam_h, (0, p.n // 3, p.n // 2, p.n - 1), 4.0 / p.h ** 2):
+                assert _bracketed(A, lam_h, i), (j, i)
+        if j == 5:
+            assert U is None
+            continue
+        Uh = U.cpu().numpy()
+        for q in np.nonzero(p.pair_alpha == 2.0)[0]:
+            ref = O.band_solve(A, p.F[:, p.pair_f[q]])
+            assert np.linalg.norm(Uh[:, q] - ref) <= 1e-10 * np.linalg.norm(ref)
+        Vh = V.cpu().numpy()
+        assert np.max(np.abs(Vh.T @ Vh - np.eye(p.n))) <= 1e-12
