@@ -151,6 +151,12 @@ int eig_full_mixed(fraclap_ctx* ctx, const double* A_dev, int64_t n, int64_t lda
  *  coefficients).
  * ---------------------------------------------------------------------- */
 size_t fraclap_apply_workspace_bytes(int64_t n, int64_t m, int64_t k);
+/* The same for this context's setting of fraclap_set_apply_slices. */
+size_t fraclap_apply_workspace_bytes_ctx(const fraclap_ctx* ctx, int64_t n, int64_t m, int64_t k);
+/* Products of frac_apply: 0 (default) on the FP64 GEMM engine; s = 1..8 as
+ * products of s BF16 slices on the tensor cores (error about 2^-8s relative
+ * to |row max| |column max| per term; s = 7 is FP64-level, s = 5 about 1e-12). */
+int fraclap_set_apply_slices(fraclap_ctx* ctx, int slices);
 int frac_apply(fraclap_ctx* ctx, const double* V_dev, int64_t ldv, const double* lambda_dev,
                int64_t n, const double* F_dev, int64_t ldf, int64_t m,
                const int32_t* pair_f_dev, const double* pair_alpha_dev, int64_t k,

@@ -45,6 +45,8 @@ SIGNATURES = {
     "fraclap_dgemm": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64, _p]),
     "fraclap_sgemm_workspace_bytes": (ctypes.c_size_t, [_i64, _i64, _i64]),
     "fraclap_solve_batched": (_i32, [_p, _p, _i32, _i32, _p]),
+    "fraclap_apply_workspace_bytes_ctx": (ctypes.c_size_t, [_p, _i64, _i64, _i64]),
+    "fraclap_set_apply_slices": (_i32, [_p, _i32]),
     "fraclap_sgemm": (_i32, [_p, _i32, _i32, _i32, _i64, _i64, _i64, ctypes.c_float, _p, _i64, _p, _i64,
                              ctypes.c_float, _p, _i64, _i32, _p, ctypes.c_size_t, _p]),
 }
@@ -147,6 +149,10 @@ class Context:
     def set_refine_tau(self, tau: float):
         """Refinement safeguard: pairs with a first-order coefficient above tau are clustered."""
         self.check(self.lib.fraclap_set_refine_tau(self.handle, float(tau)))
+
+    def set_apply_slices(self, slices: int):
+        """frac_apply products: 0 = FP64 engine; s = 1..8 BF16 slices on the tensor cores."""
+        self.check(self.lib.fraclap_set_apply_slices(self.handle, int(slices)))
 
     def set_tensor_route(self, route: int):
         """1: tcgen05 + TMA slice products (default); 0: mma.sync."""
@@ -272,7 +278,7 @@ def frac_apply(V: torch.Tensor, lam: torch.Tensor, F: torch.Tensor, pair_f, pair
     k, m = pf.numel(), F.shape[1]
     U = out if out is not None else empty_colmajor(n, k, dev)
     if workspace is None:
-        nbytes = ctx.lib.fraclap_apply_workspace_bytes(n, m, k)
+        nbytes = ctx.lib.fraclap_apply_workspace_bytes_ctx(ctx.handle, n, m, k)
         workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
     st = ctypes.c_void_p(_stream(stream))
     ctx.check(ctx.lib.frac_apply(ctx.handle, _ptr(V), _ld(V), _ptr(lam.contiguous()), n, _ptr(F), _ld(F), m,

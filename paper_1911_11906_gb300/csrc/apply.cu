@@ -1,10 +1,13 @@
 // frac_apply: u_j = V diag(lambda^{-alpha_j/2}) V^T f_{pair_f[j]}
 // (Sec. II, eq. poisson_solution; the sum v after eq. discrete_laplace).
 //
-// Two FP64 GEMMs on the engine (W = V^T F over the m distinct forcings, then
-// U = V C) around an elementwise kernel that forms the spectral
-// coefficients C(i, j) = lambda_i^{-alpha_j/2} W(i, pair_f[j]); pow() is
-// CUDA's double-precision pow.  A zero or negative eigenvalue met with
+// Two GEMMs (W = V^T F over the m distinct forcings, then U = V C) around an
+// elementwise kernel that forms the spectral coefficients
+// C(i, j) = lambda_i^{-alpha_j/2} W(i, pair_f[j]); pow() is CUDA's
+// double-precision pow.  The GEMMs run on the FP64 engine, or (context
+// setting apply_slices = s > 0) as products of s BF16 slices on the tensor
+// cores, accurate to about 2^-8s relative to |row max| |column max| per
+// term (s = 7: FP64 level).  A zero or negative eigenvalue met with
 // alpha != 0 raises FRACLAP_ERR_NOT_SPD in the device status.
 #include "internal.cuh"
 
@@ -44,6 +47,20 @@ extern "C" size_t fraclap_apply_workspace_bytes(int64_t n, int64_t m, int64_t k)
          align256(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(k > 0 ? k : 1)) + 512;
 }
 
+extern "C" size_t fraclap_apply_workspace_bytes_ctx(const fraclap_ctx* ctx, int64_t n, int64_t m, int64_t k) {
+  const size_t base = fraclap_apply_workspace_bytes(n, m, k);
+  if (!ctx || ctx->apply_slices <= 0 || base == 0) return base;
+  const int64_t nn = n > 0 ? n : 1;
+  return base + std::max(ozaki_ws(nn, m > 0 ? m : 1, nn, ctx->apply_slices),
+                         ozaki_ws(nn, k > 0 ? k : 1, nn, ctx->apply_slices)) + 1024;
+}
+
+extern "C" int fraclap_set_apply_slices(fraclap_ctx* ctx, int slices) {
+  if (!ctx || slices < 0 || slices > 8) return FRACLAP_ERR_INVALID_ARG;
+  ctx->apply_slices = slices;
+  return 0;
+}
+
 extern "C" int frac_apply(fraclap_ctx* ctx, const double* V_dev, int64_t ldv,
                           const double* lambda_dev, int64_t n, const double* F_dev, int64_t ldf,
                           int64_t m, const int32_t* pair_f_dev, const double* pair_alpha_dev,
@@ -60,21 +77,32 @@ extern "C" int frac_apply(fraclap_ctx* ctx, const double* V_dev, int64_t ldv,
   FL_CHECK(ctx, k <= 65535 * 64 && m <= 65535 * 64, FRACLAP_ERR_UNSUPPORTED, "frac_apply: too many pairs");
   StageTimer timer(ctx, kStageApply, st);
   Arena ar;
-  FL_TRY(get_workspace(ctx, work_dev, work_bytes, fraclap_apply_workspace_bytes(n, m, k), &ar));
+  FL_TRY(get_workspace(ctx, work_dev, work_bytes, fraclap_apply_workspace_bytes_ctx(ctx, n, m, k), &ar));
   double* W = ar.take<double>(n * m);
   double* C = ar.take<double>(n * k);
   FL_CHECK(ctx, W && C, FRACLAP_ERR_ALLOC, "frac_apply: workspace too small");
+  const int ozs = ctx->apply_slices;
   // W = V^T F
-  GemmDesc d{n, m, n, V_dev, ldv, F_dev, ldf, W, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
-  FL_TRY(gemm(ctx, true, false, kGemmPlain, d, 1, st));
+  if (ozs > 0) {
+    Arena oz = ar;
+    FL_TRY(ozaki_gemm(ctx, true, false, n, m, n, 1.0, V_dev, ldv, F_dev, ldf, 0.0, W, n, ozs, false, &oz, st));
+  } else {
+    GemmDesc d{n, m, n, V_dev, ldv, F_dev, ldf, W, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+    FL_TRY(gemm(ctx, true, false, kGemmPlain, d, 1, st));
+  }
   FL_CHECK(ctx, k <= 65535, FRACLAP_ERR_UNSUPPORTED, "frac_apply: at most 65535 pairs per call");
   spectral_scale<<<dim3((unsigned)cdiv(n, 256), (unsigned)k), 256, 0, st>>>(
       lambda_dev, n, W, n, pair_f_dev, pair_alpha_dev, k, m, C, n, ctx->d_status);
   count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
   // U = V C
-  d = GemmDesc{n, k, n, V_dev, ldv, C, n, U_dev, ldu, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
-  FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+  if (ozs > 0) {
+    Arena oz = ar;
+    FL_TRY(ozaki_gemm(ctx, false, false, n, k, n, 1.0, V_dev, ldv, C, n, 0.0, U_dev, ldu, ozs, false, &oz, st));
+  } else {
+    GemmDesc d{n, k, n, V_dev, ldv, C, n, U_dev, ldu, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+    FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+  }
   return 0;
 }
 

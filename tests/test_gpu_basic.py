@@ -207,3 +207,18 @@ def test_sgemm_fp32_accurate(route, form, ta, tb, m, n, k):
         assert np.array_equal(got[~low], C0.astype(np.float64)[~low])  # untouched above the diagonal
         got, ref, scale = got[low], ref[low], scale[low]
     assert np.max(np.abs(got - ref) / scale) <= 4e-6
+
+
+@pytest.mark.parametrize("slices,tol", [(7, 1e-13), (5, 1e-10), (3, 1e-5)])
+def test_frac_apply_tensor_slices(square_small, slices, tol):
+    """frac_apply with its products as BF16 slices on the tensor cores,
+    against the oracle's FP64 apply: 7 slices reach FP64 level, fewer slices
+    lose about 8 bits each."""
+    F = _F()
+    p, A, lam, V = square_small
+    U_o = O.frac_apply(V, lam, p.F, p.pair_f, p.pair_alpha)
+    ctx = F.Context()
+    ctx.set_apply_slices(slices)
+    U = F.frac_apply(_colmajor(V), _cuda(lam), _colmajor(p.F), p.pair_f, p.pair_alpha, ctx=ctx).cpu().numpy()
+    for j in range(U_o.shape[1]):
+        assert np.linalg.norm(U[:, j] - U_o[:, j]) <= tol * np.linalg.norm(U_o[:, j])

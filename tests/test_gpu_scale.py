@@ -124,3 +124,34 @@ def test_batched_problems_match_oracle():
             assert np.linalg.norm(Uh[:, q] - ref) <= 1e-10 * np.linalg.norm(ref)
         Vh = V.cpu().numpy()
         assert np.max(np.abs(Vh.T @ Vh - np.eye(p.n))) <= 1e-12
+
+
+def test_apply_at_scale():
+    """The apply workload at scale (192 x 192 grid, n = 18278, 4096 distinct
+    forcings with alpha ~ U(0.1, 1.9)), plus four alpha = 2 pairs that the
+    oracle's direct solve checks: FP64 products and 6 BF16 slices on the
+    tensor cores, each within 1e-10 of the direct solve, and within 1e-10 of
+    each other on every pair (5 slices missed the bar: about 2e-10)."""
+    import paper_1911_11906_gb300 as F
+    p = I.apply_at_scale_problem()
+    _, A = O.assemble(p.mask, p.h)
+    ctx = F.Context(band_width=64)
+    mask = torch.from_numpy(p.mask).cuda()
+    asm = F.fd_assemble(mask, p.h, ctx=ctx)
+    lam, V = F.eig_full_mixed(asm["A"], asm["rowptr"], asm["col"], asm["val"], refine_iters=6, ctx=ctx)
+    del asm
+    Fd = torch.from_numpy(np.ascontiguousarray(p.F.T)).cuda().t()
+    extra = [0, 1, 2, 3]
+    pf = np.concatenate([p.pair_f, np.array(extra, dtype=np.int32)])
+    pa = np.concatenate([p.pair_alpha, np.full(len(extra), 2.0)])
+    refs = [O.band_solve(A, p.F[:, f]) for f in extra]
+    outs = {}
+    for slices in (0, 6):
+        ctx.set_apply_slices(slices)
+        U = F.frac_apply(V, lam, Fd, pf, pa, ctx=ctx)
+        for t, ref in enumerate(refs):
+            u = U[:, p.F.shape[1] + t].cpu().numpy()
+            assert np.linalg.norm(u - ref) <= 1e-10 * np.linalg.norm(ref), (slices, t)
+        outs[slices] = U
+    diff = torch.linalg.norm(outs[6] - outs[0], dim=0) / torch.linalg.norm(outs[0], dim=0)
+    assert float(diff.max()) <= 1e-10
