@@ -345,7 +345,9 @@ def _measured_peak(key):
 
 def _csr(F, mask, h, ctx):
     """The assembled operator as a torch sparse CSR matrix (for evidence only)."""
+    import warnings
     import torch
+    warnings.filterwarnings("ignore", message="Sparse CSR tensor support is in beta state")
     asm = F.fd_assemble(mask, h, dense=False, ctx=ctx)
     n = asm["n"]
     return torch.sparse_csr_tensor(asm["rowptr"], asm["col"].to(torch.int64), asm["val"], size=(n, n))
