@@ -294,13 +294,16 @@ __global__ void band_diagonals(const T* band, int ldb, int64_t n, double* d, dou
 // CTA stages the reflectors of the next D steps in shared memory (double
 // buffered) while it applies the current D; the rows entering the window are
 // loaded one batch ahead.  Work: 4 L n flops per reflector of length L.
-constexpr int Q2T_WARPS = 8, Q2T_D = 8;
+constexpr int Q2T_WARPS = 8;
 
 template <class T, int B, int P>
 __global__ void __launch_bounds__(Q2T_WARPS * 32, 2)
 q2t_apply_kernel(const T* __restrict__ refl, const double* __restrict__ rtau, int64_t n,
                  int64_t kmax, T* Y, int64_t ldy, int64_t ncols) {
-  constexpr int R = B / P, CPW = 32 / P, D = Q2T_D, NT = Q2T_WARPS * 32;
+  // D = R: a batch of D reflectors slides the window by one full register
+  // rotation, and the sweep is padded with zero reflectors (tau = 0) to whole
+  // batches, so every slide is unconditional and compiles to renaming.
+  constexpr int R = B / P, CPW = 32 / P, D = R, NT = Q2T_WARPS * 32;
   constexpr int PER = (D * B + NT - 1) / NT;  // staged doubles per thread
   __shared__ T vbuf[2][D][B];
   __shared__ T tbuf[2][D];
@@ -372,9 +375,7 @@ q2t_apply_kernel(const T* __restrict__ refl, const double* __restrict__ rtau, in
       }
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        const int64_t s = smax - (batch * D + j);
-        if (s < 0) break;
-        const T* v = &vbuf[buf][j][part * R];
+        const T* v = &vbuf[buf][j][part * R];  // zero (with tau 0) past s = 0
         T d0 = T(0), d1 = T(0);
 #pragma unroll
         for (int i = 0; i < R; i += 2) {
@@ -387,7 +388,7 @@ q2t_apply_kernel(const T* __restrict__ refl, const double* __restrict__ rtau, in
         const T f = tbuf[buf][j] * dot;
 #pragma unroll
         for (int i = 0; i < R; ++i) w[i] = fma(-f, v[i], w[i]);
-        if (s > 0) {  // slide the window up by one row
+        {  // slide the window up by one row (rows above 1 + kB enter as zeros and are never written)
           const T out = w[R - 1];
           const int64_t leaving = r0 + B - 1;
           if (part == P - 1 && active && leaving < n) yc[leaving * ldy] = out;
@@ -408,7 +409,7 @@ q2t_apply_kernel(const T* __restrict__ refl, const double* __restrict__ rtau, in
 #pragma unroll
     for (int i = 0; i < R; ++i) {  // flush the final window (rows 1 + kB ..)
       const int64_t row = r0 + part * R + i;
-      if (active && row < n) yc[row * ldy] = w[i];
+      if (active && row < n && row >= 1 + k * B) yc[row * ldy] = w[i];
     }
   }
 }
@@ -513,7 +514,11 @@ int q2_apply_run(fraclap_ctx* ctx, const Stage2T<T>* s, int64_t n, int b, T* Z, 
   FL_Q2T(8, 2)
   FL_Q2T(16, 4)
   FL_Q2T(32, 8)
-  FL_Q2T(64, 4)
+  if constexpr (sizeof(T) == 4) {  // FP64 windows of 16 rows would not fit the registers
+    FL_Q2T(64, 4)
+  } else {
+    FL_Q2T(64, 8)
+  }
 #undef FL_Q2T
   FL_CHECK(ctx, cpw != 0, FRACLAP_ERR_UNSUPPORTED, "q2 back-transformation: band width %d not in {4, 8, 16, 32, 64}", b);
   FL_CUDA(ctx, cudaGetLastError());
