@@ -316,6 +316,7 @@ constexpr int kMaxCluster = 64;
 constexpr double kConvergedR = 3e-9;
 // BF16 slices per operand in the refinement's residual products (7: FP64).
 constexpr int kRefineSlices = 7;
+constexpr int kRefineFirstSlices = 5;  // first iteration (40 bits)
 
 __device__ void cluster_jacobi_body(const double* Sc, const double* Bc, int c, double* Q, double* w,
                                     int32_t* status) {
@@ -759,19 +760,22 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
     spmm_csr<<<dim3(rows, (unsigned)std::min<int64_t>(n, 4096)), 128, 0, st>>>(n, rowptr, col, val, X, ldx, n, AX, n);
     count_launch(ctx);
     span.stop();
+    // The first iteration starts from FP32 vectors (|R| ~ 1e-5); its products
+    // need about 40 bits, the later iterations remove their error.
+    const int slices_it = (it == 0 && iters > 1) ? kRefineFirstSlices : kRefineSlices;
     // R = I - X^T X, S = X^T (A X): lower triangles, FP64-accurate products
     // from BF16 tensor-core slices (the slices live in the scratch arena)
     {
       StageTimer tm(ctx, kStageResidualGemm, st);
       Arena oz = *ar;
-      FL_TRY(ozaki_gemm(ctx, true, false, n, n, n, -1.0, X, ldx, X, ldx, 0.0, R, n, kRefineSlices, true, &oz, st));
+      FL_TRY(ozaki_gemm(ctx, true, false, n, n, n, -1.0, X, ldx, X, ldx, 0.0, R, n, slices_it, true, &oz, st));
     }
     add_identity<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(R, n, n);
     count_launch(ctx);
     {
       StageTimer tm(ctx, kStageResidualGemm, st);
       Arena oz = *ar;
-      FL_TRY(ozaki_gemm(ctx, true, false, n, n, n, 1.0, X, ldx, AX, n, 0.0, S, n, kRefineSlices, true, &oz, st));
+      FL_TRY(ozaki_gemm(ctx, true, false, n, n, n, 1.0, X, ldx, AX, n, 0.0, S, n, slices_it, true, &oz, st));
     }
     span.start(kStageRefineNorms);
     ritz_values<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(S, n, R, n, n, lt);
@@ -848,7 +852,7 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
       ctx->refine_stats.insert(ctx->refine_stats.end(), row, row + 8);
       // converged: this iteration started with small residuals, so its
       // quadratic step leaves them at rounding level
-      converged = (hs[5] <= kConvergedR) && (hs[4] <= kConvergedR * na);
+      converged = (hs[5] <= kConvergedR) && (hs[4] <= kConvergedR * na) && slices_it == kRefineSlices;
     }
     span.start(kStageRefineClusters);
     if (ncl > 0) {
