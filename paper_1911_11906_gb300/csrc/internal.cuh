@@ -225,6 +225,7 @@ struct Stage1T {
   T* Y;              // b * b
   T* Mm;             // b * b
   double* gram;      // b * b
+  T* gramT;          // b * b (cluster panel route)
   double* partials;  // 2 * G * 2b
   int64_t npanel;
   int64_t vtotal;

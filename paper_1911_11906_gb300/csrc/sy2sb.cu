@@ -10,12 +10,18 @@
 // with X = A22 (V T), W = X - 1/2 V (T^T V^T X), through the GEMM engine
 // (symmetric A22 read from its lower triangle; lower-triangular rank-2b
 // update).  FP64 throughout; the Householder norms and scalings stay FP64.
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
 
 namespace fraclap {
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int PQR_NT = 256;
+constexpr int kClusterMax = 16;                  // CTAs of the cluster panel kernel (non-portable above 8)
+constexpr int kPanelClusterSmemMax = 220 * 1024;  // panel rows one CTA of the cluster holds
 constexpr int kPanelSmemMax = 180 * 1024;  // largest panel slice one CTA holds
 
 // Cooperative panel QR.  P: m x bw panel (ld ldp) in the working matrix.
@@ -160,6 +166,143 @@ panel_qr_kernel(T* P, int64_t ldp, int64_t m, int bw, T* Vout, int64_t ldv,
   for (int p = tid; p < bw * bw; p += PQR_NT) Tf[p] = (T)Ts[p];
 }
 
+// The same panel factorisation on one thread-block cluster (up to 16 CTAs)
+// when the panel fits in their shared memory: each column's partial sums are
+// read from the other CTAs' shared memory (distributed shared memory) after
+// one hardware cluster barrier, in the same rank order everywhere, instead of
+// a grid-wide barrier and global atomics.  Partial sums are double-buffered
+// by column parity, so one barrier per column suffices: a CTA writes the
+// next column's partials only after the barrier that ends everyone's reads
+// of the same buffer two columns back.  Writes R, the reflectors and the
+// explicit V; the Gram matrix and T follow in separate kernels.
+template <class T>
+__global__ void __launch_bounds__(PQR_NT)
+panel_qr_cluster_kernel(T* P, int64_t ldp, int64_t m, int bw, T* Vout, int64_t ldv, double* tau,
+                        int64_t rows_per_cta) {
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);  // rows_per_cta x bw, column-major (ld rows_per_cta)
+  __shared__ double part[2][2 * 64];
+  __shared__ double red[2 * 64 + 4];
+  __shared__ double sw[64];
+  __shared__ double s_coef[4];
+  const unsigned rank = cluster.block_rank(), CS = cluster.num_blocks();
+  const int64_t rb = (int64_t)rank * rows_per_cta;
+  const int64_t re = (rb + rows_per_cta < m) ? rb + rows_per_cta : m;
+  const int64_t nr = (re > rb) ? re - rb : 0;
+  const int64_t ld = rows_per_cta;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = PQR_NT / 32;
+
+  for (int c = 0; c < bw; ++c)
+    for (int64_t r = tid; r < nr; r += PQR_NT) S[r + c * ld] = P[(rb + r) + c * ldp];
+  __syncthreads();
+
+  const int nref = (m < bw) ? (int)m : bw;
+  for (int c = 0; c < nref; ++c) {
+    double* mine = part[c & 1];
+    const int64_t r0 = (c > rb) ? c - rb : 0;  // first local row with global row >= c
+    for (int j = c + warp; j < bw; j += nwarp) {
+      // per-CTA partial dots in the working precision (FP64 work on ~m/16 rows
+      // would occupy GB300's narrow FP64 pipe); the cluster sum is FP64
+      T sum = T(0);
+      for (int64_t r = r0 + lane; r < nr; r += 32) {
+        const int64_t gr = rb + r;
+        if (j == c && gr == c) continue;  // g_c is the tail sum of squares (rows > c)
+        sum += S[r + c * ld] * S[r + j * ld];
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) mine[j] = (double)sum;
+    }
+    for (int j = c + tid; j < bw; j += PQR_NT) mine[bw + j] = (c >= rb && c < re) ? (double)S[(c - rb) + j * ld] : 0.0;
+    cluster.sync();
+    for (int t = tid; t < 2 * (bw - c); t += PQR_NT) {
+      const int slot = (t < bw - c) ? c + t : bw + c + (t - (bw - c));
+      double v[kClusterMax];  // all remote loads in flight, then the sum in rank order
+#pragma unroll
+      for (int q = 0; q < kClusterMax; ++q)
+        v[q] = (q < (int)CS) ? cluster.map_shared_rank(&part[c & 1][0], q)[slot] : 0.0;
+      double sum = 0.0;
+#pragma unroll
+      for (int q = 0; q < kClusterMax; ++q) sum += v[q];
+      red[(t < bw - c) ? t : 64 + (t - (bw - c))] = sum;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double tail = red[0], x0 = red[64];
+      double beta = x0, v0 = 1.0, tu = 0.0;
+      if (tail > 0.0 && m - c > 1) {
+        const double alpha = sqrt(x0 * x0 + tail);
+        beta = (x0 >= 0.0) ? -alpha : alpha;
+        v0 = x0 - beta;
+        tu = (beta - x0) / beta;
+      }
+      s_coef[0] = beta;
+      s_coef[1] = 1.0 / v0;
+      s_coef[2] = tu;
+      if (rank == 0) tau[c] = tu;
+    }
+    __syncthreads();
+    const double beta = s_coef[0], inv_v0 = s_coef[1], tu = s_coef[2];
+    for (int j = c + 1 + tid; j < bw; j += PQR_NT) {
+      const double g = red[j - c], pc = red[64 + (j - c)];
+      sw[j] = (tu == 0.0) ? 0.0 : tu * (g - beta * pc) * inv_v0;
+    }
+    __syncthreads();
+    for (int64_t r = r0 + tid; r < nr; r += PQR_NT) {
+      const int64_t gr = rb + r;
+      double vr;
+      if (gr == c) {
+        vr = 1.0;
+        S[r + c * ld] = (T)beta;
+      } else {
+        vr = (tu == 0.0) ? 0.0 : (double)S[r + c * ld] * inv_v0;
+        S[r + c * ld] = (T)vr;
+      }
+      if (tu != 0.0) {
+        const T vt = (T)vr;
+        for (int j = c + 1; j < bw; ++j) S[r + j * ld] -= vt * (T)sw[j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int c = nref; c < bw && rank == 0 && tid == 0; ++c) tau[c] = 0.0;
+  for (int c = 0; c < bw; ++c)
+    for (int64_t r = tid; r < nr; r += PQR_NT) {
+      const int64_t gr = rb + r;
+      const T sv = S[r + c * ld];
+      P[gr + c * ldp] = sv;
+      T v = T(0);
+      if (c < nref) v = (gr < c) ? T(0) : (gr == c ? T(1) : sv);
+      Vout[gr + c * ldv] = v;
+    }
+  cluster.sync();  // no CTA leaves while another may still read its partial sums
+}
+
+// T of the compact WY form from tau and the Gram matrix G = V^T V (bw x bw):
+// T(i, i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i).  One CTA.
+template <class T>
+__global__ void __launch_bounds__(PQR_NT) panel_t_kernel(const T* gram, const double* tau, int bw, T* Tf) {
+  __shared__ double Ts[64 * 64];
+  __shared__ double y[64];
+  const int tid = threadIdx.x;
+  for (int p = tid; p < bw * bw; p += PQR_NT) Ts[p] = 0.0;
+  __syncthreads();
+  for (int i = 0; i < bw; ++i) {
+    const double ti = tau[i];
+    if (tid < i) y[tid] = (double)gram[tid + i * bw];
+    __syncthreads();
+    if (tid < i) {
+      double sum = 0.0;
+      for (int q = tid; q < i; ++q) sum += Ts[tid + q * bw] * y[q];
+      Ts[tid + i * bw] = -ti * sum;
+    }
+    if (tid == 0) Ts[i + i * bw] = ti;
+    __syncthreads();
+  }
+  for (int p = tid; p < bw * bw; p += PQR_NT) Tf[p] = (T)Ts[p];
+}
+
 // Band extraction: band(off, j) = A(j + off, j) for off <= b, 0 for b < off < ldb.
 template <class T>
 __global__ void extract_band(const T* A, int64_t lda, int64_t n, int b, T* band, int ldb) {
@@ -188,6 +331,7 @@ int stage1_take(Arena* ar, int64_t n, int b, int G, Stage1T<T>* s) {
   s->Y = ar->take<T>((int64_t)b * b);
   s->Mm = ar->take<T>((int64_t)b * b);
   s->gram = ar->take<double>((int64_t)b * b);
+  s->gramT = ar->take<T>((int64_t)b * b);
   s->partials = ar->take<double>(3 * 2 * (int64_t)b);
   return 0;
 }
@@ -203,6 +347,55 @@ static int panel_grid(fraclap_ctx* ctx, int64_t m, int bw, size_t elem, int64_t*
   return G;
 }
 
+// Panel on one cluster, then G = V^T V (split over the rows) and T.  Returns
+// 1 (nothing launched) when the panel does not fit in a cluster's shared
+// memory or no cluster of that size can be resident; < 0 on a CUDA error.
+template <class T>
+int panel_cluster(fraclap_ctx* ctx, T* P, int64_t ldp, int64_t m, int b, T* V, double* tau, T* gramT, T* Tf,
+                  cudaStream_t st) {
+  // FP64 panels keep the grid kernel: spread over all SMs, their FP64 dot
+  // products are not bound by one SM's narrow FP64 pipe
+  if (sizeof(T) == 8) return 1;
+  const int64_t cap = kPanelClusterSmemMax / ((int64_t)b * (int64_t)sizeof(T));
+  const int limit = std::max(1, std::min(kClusterMax, ctx->sm_count));
+  int CS = (int)std::max<int64_t>(cdiv(m, cap), std::min<int64_t>(limit, cdiv(m, 128)));
+  if (CS > limit) return 1;
+  const int64_t rows = cdiv(m, CS);
+  CS = (int)cdiv(m, rows);
+  const size_t smem = (size_t)rows * b * sizeof(T);
+  FL_CUDA(ctx, cudaFuncSetAttribute(panel_qr_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  FL_CUDA(ctx, cudaFuncSetAttribute(panel_qr_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kPanelClusterSmemMax));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)CS);
+  cfg.blockDim = dim3(PQR_NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, panel_qr_cluster_kernel<T>, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  int bw = b;
+  count_launch(ctx);
+  FL_CUDA(ctx, cudaLaunchKernelEx(&cfg, panel_qr_cluster_kernel<T>, P, ldp, m, bw, V, m, tau, rows));
+  using D = GemmDescT<T>;
+  FL_CUDA(ctx, cudaMemsetAsync(gramT, 0, sizeof(T) * b * b, st));
+  FL_TRY(gemm<T>(ctx, true, false, kGemmPlain, D{b, b, m, V, m, V, m, gramT, b, nullptr, 0, nullptr, 0, 0, 1.0, 1.0},
+                 (int)std::min<int64_t>(cdiv(m, 512), 16), st));
+  panel_t_kernel<T><<<1, PQR_NT, 0, st>>>(gramT, tau, b, Tf);
+  count_launch(ctx);
+  FL_CUDA(ctx, cudaGetLastError());
+  return 0;
+}
+
 // Reduces Aw (n x n, lower triangle valid, overwritten) to band form and
 // writes the band (ld 2b, offsets 0..2b-1, zero beyond b) to `band`.
 template <class T>
@@ -215,6 +408,11 @@ int sy2sb_run(fraclap_ctx* ctx, T* Aw, int64_t n, int64_t lda, int b, T* band, S
     T* P = Aw + (j0 + b) + j0 * lda;
     T* V = s->Vstore + voff;
     T* Tf = s->Tstore + p * b * b;
+    const int crc = panel_cluster(ctx, P, lda, m, b, V, s->tau + p * b, s->gramT, Tf, st);
+    if (crc < 0) return crc;
+    if (crc == 0) {
+      // done on one cluster
+    } else {
     int64_t rows_per_cta;
     size_t smem;
     const int G = panel_grid(ctx, m, b, sizeof(T), &rows_per_cta, &smem);
@@ -237,6 +435,7 @@ int sy2sb_run(fraclap_ctx* ctx, T* Aw, int64_t n, int64_t lda, int b, T* band, S
       FL_CUDA(ctx, cudaFuncSetAttribute(panel_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmemMax));
       count_launch(ctx);
       FL_CUDA(ctx, cudaLaunchCooperativeKernel((void*)panel_qr_kernel<T>, dim3(G), dim3(PQR_NT), args, smem, st));
+    }
     }
     T* A22 = Aw + (j0 + b) + (j0 + b) * lda;
     using D = GemmDescT<T>;
