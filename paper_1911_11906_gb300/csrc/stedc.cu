@@ -193,7 +193,8 @@ __global__ void dc_leaf(const double* D, const double* e, int64_t n, int L, doub
 }
 
 // ----------------------------------------------------------------------------
-// Merge preparation: one CTA per merge, sequential parts on thread 0.
+// Merge preparation: one CTA (128 threads) per merge; only the deflation by
+// rotations between consecutive survivors runs on one thread.
 template <class T>
 __global__ void dc_merge_prep(DcBuf<T> B, const double* e, const double* lambda, const T* Z,
                               int64_t ldz, int64_t n, int L, int level, int64_t nmax) {
@@ -203,95 +204,134 @@ __global__ void dc_merge_prep(DcBuf<T> B, const double* e, const double* lambda,
   const int64_t mid = leaf_bound(j * span + span / 2, n, L);
   const int64_t nm = hi - lo, n1 = mid - lo;
   MergeInfo* inf = B.info + j;
-  __shared__ double s_nrm;
+  __shared__ double s_red[32];
+  __shared__ int64_t s_cnt[129];
+  __shared__ int64_t s_nrot;
+  const int tid = threadIdx.x, nt = blockDim.x;  // nt = 128
   // z and D in original local order (scratch: zhat and outval regions)
   double* zloc = B.zhat + lo;
   double* dloc = B.outval + lo;
   const double beta = e[mid - 1];
   const double sgn = (beta < 0.0) ? -1.0 : 1.0;
-  for (int64_t i = threadIdx.x; i < nm; i += blockDim.x) {
-    zloc[i] = (i < n1) ? (double)Z[(mid - 1) + (lo + i) * ldz] : (double)Z[mid + (lo + i) * ldz];
+  double part = 0.0;
+  for (int64_t i = tid; i < nm; i += nt) {
+    const double zv = (i < n1) ? (double)Z[(mid - 1) + (lo + i) * ldz] : (double)Z[mid + (lo + i) * ldz];
+    zloc[i] = zv;
     dloc[i] = sgn * lambda[lo + i];
+    part += zv * zv;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double nz2 = 0.0;
-    for (int64_t i = 0; i < nm; ++i) nz2 += zloc[i] * zloc[i];
-    s_nrm = nz2;
-  }
-  __syncthreads();
-  const double nz2 = s_nrm;
+  auto block_sum = [&](double v) -> double {
+    v = warp_sum(v);
+    __syncthreads();
+    if ((tid & 31) == 0) s_red[tid >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nt / 32; ++w) t += s_red[w];
+    return t;
+  };
+  const double nz2 = block_sum(part);
   const double rho = fabs(beta) * nz2;
   const double inv = 1.0 / sqrt(nz2);
-  if (threadIdx.x != 0) return;
-  // merge the two sorted runs (descending when sgn < 0)
+  // merge the two sorted runs (descending when sgn < 0) by merge path: output
+  // o takes a elements from run A before it, a the smallest with
+  // A(a) > B(o - 1 - a); ties go to A first, as in a sequential merge
   double* Dp = B.Dp + lo;
   double* zp = B.zp + lo;
   int* perm = B.perm + lo;
-  {
-    int64_t a = (sgn > 0) ? 0 : n1 - 1, aend = (sgn > 0) ? n1 : -1, astep = (sgn > 0) ? 1 : -1;
-    int64_t b = (sgn > 0) ? n1 : nm - 1, bend = (sgn > 0) ? nm : n1 - 1, bstep = astep;
-    for (int64_t o = 0; o < nm; ++o) {
-      bool take_a;
-      if (a == aend) take_a = false;
-      else if (b == bend) take_a = true;
-      else take_a = dloc[a] <= dloc[b];
-      const int64_t src = take_a ? a : b;
-      Dp[o] = dloc[src];
-      zp[o] = zloc[src] * inv;
-      perm[o] = (int)src;
-      if (take_a) a += astep; else b += bstep;
+  const int64_t n2 = nm - n1;
+  auto ia = [&](int64_t i) -> int64_t { return (sgn > 0) ? i : n1 - 1 - i; };
+  auto ib = [&](int64_t i) -> int64_t { return (sgn > 0) ? n1 + i : nm - 1 - i; };
+  for (int64_t o = tid; o < nm; o += nt) {
+    int64_t l = (o - n2 > 0) ? o - n2 : 0, h = (o < n1) ? o : n1;
+    while (l < h) {
+      const int64_t md = (l + h) >> 1;
+      // A(md) > B(o - 1 - md)?  (o - 1 - md < n2 holds for md >= o - n2)
+      if (dloc[ia(md)] > dloc[ib(o - 1 - md)]) h = md;
+      else l = md + 1;
     }
+    const int64_t ac = l, bc = o - l;
+    const bool take_a = ac < n1 && (bc >= n2 || dloc[ia(ac)] <= dloc[ib(bc)]);
+    const int64_t src = take_a ? ia(ac) : ib(bc);
+    Dp[o] = dloc[src];
+    zp[o] = zloc[src] * inv;
+    perm[o] = (int)src;
   }
-  // deflation
+  __syncthreads();
+  // deflation tolerance and flags (1 = deflated)
+  double dm = 0.0;
+  for (int64_t i = tid; i < nm; i += nt) dm = fmax(dm, fabs(Dp[i]));
+  for (int o = 16; o >= 1; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+  __syncthreads();
+  if ((tid & 31) == 0) s_red[tid >> 5] = dm;
+  __syncthreads();
   double dmax = 0.0;
-  for (int64_t i = 0; i < nm; ++i) dmax = fmax(dmax, fabs(Dp[i]));
+  for (int w = 0; w < nt / 32; ++w) dmax = fmax(dmax, s_red[w]);
   // deflation at the working precision's rounding level (FP32 merges
   // deflate at 8 eps_32: their results are only FP32-accurate anyway)
   const double eps_t = (sizeof(T) == 4) ? 1.1920928955078125e-07 : kEps;
   const double tol = 8.0 * eps_t * fmax(dmax, rho);
   int* kept = B.kept + lo;
-  int64_t nrot = 0, K = 0, ndef = 0;
-  int64_t prev = -1;
-  // flags: use outsrc region as scratch (1 = deflated)
-  int* flag = B.outsrc + lo;
-  for (int64_t i = 0; i < nm; ++i) flag[i] = (rho * fabs(zp[i]) <= tol) ? 1 : 0;
-  for (int64_t i = 0; i < nm; ++i) {
-    if (flag[i]) continue;
-    if (prev >= 0) {
-      const double zp_ = zp[prev], zj = zp[i];
-      const double r = hypot(zp_, zj);
-      const double c = zj / r, s = -zp_ / r;
-      if (fabs((Dp[i] - Dp[prev]) * c * s) <= tol) {
-        zp[i] = r;
-        zp[prev] = 0.0;
-        const double dp = Dp[prev], dj = Dp[i];
-        Dp[prev] = dp * c * c + dj * s * s;
-        Dp[i] = dp * s * s + dj * c * c;
-        B.rot_i[lo + nrot] = (int)prev;
-        B.rot_j[lo + nrot] = (int)i;
-        B.rot_c[lo + nrot] = c;
-        B.rot_s[lo + nrot] = s;
-        ++nrot;
-        flag[prev] = 1;
+  int* flag = B.outsrc + lo;  // scratch
+  for (int64_t i = tid; i < nm; i += nt) flag[i] = (rho * fabs(zp[i]) <= tol) ? 1 : 0;
+  __syncthreads();
+  // close poles: Givens rotations between consecutive survivors (sequential)
+  if (tid == 0) {
+    int64_t nrot = 0, prev = -1;
+    for (int64_t i = 0; i < nm; ++i) {
+      if (flag[i]) continue;
+      if (prev >= 0) {
+        const double zp_ = zp[prev], zj = zp[i];
+        const double r = hypot(zp_, zj);
+        const double c = zj / r, s = -zp_ / r;
+        if (fabs((Dp[i] - Dp[prev]) * c * s) <= tol) {
+          zp[i] = r;
+          zp[prev] = 0.0;
+          const double dp = Dp[prev], dj = Dp[i];
+          Dp[prev] = dp * c * c + dj * s * s;
+          Dp[i] = dp * s * s + dj * c * c;
+          B.rot_i[lo + nrot] = (int)prev;
+          B.rot_j[lo + nrot] = (int)i;
+          B.rot_c[lo + nrot] = c;
+          B.rot_s[lo + nrot] = s;
+          ++nrot;
+          flag[prev] = 1;
+        }
       }
+      prev = i;
     }
-    prev = i;
+    s_nrot = nrot;
   }
-  for (int64_t i = 0; i < nm; ++i)
+  __syncthreads();
+  const int64_t nrot = s_nrot;
+  // compaction: survivors first, then the deflated, each in order (block scan)
+  const int64_t chunk = (nm + nt - 1) / nt;
+  const int64_t c0 = tid * chunk, c1 = (c0 + chunk < nm) ? c0 + chunk : nm;
+  int64_t mine = 0;
+  for (int64_t i = c0; i < c1; ++i) mine += flag[i] ? 0 : 1;
+  s_cnt[tid + 1] = mine;
+  if (tid == 0) s_cnt[0] = 0;
+  __syncthreads();
+  if (tid == 0)
+    for (int t = 1; t <= nt; ++t) s_cnt[t] += s_cnt[t - 1];
+  __syncthreads();
+  const int64_t K = s_cnt[nt];
+  int64_t kk = s_cnt[tid], kd = K + (c0 - s_cnt[tid]);
+  for (int64_t i = c0; i < c1; ++i) {
     if (!flag[i]) {
-      kept[K] = (int)i;
+      kept[kk] = (int)i;
       // the poles and weights as the working precision holds them, so that
       // the roots (found in T) and the Gu-Eisenstat weights and vectors
       // (formed in FP64 from dd, zz) see the same secular equation
-      B.ddt[lo + K] = (T)Dp[i];
-      B.zzt[lo + K] = (T)zp[i];
-      B.dd[lo + K] = (double)(T)Dp[i];
-      B.zz[lo + K] = (double)(T)zp[i];
-      ++K;
+      B.ddt[lo + kk] = (T)Dp[i];
+      B.zzt[lo + kk] = (T)zp[i];
+      B.dd[lo + kk] = (double)(T)Dp[i];
+      B.zz[lo + kk] = (double)(T)zp[i];
+      ++kk;
+    } else {
+      kept[kd++] = (int)i;
     }
-  for (int64_t i = 0; i < nm; ++i)
-    if (flag[i]) kept[K + ndef++] = (int)i;
+  }
+  if (tid != 0) return;
   inf->lo = lo;
   inf->mid = mid;
   inf->hi = hi;

@@ -279,26 +279,54 @@ panel_qr_cluster_kernel(T* P, int64_t ldp, int64_t m, int bw, T* Vout, int64_t l
   cluster.sync();  // no CTA leaves while another may still read its partial sums
 }
 
-// T of the compact WY form from tau and the Gram matrix G = V^T V (bw x bw):
+// T of the compact WY form from tau and the Gram matrix G = V^T V (bw x bw).
+// When every tau is nonzero, T^-1 = diag(1/tau) + strictly-upper(G)
+// (Schreiber and Van Loan's form of H_1 ... H_bw = I - V T V^T): T is that
+// triangle's inverse, one column per thread by back substitution, with no
+// barrier between steps.  Otherwise the column recurrence
 // T(i, i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i).  One CTA.
 template <class T>
 __global__ void __launch_bounds__(PQR_NT) panel_t_kernel(const T* gram, const double* tau, int bw, T* Tf) {
+  __shared__ double U[64][65];  // U(i, k), i <= k
   __shared__ double Ts[64 * 64];
   __shared__ double y[64];
+  __shared__ int s_zero;
   const int tid = threadIdx.x;
-  for (int p = tid; p < bw * bw; p += PQR_NT) Ts[p] = 0.0;
+  if (tid == 0) s_zero = 0;
   __syncthreads();
-  for (int i = 0; i < bw; ++i) {
-    const double ti = tau[i];
-    if (tid < i) y[tid] = (double)gram[tid + i * bw];
-    __syncthreads();
-    if (tid < i) {
-      double sum = 0.0;
-      for (int q = tid; q < i; ++q) sum += Ts[tid + q * bw] * y[q];
-      Ts[tid + i * bw] = -ti * sum;
+  for (int p = tid; p < bw * bw; p += PQR_NT) {
+    const int i = p % bw, k = p / bw;
+    if (i < k) U[i][k] = (double)gram[i + k * bw];
+    else if (i == k) {
+      const double t = tau[i];
+      if (t == 0.0) s_zero = 1;
+      U[i][i] = (t == 0.0) ? 1.0 : 1.0 / t;
     }
-    if (tid == 0) Ts[i + i * bw] = ti;
+    Ts[p] = 0.0;
+  }
+  __syncthreads();
+  if (!s_zero) {
+    for (int j = tid; j < bw; j += PQR_NT) {  // column j of U^-1
+      for (int i = j; i >= 0; --i) {
+        double sum = (i == j) ? 1.0 : 0.0;
+        for (int k = i + 1; k <= j; ++k) sum -= U[i][k] * Ts[k + j * bw];
+        Ts[i + j * bw] = sum / U[i][i];
+      }
+    }
     __syncthreads();
+  } else {
+    for (int i = 0; i < bw; ++i) {
+      const double ti = tau[i];
+      if (tid < i) y[tid] = (double)gram[tid + i * bw];
+      __syncthreads();
+      if (tid < i) {
+        double sum = 0.0;
+        for (int q = tid; q < i; ++q) sum += Ts[tid + q * bw] * y[q];
+        Ts[tid + i * bw] = -ti * sum;
+      }
+      if (tid == 0) Ts[i + i * bw] = ti;
+      __syncthreads();
+    }
   }
   for (int p = tid; p < bw * bw; p += PQR_NT) Tf[p] = (T)Ts[p];
 }
