@@ -145,10 +145,21 @@ BAND = {"fp64": 64, "mixed": 64}
 
 def ozaki_bf16_flops(n: int, slices: int = 8) -> float:
     """Algorithmic BF16 tensor flops of one lower-triangular n x n x n
-    residual product: the 7-bit slicing for K > 256 uses 8 slices, pairs
-    with p + q < 8 (36 products), each 2 n flops per lower-triangle entry."""
+    residual product cut into `slices` 7-bit slices (K > 256): pairs with
+    p + q < slices, each 2 n flops per lower-triangle entry."""
     pairs = slices * (slices + 1) // 2
     return 2.0 * pairs * n * (n * (n + 1) // 2)
+
+
+def refine_slice_counts(iterations: int, cap: int) -> list:
+    """7-bit slices per operand of the refinement's two residual products in
+    each iteration: 40, 48 and then 56 bits (5, 6, 7 slices of 8 bits), the
+    last allowed iteration always full."""
+    bits = []
+    for it in range(iterations):
+        s8 = 7 if it + 1 >= cap else (5 if it == 0 else (6 if it == 1 else 7))
+        bits.append((8 * s8 + 6) // 7)
+    return bits
 
 
 # DRAM bytes per BF16 flop of ozaki_tc_kernel, from one ncu capture of the
@@ -278,7 +289,10 @@ def run_gpu(args, rank, world, local_rank):
     else:
         g_ms, g_cnt = stages["slice_products"]
         dur = g_ms / max(g_cnt, 1)
-        work = ozaki_bf16_flops(n)
+        # average over the launches (2 per iteration, fewer slices in the first two)
+        per_iter = refine_slice_counts(len(R.get("refine", [])) or 3, REFINE_ITERS)
+        total = sum(2 * ozaki_bf16_flops(n, sl) for sl in per_iter)
+        work = total / max(2 * len(per_iter), 1)
         traffic = OZAKI_DRAM_BYTES_PER_FLOP * work
         peak = _measured_peak("bf16_tflops") or 1900.0
         roof = {"kernel": "ozaki_tc_kernel (residual products of the refinement: tcgen05.mma on TMA-loaded BF16 slices)",

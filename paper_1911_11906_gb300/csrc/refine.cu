@@ -316,7 +316,8 @@ constexpr int kMaxCluster = 64;
 constexpr double kConvergedR = 3e-9;
 // BF16 slices per operand in the refinement's residual products (7: FP64).
 constexpr int kRefineSlices = 7;
-constexpr int kRefineFirstSlices = 5;  // first iteration (40 bits)
+constexpr int kRefineFirstSlices = 5;   // first iteration (40 bits)
+constexpr int kRefineSecondSlices = 6;  // second iteration (48 bits)
 
 __device__ void cluster_jacobi_body(const double* Sc, const double* Bc, int c, double* Q, double* w,
                                     int32_t* status) {
@@ -760,9 +761,12 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
     spmm_csr<<<dim3(rows, (unsigned)std::min<int64_t>(n, 4096)), 128, 0, st>>>(n, rowptr, col, val, X, ldx, n, AX, n);
     count_launch(ctx);
     span.stop();
-    // The first iteration starts from FP32 vectors (|R| ~ 1e-5); its products
-    // need about 40 bits, the later iterations remove their error.
-    const int slices_it = (it == 0 && iters > 1) ? kRefineFirstSlices : kRefineSlices;
+    // The first iteration starts from FP32 vectors (|R| ~ 1e-5) and the second
+    // from |R| ~ 1e-6..1e-5: their products need about 40 and 48 bits, the later
+    // iterations remove their error.  An iteration run with fewer slices never
+    // counts as the converged (last) one.
+    const int slices_it = (it + 1 >= iters) ? kRefineSlices
+                          : (it == 0 ? kRefineFirstSlices : (it == 1 ? kRefineSecondSlices : kRefineSlices));
     // R = I - X^T X, S = X^T (A X): lower triangles, FP64-accurate products
     // from BF16 tensor-core slices (the slices live in the scratch arena)
     {
