@@ -7,6 +7,6 @@ Sec. III-D-2), written independently of the CUDA path: the two share no code.
 
 Pinned functions (see ``tests/test_oracle_*.py``): assembly, Householder +
 implicit-QR eigensolver, Jacobi, inertia counting, banded direct solve,
-spectral apply.  No function here is unpinned.
+spectral apply, fractional diffusion.  No function here is unpinned.
 """
 from .oracle import *  # noqa: F401,F403

@@ -12,6 +12,8 @@
  *     Laplacian scaled by 1/h^2.
  *   - Sec. II, the sums g and v after eq. (discrete_laplace):
  *     v = sum_k theta_k^{-alpha/2} <f, phi_k> phi_k  (eq. poisson_solution).
+ *   - Sec. II, eq. (diffusion_solution): the fractional diffusion solution
+ *     u(t) = sum_k exp(-mu theta_k^{alpha/2} t) <u0, phi_k> phi_k.
  *   - Sec. III-D-2 (exact eigenvalue counting): the number of eigenvalues
  *     below sigma equals the number of negative pivots of the LDL^T
  *     factorisation of A - sigma I (Sylvester's law of inertia).
@@ -500,6 +502,60 @@ int oracle_frac_apply(int64_t n, const double* V, int64_t ldv, const double* lam
     for (int64_t i = 0; i < n; ++i) coef[i] = pow(lam[i], ex) * w[i];
     double* u = &U[j * ldu];
     /* u = sum_i coef_i v_i, rows split into independent chunks */
+    const int64_t blk = 256, nblk = (n + blk - 1) / blk;
+#pragma omp parallel for schedule(static)
+    for (int64_t b = 0; b < nblk; ++b) {
+      const int64_t r0 = b * blk, r1 = (r0 + blk < n) ? r0 + blk : n;
+      for (int64_t r = r0; r < r1; ++r) u[r] = 0.0;
+      for (int64_t i = 0; i < n; ++i) {
+        const double ci = coef[i];
+        const double* vi = &V[i * ldv];
+        for (int64_t r = r0; r < r1; ++r) u[r] += vi[r] * ci;
+      }
+    }
+  }
+  free(coef);
+  free(W);
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fractional diffusion, Sec. II eq. diffusion_solution: the solution of     */
+/*   du/dt + mu (-Laplacian)^{alpha/2} u = 0,  u(0) = u0,                    */
+/* at time t is sum_i exp(-mu lam_i^{alpha/2} t) <u0, v_i> v_i.              */
+/* Pair j takes initial state U0(:, pair_f[j]), order pair_alpha[j] and      */
+/* time pair_t[j]; mu is shared.  pow() and exp() in double decide every     */
+/* multiplier.                                                               */
+/* ------------------------------------------------------------------------ */
+int oracle_frac_diffusion(int64_t n, const double* V, int64_t ldv, const double* lam,
+                          const double* U0, int64_t ldu0, int64_t m, const int32_t* pair_f,
+                          const double* pair_alpha, const double* pair_t, double mu, int64_t k,
+                          double* U, int64_t ldu) {
+  if (n < 0 || m < 0 || k < 0 || ldv < n || ldu0 < n || ldu < n) return ORACLE_EINVAL;
+  for (int64_t j = 0; j < k; ++j)
+    if (pair_f[j] < 0 || pair_f[j] >= m) return ORACLE_EINVAL;
+  if (n == 0 || k == 0) return ORACLE_OK;
+  double* W = (double*)malloc(sizeof(double) * (size_t)n * (size_t)(m ? m : 1));
+  if (!W) return ORACLE_ENOMEM;
+  /* W(i, c) = <u0_c, v_i>: the expansion coefficients of each initial state */
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    const double* vi = &V[i * ldv];
+    for (int64_t c = 0; c < m; ++c) {
+      const double* uc = &U0[c * ldu0];
+      double s = 0.0;
+      for (int64_t r = 0; r < n; ++r) s += vi[r] * uc[r];
+      W[i + c * n] = s;
+    }
+  }
+  double* coef = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!coef) { free(W); return ORACLE_ENOMEM; }
+  for (int64_t j = 0; j < k; ++j) {
+    const double half = 0.5 * pair_alpha[j], t = pair_t[j];
+    const double* w = &W[(int64_t)pair_f[j] * n];
+    /* each mode decays with its own rate mu lam_i^{alpha/2} */
+    for (int64_t i = 0; i < n; ++i) coef[i] = exp(-mu * pow(lam[i], half) * t) * w[i];
+    double* u = &U[j * ldu];
     const int64_t blk = 256, nblk = (n + blk - 1) / blk;
 #pragma omp parallel for schedule(static)
     for (int64_t b = 0; b < nblk; ++b) {

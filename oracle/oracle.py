@@ -65,6 +65,9 @@ def _load():
             lib.oracle_band_solve.argtypes = [_i64, _p, _p, _p, _p, _p]
             lib.oracle_frac_apply.restype = ctypes.c_int
             lib.oracle_frac_apply.argtypes = [_i64, _p, _i64, _p, _p, _i64, _i64, _p, _p, _i64, _p, _i64]
+            lib.oracle_frac_diffusion.restype = ctypes.c_int
+            lib.oracle_frac_diffusion.argtypes = [_i64, _p, _i64, _p, _p, _i64, _i64, _p, _p, _p, _dbl,
+                                                  _i64, _p, _i64]
             _lib = lib
     return _lib
 
@@ -216,6 +219,29 @@ def frac_apply(V: np.ndarray, lam: np.ndarray, F: np.ndarray, pair_f, pair_alpha
     return U
 
 
+def frac_diffusion(V: np.ndarray, lam: np.ndarray, U0: np.ndarray, pair_f, pair_alpha, pair_t,
+                   mu: float = 1.0) -> np.ndarray:
+    """u_j = V diag(exp(-mu lam^{alpha_j/2} t_j)) V^T U0[:, pair_f[j]]: the
+    fractional diffusion solution at time t_j (Sec. II, eq. diffusion_solution)."""
+    V = np.asfortranarray(V, dtype=np.float64)
+    n = V.shape[0]
+    U0 = np.asfortranarray(U0.reshape(n, -1), dtype=np.float64)
+    m = U0.shape[1]
+    pf = np.ascontiguousarray(pair_f, np.int32)
+    pa = np.ascontiguousarray(pair_alpha, np.float64)
+    pt = np.ascontiguousarray(pair_t, np.float64)
+    k = pf.shape[0]
+    if pa.shape[0] != k or pt.shape[0] != k:
+        raise ValueError("pair_f, pair_alpha and pair_t differ in length")
+    lam = np.ascontiguousarray(lam, np.float64)
+    U = np.empty((n, k), order="F")
+    rc = _load().oracle_frac_diffusion(n, _ptr(V), n, _ptr(lam), _ptr(U0), n, m, _ptr(pf), _ptr(pa),
+                                       _ptr(pt), float(mu), k, _ptr(U), n)
+    if rc != 0:
+        raise RuntimeError(f"oracle_frac_diffusion failed ({rc})")
+    return U
+
+
 def solve(mask: np.ndarray, h: float, F: np.ndarray, pair_f, pair_alpha):
     """Whole path on the CPU: assemble, decompose, apply.  Returns (lam, V, U)."""
     _, A = assemble(mask, h)
@@ -225,4 +251,4 @@ def solve(mask: np.ndarray, h: float, F: np.ndarray, pair_f, pair_alpha):
 
 
 __all__ = ["build", "CSR", "num_threads", "assemble", "spmv", "tridiagonalize", "tridiag_eig",
-           "eig_full", "eig_jacobi", "count_below", "band_solve", "frac_apply", "solve"]
+           "eig_full", "eig_jacobi", "count_below", "band_solve", "frac_apply", "frac_diffusion", "solve"]

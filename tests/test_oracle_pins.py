@@ -365,3 +365,126 @@ def test_continuum_convergence_e8(alpha):
         assert max(errs) <= 1e-13
     else:
         assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
+
+
+# --------------------------------------------------------------------------
+# Fractional diffusion: Sec. II eq. (diffusion_solution)
+# --------------------------------------------------------------------------
+def test_diffusion_time_zero_and_alpha0(masked):
+    """t = 0 returns the initial state; alpha = 0 decays every mode alike,
+    u(t) = exp(-mu t) u0."""
+    p, A, lam, V = masked
+    k = p.F.shape[1]
+    U = O.frac_diffusion(V, lam, p.F, np.arange(k), np.full(k, 1.3), np.zeros(k), mu=2.0)
+    assert _rel(U, p.F) <= 1e-13
+    U = O.frac_diffusion(V, lam, p.F[:, :1], [0], [0.0], [0.3], mu=2.0)[:, 0]
+    assert _rel(U, np.exp(-0.6) * p.F[:, 0]) <= 1e-13
+
+
+@pytest.mark.parametrize("mu,t", [(1.0, 1e-4), (2.5, 1e-3)])
+def test_diffusion_alpha2_is_matrix_exponential(masked, mu, t):
+    """alpha = 2: the heat equation, u(t) = expm(-mu t A) u0 (scipy's Pade
+    scaling and squaring on the dense matrix, no eigenvectors involved).  t is
+    small enough that the top of the spectrum has not decayed away."""
+    sl = pytest.importorskip("scipy.linalg")
+    p, A, lam, V = masked
+    E = sl.expm(-mu * t * A.dense())
+    for c in range(3):
+        u = O.frac_diffusion(V, lam, p.F[:, c:c + 1], [0], [2.0], [t], mu=mu)[:, 0]
+        assert _rel(u, E @ p.F[:, c]) <= 1e-12
+
+
+def test_diffusion_alpha4_and_alpha1_match_matrix_functions(masked):
+    """alpha = 4: expm(-mu t A^2); alpha = 1: expm(-mu t sqrtm(A)) with scipy's
+    Schur-based square root."""
+    sl = pytest.importorskip("scipy.linalg")
+    p, A, lam, V = masked
+    D = A.dense()
+    f = p.F[:, 2]
+    u = O.frac_diffusion(V, lam, f[:, None], [0, 0], [4.0, 1.0], [2e-8, 1e-2], mu=1.5)
+    assert _rel(u[:, 0], sl.expm(-1.5 * 2e-8 * (D @ D)) @ f) <= 1e-11
+    R = np.real(sl.sqrtm(D))
+    assert _rel(u[:, 1], sl.expm(-1.5 * 1e-2 * R) @ f) <= 1e-10
+
+
+def test_diffusion_semigroup(masked):
+    """Evolving to t1 and then by t2 equals evolving to t1 + t2."""
+    p, A, lam, V = masked
+    f = p.F[:, 1]
+    u1 = O.frac_diffusion(V, lam, f[:, None], [0], [1.2], [3e-3], mu=0.8)
+    u2 = O.frac_diffusion(V, lam, u1, [0], [1.2], [5e-3], mu=0.8)[:, 0]
+    u3 = O.frac_diffusion(V, lam, f[:, None], [0], [1.2], [8e-3], mu=0.8)[:, 0]
+    assert _rel(u2, u3) <= 1e-12
+
+
+def _decay_error(U, p, lam11, alphas, t, mu):
+    u0 = 2.0 * p.F[:, 0]
+    return max(_rel(U[:, j], np.exp(-mu * lam11 ** (a / 2) * t) * u0) for j, a in enumerate(alphas))
+
+
+DIFF_ALPHAS = list(np.linspace(0.0, 2.0, 11))
+
+
+@pytest.mark.parametrize("mu", [1.0, 2.5])
+def test_diffusion_sine_mode_square48(square48, mu):
+    """u0 = 2 sin(pi x) sin(pi y) is the exact discrete eigenvector of
+    lambda_11, so u(t) = exp(-mu lambda_11^{alpha/2} t) u0 (discrete form of
+    eqs. diffusion_ics/diffusion_sols at the paper's t = 0.4 and 11 orders)."""
+    p, A, lam, V = square48
+    lam11 = 8.0 / p.h ** 2 * np.sin(np.pi * p.h / 2) ** 2
+    k = len(DIFF_ALPHAS)
+    U = O.frac_diffusion(V, lam, 2.0 * p.F[:, :1], [0] * k, DIFF_ALPHAS, [0.4] * k, mu=mu)
+    # lambda_11 carries ~1e-12 relative error; the exponent mu lambda^{alpha/2} t <= 20 amplifies it
+    assert _decay_error(U, p, lam11, DIFF_ALPHAS, 0.4, mu) <= 5e-11
+
+
+def test_diffusion_pins_catch_planted_mistakes(square48, masked):
+    """Mistakes planted in the oracle's inputs must trip the diffusion pins."""
+    p, A, lam, V = square48
+    lam11 = 8.0 / p.h ** 2 * np.sin(np.pi * p.h / 2) ** 2
+    k = len(DIFF_ALPHAS)
+    u0 = 2.0 * p.F[:, :1]
+    err = lambda U, mu=2.5: _decay_error(U, p, lam11, DIFF_ALPHAS, 0.4, mu)
+    # growth instead of decay (sign of the exponent)
+    assert err(O.frac_diffusion(V, lam, u0, [0] * k, DIFF_ALPHAS, [-0.4] * k, mu=2.5)) > 1e-3
+    # mu dropped
+    assert err(O.frac_diffusion(V, lam, u0, [0] * k, DIFF_ALPHAS, [0.4] * k, mu=1.0)) > 1e-3
+    # lambda^alpha instead of lambda^{alpha/2}
+    assert err(O.frac_diffusion(V, lam, u0, [0] * k, [2 * a for a in DIFF_ALPHAS], [0.4] * k, mu=2.5)) > 1e-3
+    # eigenvalues off by one index
+    assert err(O.frac_diffusion(V, np.roll(lam, 1), u0, [0] * k, DIFF_ALPHAS, [0.4] * k, mu=2.5)) > 1e-3
+    # a transposed operand on a general initial state: caught by the matrix exponential
+    sl = pytest.importorskip("scipy.linalg")
+    pm, Am, lm, Vm = masked
+    f = pm.F[:, 0]
+    ref = sl.expm(-1e-4 * Am.dense()) @ f
+    bad = O.frac_diffusion(np.asfortranarray(Vm.T), lm, f[:, None], [0], [2.0], [1e-4])[:, 0]
+    assert _rel(bad, ref) > 1e-3
+
+
+def test_diffusion_rejects_bad_pairs(masked):
+    p, A, lam, V = masked
+    with pytest.raises(RuntimeError):
+        O.frac_diffusion(V, lam, p.F[:, :1], [1], [1.0], [0.1])
+    with pytest.raises(ValueError):
+        O.frac_diffusion(V, lam, p.F[:, :1], [0, 0], [1.0], [0.1, 0.2])
+
+
+@pytest.mark.parametrize("alpha", DIFF_ALPHAS)
+def test_diffusion_continuum_convergence(alpha):
+    """Sec. V eqs. (diffusion_ics, diffusion_sols): u0 = 2 sin(pi x) sin(pi y)
+    has u = 2 exp(-mu (2 pi^2)^{alpha/2} t) sin(pi x) sin(pi y); at the
+    paper's t = 0.4, mu = 1 the FD solution converges at O(h^2)."""
+    errs = []
+    for m in (7, 15, 31):
+        p = I.square_problem(m, n_poly=0)
+        _, A = O.assemble(p.mask, p.h)
+        lam, V = O.eig_full(A.dense())
+        u0 = 2.0 * p.F[:, 0]
+        u = O.frac_diffusion(V, lam, u0[:, None], [0], [alpha], [0.4], mu=1.0)[:, 0]
+        exact = 2.0 * np.exp(-(2 * np.pi ** 2) ** (alpha / 2) * 0.4) * p.F[:, 0]
+        errs.append(np.max(np.abs(u - exact)))
+    if alpha == 0.0:
+        assert max(errs) <= 1e-13
+    else:
+        assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
