@@ -135,6 +135,25 @@ def eig_flops(n: int) -> float:
 
 
 # ----------------------------------------------------------------------------
+# replicas: every rank runs the whole workload on its own GPU (weak scaling)
+# ----------------------------------------------------------------------------
+def max_over_ranks(values, world: int, device=None) -> list:
+    """The slowest rank's figures: an all-reduce MAX over the process group
+    (NCCL on GPUs, gloo on the host); a no-op for one rank."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Units per second over all ranks, timed by the slowest rank."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
+# ----------------------------------------------------------------------------
 # the GPU arm
 # ----------------------------------------------------------------------------
 # FP32 SIMT peak (mixed path stages): 152 SMs x 2.07 GHz x 128 FFMA/clk x 2.
@@ -269,10 +288,7 @@ def run_gpu(args, rank, world, local_rank):
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
 
-    if world > 1:
-        t = torch.tensor([ms, e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], world, dev)
     if rank != 0:
         return
 
@@ -303,10 +319,9 @@ def run_gpu(args, rank, world, local_rank):
                  "traffic": (round(traffic) if traffic else None), "flops_per_launch": work,
                  "ms_per_launch": round(dur, 3)})
     eig_stages = ("band_reduction", "bulge_chasing", "tridiag_dc", "back_q2", "back_q1", "refine")
-    solves = k * world
     line = {
         "metric": METRIC,
-        "value": round(solves / (ms * 1e-3), 4),
+        "value": round(whole_job_rate(k, world, ms), 4),
         "unit": "solves/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -321,7 +336,7 @@ def run_gpu(args, rank, world, local_rank):
                               "precision": head}),
         "paths": {},
         "roofline": roof,
-        "e2e": {"value": round(solves / (e2e_ms * 1e-3), 4), "unit": "solves/s",
+        "e2e": {"value": round(whole_job_rate(k, world, e2e_ms), 4), "unit": "solves/s",
                 "h2d_bytes_per_step": int(mask_h.numel() + F_h.numel() * 8 + pf_h.numel() * 4 + pa_h.numel() * 8),
                 "d2h_bytes_per_step": int(U_h.numel() * 8), "ms_per_step": round(e2e_ms, 3)},
         "gpu_launches": int(R["launches"]),
@@ -548,11 +563,13 @@ def run_batched_bench(args):
     print(json.dumps(line), flush=True)
 
 
-def run_apply_bench(args):
+def run_apply_bench(args, diffusion=False):
     """The apply at scale: 192 x 192 grid (n = 18278), 4096 distinct forcings
     with alpha ~ U(0.1, 1.9); (V, lambda) computed once beforehand; one step =
     frac_apply of all 4096 pairs with the products as 6 BF16 slices on the
-    tensor cores (FP64 products timed beside it)."""
+    tensor cores (FP64 products timed beside it).  With diffusion=True the
+    step is frac_diffusion instead: the 4096 columns are initial states
+    evolved to the paper's t = 0.4 with mu = 1."""
     import torch
     import paper_1911_11906_gb300 as F
     from paper_1911_11906_gb300 import inputs as I
@@ -566,6 +583,7 @@ def run_apply_bench(args):
     pf = torch.from_numpy(p.pair_f.astype(np.int32)).cuda()
     pa = torch.from_numpy(p.pair_alpha.astype(np.float64)).cuda()
     k = len(p.pair_f)
+    pt = torch.full((k,), 0.4, dtype=torch.float64, device=mask.device)
     U = F._binding.empty_colmajor(p.n, k, mask.device)
     lines = {}
     for slices in (0, 6):
@@ -574,11 +592,37 @@ def run_apply_bench(args):
                          dtype=torch.uint8, device=mask.device)
 
         def step():
-            F.frac_apply(V, lam, Fd, pf, pa, ctx=ctx, out=U, workspace=ws, sync=False)
+            if diffusion:
+                F.frac_diffusion(V, lam, Fd, pf, pa, pt, mu=1.0, ctx=ctx, out=U, workspace=ws, sync=False)
+            else:
+                F.frac_apply(V, lam, Fd, pf, pa, ctx=ctx, out=U, workspace=ws, sync=False)
 
-        lines[slices] = _timed_line(args, "fractional solves/s at <=1e-10 err vs FP64 (apply at scale, n=18278)",
-                                    "solves/s", k, step, ctx, {})
+        metric = ("fractional diffusion solves/s at <=1e-10 err vs FP64 (n=18278, t=0.4)" if diffusion else
+                  "fractional solves/s at <=1e-10 err vs FP64 (apply at scale, n=18278)")
+        lines[slices] = _timed_line(args, metric, "solves/s", k, step, ctx, {})
         lines[slices]["U"] = U.clone()
+    if diffusion:
+        d = lines[6].pop("U") - lines[0].pop("U")
+        rel = float((torch.linalg.norm(d, dim=0) / torch.linalg.norm(U, dim=0)).max())
+        # semigroup evidence on 8 states: S(0.3) S(0.1) u0 = S(0.4) u0, 6 slices
+        ctx.set_apply_slices(6)
+        f8 = torch.arange(8, dtype=torch.int32, device=mask.device)
+        half = F.frac_diffusion(V, lam, Fd, f8, pa[:8], torch.full((8,), 0.1, dtype=torch.float64,
+                                                                   device=mask.device), ctx=ctx)
+        two = F.frac_diffusion(V, lam, half, f8, pa[:8], torch.full((8,), 0.3, dtype=torch.float64,
+                                                                    device=mask.device), ctx=ctx)
+        sg = float((torch.linalg.norm(two - U[:, :8], dim=0) / torch.linalg.norm(U[:, :8], dim=0)).max())
+        head = lines[6]
+        head.update({"dtype": "bf16 slices (6 per operand) into fp64",
+                     "config": {"workload": "diffusion192: 192x192 ellipse grid, n=%d, 4096 distinct initial "
+                                            "states, alpha~U(0.1,1.9), t=0.4, mu=1" % p.n,
+                                "n": p.n, "pairs": k, "products": "6 BF16 slices on tcgen05",
+                                "l2_policy": "inputs larger than L2 (V is %.1f GB)" % (8 * p.n * p.n / 1e9)},
+                     "fp64_products": {"value": lines[0]["value"], "ms_per_step": lines[0]["ms_per_step"]},
+                     "accuracy": {"u_rel_l2_vs_fp64_products_max": rel, "semigroup_rel_l2_max": sg,
+                                  "meets_1e-10": bool(rel <= 1e-10)}})
+        print(json.dumps(head), flush=True)
+        return
     # alpha = 2 evidence: solve with the same V, lambda for 8 forcings, against CG
     ctx.set_apply_slices(6)
     f8 = torch.arange(8, dtype=torch.int32, device=mask.device)
@@ -632,15 +676,16 @@ def main():
     ap.add_argument("--product-only", type=int, default=0, metavar="N",
                     help="profiling aid: run only FP64-accurate slice products N x N x N (R = X^T X "
                          "shape), --steps times after --warmup, and print their CUDA-event times")
-    ap.add_argument("--workload", default="ellipse128", choices=["ellipse128", "batched256", "apply192"],
-                    help="ellipse128: the headline workload; batched256 and apply192: the batched and "
-                         "apply-at-scale workloads, one JSON line each")
+    ap.add_argument("--workload", default="ellipse128",
+                    choices=["ellipse128", "batched256", "apply192", "diffusion192"],
+                    help="ellipse128: the headline workload; batched256, apply192 and diffusion192: the "
+                         "batched, apply-at-scale and diffusion-at-scale workloads, one JSON line each")
     args = ap.parse_args()
     if args.workload == "batched256":
         run_batched_bench(args)
         return
-    if args.workload == "apply192":
-        run_apply_bench(args)
+    if args.workload in ("apply192", "diffusion192"):
+        run_apply_bench(args, diffusion=args.workload == "diffusion192")
         return
     if args.product_only > 0:
         run_product_only(args)

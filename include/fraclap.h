@@ -164,7 +164,34 @@ int frac_apply(fraclap_ctx* ctx, const double* V_dev, int64_t ldv, const double*
                fraclap_stream_t stream);
 
 /* ------------------------------------------------------------------------
- * frac_apply_noalloc — frac_apply for callers that cannot allocate device
+ * frac_diffusion — the solution of the space-fractional diffusion equation
+ * du/dt + mu (-Laplacian)^{alpha/2} u = 0 with homogeneous Dirichlet
+ * conditions (Sec. II, eqs. model_diffusion and diffusion_solution): every
+ * eigenmode decays at its own rate,
+ *   u_j = V diag(exp(-mu lambda^{alpha_j / 2} t_j)) V^T u0_{pair_f[j]},  j = 0..k-1.
+ * Pair j evolves initial state pair_f[j] with order pair_alpha[j] to time
+ * pair_t[j] (any real t; t = 0 returns the initial state, alpha = 0 decays
+ * every mode by exp(-mu t)).  With alpha != 0 every lambda must be > 0, else
+ * the device status becomes FRACLAP_ERR_NOT_SPD; a pair index outside [0, m)
+ * sets FRACLAP_ERR_INVALID_ARG there (its column is zero).
+ *
+ *  V_dev double[ldv*n], lambda_dev double[n]: a decomposition from eig_full.
+ *  U0_dev double[ldu0*m]: m distinct initial states in columns; ldu0 >= n.
+ *  pair_f_dev int32[k], pair_alpha_dev double[k], pair_t_dev double[k].
+ *  mu: the diffusion coefficient, finite (else FRACLAP_ERR_INVALID_ARG).
+ *  U_dev double[ldu*k] out; ldu >= n.
+ *  work: fraclap_apply_workspace_bytes_ctx(ctx, n, m, k) bytes.  The products
+ *  follow the context's fraclap_set_apply_slices setting, as in frac_apply.
+ *  Returns FRACLAP_ERR_UNSUPPORTED for k > 65535; asynchronous on `stream`.
+ * ---------------------------------------------------------------------- */
+int frac_diffusion(fraclap_ctx* ctx, const double* V_dev, int64_t ldv, const double* lambda_dev,
+                   int64_t n, const double* U0_dev, int64_t ldu0, int64_t m,
+                   const int32_t* pair_f_dev, const double* pair_alpha_dev, const double* pair_t_dev,
+                   double mu, int64_t k, double* U_dev, int64_t ldu, void* work_dev,
+                   size_t work_bytes, fraclap_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * frac_apply_noalloc —frac_apply for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a deployment variant.
  * It serves code that runs where cudaMalloc is not available to it: inside a
  * host framework whose memory pool already owns the device (an extra

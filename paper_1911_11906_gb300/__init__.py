@@ -17,6 +17,7 @@ from ._binding import (  # noqa: F401
     eig_full,
     eig_full_mixed,
     frac_apply,
+    frac_diffusion,
     tridiagonalize,
     tridiag_eig,
     dgemm,

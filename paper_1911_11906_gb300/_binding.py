@@ -29,6 +29,8 @@ SIGNATURES = {
     "eig_full_mixed": (_i32, [_p, _p, _i64, _i64, _p, _p, _p, _i32, _p, _p, _i64, _p, _sz, _p, _p]),
     "fraclap_apply_workspace_bytes": (_sz, [_i64, _i64, _i64]),
     "frac_apply": (_i32, [_p, _p, _i64, _p, _i64, _p, _i64, _i64, _p, _p, _i64, _p, _i64, _p, _sz, _p]),
+    "frac_diffusion": (_i32, [_p, _p, _i64, _p, _i64, _p, _i64, _i64, _p, _p, _p, _dbl, _i64, _p, _i64, _p, _sz,
+                              _p]),
     "frac_apply_noalloc": (_i32, [_p, _i64, _p, _i64, _p, _i64, _i64, _p, _p, _i64, _p, _i64, _p, _p]),
     "fraclap_tridiagonalize": (_i32, [_p, _p, _i64, _i64, _p, _p, _p, _i64, _p, _sz, _p]),
     "fraclap_tridiag_workspace_bytes": (_sz, [_p, _i64]),
@@ -283,6 +285,35 @@ def frac_apply(V: torch.Tensor, lam: torch.Tensor, F: torch.Tensor, pair_f, pair
     st = ctypes.c_void_p(_stream(stream))
     ctx.check(ctx.lib.frac_apply(ctx.handle, _ptr(V), _ld(V), _ptr(lam.contiguous()), n, _ptr(F), _ld(F), m,
                                  _ptr(pf), _ptr(pa), k, _ptr(U), _ld(U), _ptr(workspace), workspace.numel(), st))
+    if sync:
+        ctx.sync(stream)
+    return U
+
+
+def frac_diffusion(V: torch.Tensor, lam: torch.Tensor, U0: torch.Tensor, pair_f, pair_alpha, pair_t,
+                   mu: float = 1.0, ctx: Context | None = None, stream=None, out: torch.Tensor | None = None,
+                   workspace: torch.Tensor | None = None, sync: bool = True) -> torch.Tensor:
+    """u_j = V diag(exp(-mu lam^{alpha_j/2} t_j)) V^T U0[:, pair_f[j]]: the
+    fractional diffusion solution at time t_j; returns U (n x k, column-major)."""
+    ctx = ctx or default_context()
+    V = _f64_colmajor(V, "V")
+    U0 = _f64_colmajor(U0, "U0")
+    n = V.shape[0]
+    dev = V.device
+    pf = torch.as_tensor(pair_f, dtype=torch.int32).to(dev).contiguous()
+    pa = torch.as_tensor(pair_alpha, dtype=torch.float64).to(dev).contiguous()
+    pt = torch.as_tensor(pair_t, dtype=torch.float64).to(dev).contiguous()
+    k, m = pf.numel(), U0.shape[1]
+    if pa.numel() != k or pt.numel() != k:
+        raise ValueError("pair_f, pair_alpha and pair_t differ in length")
+    U = out if out is not None else empty_colmajor(n, k, dev)
+    if workspace is None:
+        nbytes = ctx.lib.fraclap_apply_workspace_bytes_ctx(ctx.handle, n, m, k)
+        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.frac_diffusion(ctx.handle, _ptr(V), _ld(V), _ptr(lam.contiguous()), n, _ptr(U0), _ld(U0), m,
+                                     _ptr(pf), _ptr(pa), _ptr(pt), float(mu), k, _ptr(U), _ld(U),
+                                     _ptr(workspace), workspace.numel(), st))
     if sync:
         ctx.sync(stream)
     return U

@@ -1,22 +1,29 @@
 // frac_apply: u_j = V diag(lambda^{-alpha_j/2}) V^T f_{pair_f[j]}
 // (Sec. II, eq. poisson_solution; the sum v after eq. discrete_laplace).
+// frac_diffusion: u_j = V diag(exp(-mu lambda^{alpha_j/2} t_j)) V^T u0_{pair_f[j]}
+// (Sec. II, eq. diffusion_solution).
 //
-// Two GEMMs (W = V^T F over the m distinct forcings, then U = V C) around an
-// elementwise kernel that forms the spectral coefficients
-// C(i, j) = lambda_i^{-alpha_j/2} W(i, pair_f[j]); pow() is CUDA's
-// double-precision pow.  The GEMMs run on the FP64 engine, or (context
-// setting apply_slices = s > 0) as products of s BF16 slices on the tensor
-// cores, accurate to about 2^-8s relative to |row max| |column max| per
-// term (s = 7: FP64 level).  A zero or negative eigenvalue met with
-// alpha != 0 raises FRACLAP_ERR_NOT_SPD in the device status.
+// Two GEMMs (W = V^T F over the m distinct forcings or initial states, then
+// U = V C) around an elementwise kernel that forms the spectral coefficients
+// C(i, j) = g_j(lambda_i) W(i, pair_f[j]) with g_j the pair's multiplier;
+// pow() and exp() are CUDA's double-precision functions.  The GEMMs run on
+// the FP64 engine, or (context setting apply_slices = s > 0) as products of
+// s BF16 slices on the tensor cores, accurate to about 2^-8s relative to
+// |row max| |column max| per term (s = 7: FP64 level).  A zero or negative
+// eigenvalue met with alpha != 0 raises FRACLAP_ERR_NOT_SPD in the device
+// status.
+#include <cmath>
+
 #include "internal.cuh"
 
 namespace fraclap {
 namespace {
 
+// pair_t == nullptr: the Poisson multiplier lambda^{-alpha/2}; otherwise the
+// diffusion multiplier exp(-mu lambda^{alpha/2} t_j).
 __global__ void spectral_scale(const double* lambda, int64_t n, const double* W, int64_t ldw,
-                               const int32_t* pair_f, const double* pair_alpha, int64_t k,
-                               int64_t m, double* C, int64_t ldc, int32_t* status) {
+                               const int32_t* pair_f, const double* pair_alpha, const double* pair_t,
+                               double mu, int64_t k, int64_t m, double* C, int64_t ldc, int32_t* status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t j = blockIdx.y;
   if (i >= n || j >= k) return;
@@ -28,12 +35,56 @@ __global__ void spectral_scale(const double* lambda, int64_t n, const double* W,
     return;
   }
   const double lam = lambda[i];
-  double mult = 1.0;
+  double p = 1.0;  // lambda^{-alpha/2} (Poisson) or lambda^{alpha/2} (diffusion rate)
   if (alpha != 0.0) {
     if (!(lam > 0.0)) raise_status(status, FRACLAP_ERR_NOT_SPD);
-    mult = pow(lam, -0.5 * alpha);
+    p = pow(lam, (pair_t ? 0.5 : -0.5) * alpha);
   }
+  const double mult = pair_t ? exp(-mu * p * pair_t[j]) : p;
   C[i + j * ldc] = mult * W[i + (int64_t)f * ldw];
+}
+
+// The body shared by frac_apply and frac_diffusion.
+int spectral_apply(fraclap_ctx* ctx, const char* name, const double* V_dev, int64_t ldv,
+                   const double* lambda_dev, int64_t n, const double* F_dev, int64_t ldf, int64_t m,
+                   const int32_t* pair_f_dev, const double* pair_alpha_dev, const double* pair_t_dev,
+                   double mu, int64_t k, double* U_dev, int64_t ldu, void* work_dev, size_t work_bytes,
+                   cudaStream_t st) {
+  FL_CHECK(ctx, n >= 0 && m >= 0 && k >= 0, FRACLAP_ERR_INVALID_ARG, "%s: negative size", name);
+  if (n == 0 || k == 0) return 0;
+  FL_CHECK(ctx, m >= 1, FRACLAP_ERR_INVALID_ARG, "%s: pairs need at least one input column", name);
+  FL_CHECK(ctx, V_dev && lambda_dev && F_dev && pair_f_dev && pair_alpha_dev && U_dev,
+           FRACLAP_ERR_INVALID_ARG, "%s: null pointer", name);
+  FL_CHECK(ctx, ldv >= n && ldf >= n && ldu >= n, FRACLAP_ERR_INVALID_ARG, "%s: leading dimension < n", name);
+  FL_CHECK(ctx, k <= 65535 && m <= 65535 * 64, FRACLAP_ERR_UNSUPPORTED, "%s: at most 65535 pairs per call", name);
+  StageTimer timer(ctx, kStageApply, st);
+  Arena ar;
+  FL_TRY(get_workspace(ctx, work_dev, work_bytes, fraclap_apply_workspace_bytes_ctx(ctx, n, m, k), &ar));
+  double* W = ar.take<double>(n * m);
+  double* C = ar.take<double>(n * k);
+  FL_CHECK(ctx, W && C, FRACLAP_ERR_ALLOC, "%s: workspace too small", name);
+  const int ozs = ctx->apply_slices;
+  // W = V^T F
+  if (ozs > 0) {
+    Arena oz = ar;
+    FL_TRY(ozaki_gemm(ctx, true, false, n, m, n, 1.0, V_dev, ldv, F_dev, ldf, 0.0, W, n, ozs, false, &oz, st));
+  } else {
+    GemmDesc d{n, m, n, V_dev, ldv, F_dev, ldf, W, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+    FL_TRY(gemm(ctx, true, false, kGemmPlain, d, 1, st));
+  }
+  spectral_scale<<<dim3((unsigned)cdiv(n, 256), (unsigned)k), 256, 0, st>>>(
+      lambda_dev, n, W, n, pair_f_dev, pair_alpha_dev, pair_t_dev, mu, k, m, C, n, ctx->d_status);
+  count_launch(ctx);
+  FL_CUDA(ctx, cudaGetLastError());
+  // U = V C
+  if (ozs > 0) {
+    Arena oz = ar;
+    FL_TRY(ozaki_gemm(ctx, false, false, n, k, n, 1.0, V_dev, ldv, C, n, 0.0, U_dev, ldu, ozs, false, &oz, st));
+  } else {
+    GemmDesc d{n, k, n, V_dev, ldv, C, n, U_dev, ldu, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
+    FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
+  }
+  return 0;
 }
 
 }  // namespace
@@ -67,43 +118,22 @@ extern "C" int frac_apply(fraclap_ctx* ctx, const double* V_dev, int64_t ldv,
                           int64_t k, double* U_dev, int64_t ldu, void* work_dev, size_t work_bytes,
                           fraclap_stream_t stream) {
   if (!ctx) return FRACLAP_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  FL_CHECK(ctx, n >= 0 && m >= 0 && k >= 0, FRACLAP_ERR_INVALID_ARG, "frac_apply: negative size");
-  if (n == 0 || k == 0) return 0;
-  FL_CHECK(ctx, m >= 1, FRACLAP_ERR_INVALID_ARG, "frac_apply: pairs need at least one forcing");
-  FL_CHECK(ctx, V_dev && lambda_dev && F_dev && pair_f_dev && pair_alpha_dev && U_dev,
-           FRACLAP_ERR_INVALID_ARG, "frac_apply: null pointer");
-  FL_CHECK(ctx, ldv >= n && ldf >= n && ldu >= n, FRACLAP_ERR_INVALID_ARG, "frac_apply: leading dimension < n");
-  FL_CHECK(ctx, k <= 65535 * 64 && m <= 65535 * 64, FRACLAP_ERR_UNSUPPORTED, "frac_apply: too many pairs");
-  StageTimer timer(ctx, kStageApply, st);
-  Arena ar;
-  FL_TRY(get_workspace(ctx, work_dev, work_bytes, fraclap_apply_workspace_bytes_ctx(ctx, n, m, k), &ar));
-  double* W = ar.take<double>(n * m);
-  double* C = ar.take<double>(n * k);
-  FL_CHECK(ctx, W && C, FRACLAP_ERR_ALLOC, "frac_apply: workspace too small");
-  const int ozs = ctx->apply_slices;
-  // W = V^T F
-  if (ozs > 0) {
-    Arena oz = ar;
-    FL_TRY(ozaki_gemm(ctx, true, false, n, m, n, 1.0, V_dev, ldv, F_dev, ldf, 0.0, W, n, ozs, false, &oz, st));
-  } else {
-    GemmDesc d{n, m, n, V_dev, ldv, F_dev, ldf, W, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
-    FL_TRY(gemm(ctx, true, false, kGemmPlain, d, 1, st));
-  }
-  FL_CHECK(ctx, k <= 65535, FRACLAP_ERR_UNSUPPORTED, "frac_apply: at most 65535 pairs per call");
-  spectral_scale<<<dim3((unsigned)cdiv(n, 256), (unsigned)k), 256, 0, st>>>(
-      lambda_dev, n, W, n, pair_f_dev, pair_alpha_dev, k, m, C, n, ctx->d_status);
-  count_launch(ctx);
-  FL_CUDA(ctx, cudaGetLastError());
-  // U = V C
-  if (ozs > 0) {
-    Arena oz = ar;
-    FL_TRY(ozaki_gemm(ctx, false, false, n, k, n, 1.0, V_dev, ldv, C, n, 0.0, U_dev, ldu, ozs, false, &oz, st));
-  } else {
-    GemmDesc d{n, k, n, V_dev, ldv, C, n, U_dev, ldu, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
-    FL_TRY(gemm(ctx, false, false, kGemmPlain, d, 1, st));
-  }
-  return 0;
+  return spectral_apply(ctx, "frac_apply", V_dev, ldv, lambda_dev, n, F_dev, ldf, m, pair_f_dev,
+                        pair_alpha_dev, nullptr, 0.0, k, U_dev, ldu, work_dev, work_bytes,
+                        (cudaStream_t)stream);
+}
+
+extern "C" int frac_diffusion(fraclap_ctx* ctx, const double* V_dev, int64_t ldv,
+                              const double* lambda_dev, int64_t n, const double* U0_dev, int64_t ldu0,
+                              int64_t m, const int32_t* pair_f_dev, const double* pair_alpha_dev,
+                              const double* pair_t_dev, double mu, int64_t k, double* U_dev,
+                              int64_t ldu, void* work_dev, size_t work_bytes, fraclap_stream_t stream) {
+  if (!ctx) return FRACLAP_ERR_INVALID_ARG;
+  FL_CHECK(ctx, k == 0 || n == 0 || pair_t_dev, FRACLAP_ERR_INVALID_ARG, "frac_diffusion: null pointer");
+  FL_CHECK(ctx, std::isfinite(mu), FRACLAP_ERR_INVALID_ARG, "frac_diffusion: mu is not finite");
+  return spectral_apply(ctx, "frac_diffusion", V_dev, ldv, lambda_dev, n, U0_dev, ldu0, m, pair_f_dev,
+                        pair_alpha_dev, pair_t_dev, mu, k, U_dev, ldu, work_dev, work_bytes,
+                        (cudaStream_t)stream);
 }
 
 // ----------------------------------------------------------------------------
@@ -185,7 +215,7 @@ extern "C" int frac_apply_noalloc(const double* V_dev, int64_t ldv, const double
   int r = gemm(&local, true, false, kGemmPlain, d, 1, st);
   if (r != 0) return r;
   spectral_scale<<<dim3((unsigned)cdiv(n, 256), (unsigned)k), 256, 0, st>>>(
-      lambda_dev, n, W, n, pair_f_dev, pair_alpha_dev, k, m, C, n, status);
+      lambda_dev, n, W, n, pair_f_dev, pair_alpha_dev, nullptr, 0.0, k, m, C, n, status);
   if (cudaGetLastError() != cudaSuccess) return FRACLAP_ERR_CUDA;
   d = GemmDesc{n, k, n, V_dev, ldv, C, n, U_dev, ldu, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
   return gemm(&local, false, false, kGemmPlain, d, 1, st);

@@ -75,6 +75,32 @@ def test_full_size_workload(workload, route):
     for t, i in enumerate(cols):
         r = O.spmv(A, Vc[:, t]) - lam_h[i] * Vc[:, t]
         assert np.linalg.norm(r) <= 1e-12 * nA
+    _diffusion_properties(F, ctx, A, lam, V, p.F[:, :2])
+
+
+def _diffusion_properties(F, ctx, A, lam, V, u0):
+    """Fractional diffusion (Sec. II eq. diffusion_solution) at full size,
+    through properties that hold at any size: t = 0 returns u0, the
+    semigroup u(t1 + t2) = S(t2) u(t1), norms that never grow and shrink
+    with t, and commutation with A (A from the oracle's assembly)."""
+    al = [0.75, 2.0]
+    ud = torch.from_numpy(np.ascontiguousarray(u0.T)).cuda().t()
+
+    def S(x, t):
+        return F.frac_diffusion(V, lam, x, [0, 1], al, [t, t], mu=1.0, ctx=ctx)
+
+    z = S(ud, 0.0).cpu().numpy()
+    assert np.linalg.norm(z - u0) <= 1e-12 * np.linalg.norm(u0)
+    u1, u3 = S(ud, 1e-4), S(ud, 3e-4).cpu().numpy()
+    u2 = F.frac_diffusion(V, lam, u1, [0, 1], al, [2e-4, 2e-4], ctx=ctx).cpu().numpy()
+    assert np.linalg.norm(u2 - u3) <= 1e-12 * np.linalg.norm(u3)
+    n0, n1, n3 = (np.linalg.norm(x, axis=0) for x in (u0, u1.cpu().numpy(), u3))
+    assert np.all(n1 < n0) and np.all(n3 < n1)
+    Au0 = np.stack([O.spmv(A, u0[:, c]) for c in range(2)], axis=1)
+    Sa = S(torch.from_numpy(np.ascontiguousarray(Au0.T)).cuda().t(), 3e-4).cpu().numpy()
+    for c in range(2):
+        aS = O.spmv(A, u3[:, c])
+        assert np.linalg.norm(aS - Sa[:, c]) <= 1e-9 * np.linalg.norm(Sa[:, c])
 
 
 def test_batched_problems_match_oracle():
