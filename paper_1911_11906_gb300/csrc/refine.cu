@@ -19,7 +19,10 @@
 // |l_j - l_i| <= delta (the method's own test), or a first-order coefficient
 // above the context's threshold (1e-3 by default), whose second-order error
 // would spoil the quadratic convergence when the starting vectors are only
-// FP32-accurate (this safeguard is ours).  Using the lower triangles of R and
+// FP32-accurate (this safeguard is ours).  Inside a run of more than 64
+// positions the pairs are tested again by the first-order coefficient alone
+// (ours too): delta is a bound on the whole coupling matrix, and where the
+// spectrum is denser than delta it chains most of it into one cluster.  Using the lower triangles of R and
 // S as symmetric matrices keeps E_ij + E_ji = r_ij, so orthogonality improves
 // to first order exactly.  A enters only through products with its CSR form
 // (5/7 nonzeros per row).  The eigenvalues returned are the Rayleigh
@@ -181,6 +184,9 @@ __global__ void gershgorin(int64_t n, const int64_t* rowptr, const double* val,
   atomicMax(out, (unsigned long long)__double_as_longlong(s));  // non-negative doubles order as bits
 }
 
+// Largest cluster diagonalised by the batched Jacobi step (one CTA each).
+constexpr int kMaxCluster = 64;
+
 // delta = 2 (||S - D||_2 + ||A||_2 ||R||_2) with the 2-norms of S - D and R
 // estimated by power iteration (times a safety factor 2, the estimates being
 // lower bounds) and capped by their Frobenius norms; ||A||_2 by Gershgorin.
@@ -195,9 +201,16 @@ __global__ void cluster_threshold(const double* acc, const double* est, const un
 // Unsafe pairs: |l_j - l_i| <= delta, or a first-order coefficient
 // |s_ij + l r_ij| / |l_j - l_i| above tau.  Each unsafe pair (i, j) stretches
 // the span starting at its smaller sorted position to its larger one.
+// Second pass (big != nullptr, and only if big[n] is set): for two positions
+// inside the same cluster of the first pass that is larger than kMaxCluster
+// (big[pos] = its index, else -1) only the per-pair test decides.  delta
+// bounds the coupling norm of the whole matrix, and where the spectrum is
+// denser than delta (3-D grids at n ~ 3e4) it chains thousands of pairs
+// whose first-order coefficients are all small.
 __global__ void unsafe_spans(const double* S, int64_t lds, const double* R, int64_t ldr,
                              const double* lt, const int* rank, const double* delta, double tau,
-                             int64_t n, int* reach) {
+                             int64_t n, const int* big, int* reach) {
+  if (big && !big[n]) return;
   const int64_t total = n * n;
   const double dl = *delta;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
@@ -207,22 +220,36 @@ __global__ void unsafe_spans(const double* S, int64_t lds, const double* R, int6
     const double g = fabs(lt[j] - lt[i]);
     const double s = S[i + j * lds], r = R[i + j * ldr];
     const double num = fmax(fabs(s + lt[j] * r), fabs(s + lt[i] * r));
-    if (g <= dl || num > tau * g) {
-      const int a = min(rank[i], rank[j]), b = max(rank[i], rank[j]);
-      atomicMax(reach + a, b);
-    }
+    const int a = min(rank[i], rank[j]), b = max(rank[i], rank[j]);
+    const bool inner = big && big[a] >= 0 && big[a] == big[b];
+    if ((!inner && g <= dl) || num > tau * g) atomicMax(reach + a, b);
   }
 }
 
-__global__ void init_reach(int* reach, int64_t n) {
+// reach[pos] = pos; a second pass (flag != nullptr) runs only if *flag is set.
+__global__ void init_reach(int* reach, int64_t n, const int* flag) {
+  if (flag && !*flag) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) reach[i] = (int)i;
 }
 
+// big[pos] = cluster index of pos if its cluster has more than kMaxCluster
+// members, else -1; big[n] = 1 if there is such a cluster (zeroed before).
+__global__ void mark_big(const int* cid, const int* list, int64_t n, int* big) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = cid[i];
+  const bool b = c >= 0 && list[2 * c + 1] > kMaxCluster;
+  big[i] = b ? c : -1;
+  if (b) big[n] = 1;
+}
+
 // Merges the spans (sorted positions) into clusters: cid[pos] = cluster
-// index or -1; list = (start, size) pairs; *count.  One thread.
-__global__ void merge_spans(const int* reach, int64_t n, int* cid, int* list, int* count) {
+// index or -1; list = (start, size) pairs; *count.  One thread.  A second
+// pass (flag != nullptr) runs only if *flag is set.
+__global__ void merge_spans(const int* reach, int64_t n, int* cid, int* list, int* count, const int* flag) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (flag && !*flag) return;
   int c = 0;
   int64_t i = 0;
   while (i < n) {
@@ -310,7 +337,6 @@ __global__ void copy_columns(const double* Xs, int64_t n, double* X, int64_t ldx
 // Cyclic Jacobi on one symmetric c x c block (c <= 64), one CTA.
 // In: Sc (ld c).  Out: Q (ld c, eigenvectors in columns), w (eigenvalues),
 // both ascending.
-constexpr int kMaxCluster = 64;
 // Stop after the iteration that starts with ||R||_2 and ||S - D||_2 / ||A||_2 below this
 // (its quadratic step lands at rounding level).
 constexpr double kConvergedR = 3e-9;
@@ -717,6 +743,7 @@ size_t refine_ws(const fraclap_ctx* ctx, int64_t n) {
   ar.take<int>(n);             // ranks
   ar.take<int>(n);             // span reach
   ar.take<int>(n);             // cluster id per sorted position
+  ar.take<int>(n + 1);         // big-cluster marks + flag
   ar.take<int>(2 * n + 2);     // cluster list + count
   ar.take<double>(8);          // norms, delta
   const int64_t cmax = std::min<int64_t>(n, kMaxBigCluster);
@@ -739,6 +766,7 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
   int* rank = ar->take<int>(n);
   int* reach = ar->take<int>(n);
   int* cid = ar->take<int>(n);
+  int* bigm = ar->take<int>(n + 1);
   int* clist = ar->take<int>(2 * n + 2);
   double* scal = ar->take<double>(8);
   ctx->refine_stats.clear();
@@ -814,12 +842,19 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
     // clusters from unsafe pairs, in sorted order
     ranks<<<(unsigned)cdiv(n, 128), 128, 0, st>>>(lt, n, rank);
     count_launch(ctx);
-    init_reach<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(reach, n);
+    init_reach<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(reach, n, nullptr);
     count_launch(ctx);
-    unsafe_spans<<<flat, 256, 0, st>>>(S, n, R, n, lt, rank, delta, ctx->refine_tau, n, reach);
+    unsafe_spans<<<flat, 256, 0, st>>>(S, n, R, n, lt, rank, delta, ctx->refine_tau, n, nullptr, reach);
     count_launch(ctx);
-    merge_spans<<<1, 1, 0, st>>>(reach, n, cid, clist + 1, clist);
+    merge_spans<<<1, 1, 0, st>>>(reach, n, cid, clist + 1, clist, nullptr);
     count_launch(ctx);
+    // second pass inside clusters above kMaxCluster (device-side no-op without one)
+    FL_CUDA(ctx, cudaMemsetAsync(bigm + n, 0, sizeof(int), st));
+    mark_big<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(cid, clist + 1, n, bigm);
+    init_reach<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(reach, n, bigm + n);
+    unsafe_spans<<<flat, 256, 0, st>>>(S, n, R, n, lt, rank, delta, ctx->refine_tau, n, bigm, reach);
+    merge_spans<<<1, 1, 0, st>>>(reach, n, cid, clist + 1, clist, bigm + n);
+    for (int q = 0; q < 4; ++q) count_launch(ctx);
     correction<<<flat, 256, 0, st>>>(S, n, R, n, lt, rank, cid, n, E, n, X, ldx, X32);
     count_launch(ctx);
     // X += X E  (product in FP32)

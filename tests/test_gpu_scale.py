@@ -181,3 +181,61 @@ def test_apply_at_scale():
         outs[slices] = U
     diff = torch.linalg.norm(outs[6] - outs[0], dim=0) / torch.linalg.norm(outs[0], dim=0)
     assert float(diff.max()) <= 1e-10
+
+
+def test_holed_cube_full_size(capsys):
+    """The 3-D workload at full size: the 32^3 cube minus 5 seeded spherical
+    holes (7-point stencil, h = 1/33, n = 31996), 64 polynomial forcings x
+    alpha in {0.25, 0.75, 1.25, 1.75}, mixed route (FP32 stages, refinement
+    whose residual products are BF16 slices on the tensor cores).  The oracle
+    cannot decompose n = 31996, so: eigenvalues bracketed at +-1e-10 (the
+    refined eigenvalue tolerance) by its inertia counts, the trace identity
+    6 n / h^2, Gershgorin, sampled orthogonality and residuals, and the
+    workload's own orders composed in pairs, S(1.75) S(0.25) f = S(1.25) S(0.75) f
+    = A^-1 f, against its direct banded solve."""
+    import paper_1911_11906_gb300 as F
+    p = I.holed_cube_problem()
+    assert p.n == 31996 and len(p.pair_f) == 256
+    _, A = O.assemble(p.mask, p.h)
+    ctx = F.Context(band_width=64)
+    ctx.set_profiling(True)
+    asm = F.fd_assemble(torch.from_numpy(p.mask).cuda(), p.h, ctx=ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lam, V = F.eig_full_mixed(asm["A"], asm["rowptr"], asm["col"], asm["val"], refine_iters=6, ctx=ctx)
+    e1.record()
+    torch.cuda.synchronize()
+    del asm
+    stages = {k: round(v[0], 1) for k, v in ctx.stage_times().items() if v[1]}
+    rs = ctx.refine_stats()
+    iters = len(rs)
+    Fd = torch.from_numpy(np.ascontiguousarray(p.F.T)).cuda().t()
+    U = F.frac_apply(V, lam, Fd, p.pair_f, p.pair_alpha, ctx=ctx)
+    with capsys.disabled():
+        print(f"\nholedcube32 n={p.n}: mixed decomposition {e0.elapsed_time(e1) / 1e3:.2f} s, "
+              f"{iters} refinement iterations, stages (ms) {stages}, per iteration (|R|_2, clusters, "
+              f"largest) {[(float('%.2e' % r['norm2_R']), int(r['clusters']), int(r['largest_cluster'])) for r in rs]}")
+    lam_h = lam.cpu().numpy()
+    h = p.h
+    assert np.all(np.diff(lam_h) >= 0)
+    assert lam_h[0] > 0 and lam_h[-1] <= 12.0 / h ** 2 * (1 + 1e-14)
+    tr = 6 * p.n / h ** 2
+    assert abs(lam_h.sum() - tr) <= 1e-12 * tr
+    for i in _bracket_indices(lam_h, (0, p.n // 2, p.n - 1), 6.0 / h ** 2):
+        assert _bracketed(A, lam_h, i, rel=1e-10), i
+    rng = np.random.default_rng(31996)
+    cols = np.sort(rng.choice(p.n, size=16, replace=False))
+    Vc = V[:, torch.from_numpy(cols).cuda()]
+    G = (V.t() @ Vc).cpu().numpy()
+    G[cols, np.arange(cols.size)] -= 1.0
+    assert np.abs(G).max() <= 1e-12
+    Vc = Vc.cpu().numpy()
+    for t, i in enumerate(cols):
+        r = O.spmv(A, Vc[:, t]) - lam_h[i] * Vc[:, t]
+        assert np.linalg.norm(r) <= 1e-12 * 12.0 / h ** 2
+    for f in (0, 1):
+        first = [int(np.nonzero((p.pair_f == f) & (p.pair_alpha == a))[0][0]) for a in (0.25, 0.75)]
+        U2 = F.frac_apply(V, lam, U[:, first], [0, 1], [1.75, 1.25], ctx=ctx).cpu().numpy()
+        ref = O.band_solve(A, p.F[:, f])
+        for c in range(2):
+            assert np.linalg.norm(U2[:, c] - ref) <= 1e-10 * np.linalg.norm(ref), (f, c)
