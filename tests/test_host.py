@@ -193,3 +193,24 @@ def test_reference_arm_other_ranks_do_nothing(capsys):
         steps, warmup = 1, 1
     bench.run_reference(A(), rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_ncu_launch_list_summary(tmp_path):
+    """The launch-list summary used for the committed profiles: per-kernel
+    launch counts, total device time and share, with ncu's name decoration
+    and units handled."""
+    from paper_1911_11906_gb300 import ncu_summary
+    hdr = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
+           '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n')
+    rows = [("void fraclap::<unnamed>::k1<float, 4>(float *, long)", "ns", "3,000"),
+            ("fraclap::<unnamed>::k2(double *)", "us", "1.5"),
+            ("void fraclap::<unnamed>::k1<float, 4>(float *, long)", "ns", "1000"),
+            ("fraclap::<unnamed>::k2(double *)", "ms", "0.0045")]
+    body = "".join(f'"{i}","1","p","h","{k}","1","7","(256, 1, 1)","(4, 1, 1)","0","10.3","x",'
+                   f'"gpu__time_duration.sum","{u}","{v}"\n' for i, (k, u, v) in enumerate(rows))
+    path = tmp_path / "l.csv"
+    path.write_text("==PROF== Connected\n" + hdr + body)
+    lines = ncu_summary.summarize([str(path)]).splitlines()
+    assert lines[1].split()[:3] == ["k2", "2", "0.006"] and lines[1].endswith("60.00%")
+    assert lines[2].split()[:3] == ["k1<float,", "4>", "2"] and lines[2].endswith("40.00%")
+    assert lines[-1].split()[:3] == ["TOTAL", "4", "0.010"]
