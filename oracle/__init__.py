@@ -7,6 +7,8 @@ Sec. III-D-2), written independently of the CUDA path: the two share no code.
 
 Pinned functions (see ``tests/test_oracle_*.py``): assembly, Householder +
 implicit-QR eigensolver, Jacobi, inertia counting, banded direct solve,
-spectral apply, fractional diffusion.  No function here is unpinned.
+spectral apply, fractional diffusion, and the finite-element generalised
+problem (assembly of K and M, Cholesky-reduced eigensolver, inertia of
+K - sigma M, apply in the M-inner product).  No function here is unpinned.
 """
 from .oracle import *  # noqa: F401,F403

@@ -14,6 +14,10 @@
  *     v = sum_k theta_k^{-alpha/2} <f, phi_k> phi_k  (eq. poisson_solution).
  *   - Sec. II, eq. (diffusion_solution): the fractional diffusion solution
  *     u(t) = sum_k exp(-mu theta_k^{alpha/2} t) <u0, phi_k> phi_k.
+ *   - Sec. II, eq. (discrete_laplace) with a finite-element basis: bilinear
+ *     (2-D) / trilinear (3-D) elements give K and M, the generalised problem
+ *     K phi = theta M phi is reduced by the Cholesky factor of M, and the
+ *     apply takes the M-inner product.
  *   - Sec. III-D-2 (exact eigenvalue counting): the number of eigenvalues
  *     below sigma equals the number of negative pivots of the LDL^T
  *     factorisation of A - sigma I (Sylvester's law of inertia).
@@ -571,4 +575,209 @@ int oracle_frac_diffusion(int64_t n, const double* V, int64_t ldv, const double*
   free(coef);
   free(W);
   return ORACLE_OK;
+}
+
+/* ======================================================================== */
+/* The generalised problem K phi = theta M phi of Sec. II eq.               */
+/* (discrete_laplace) with K_ij = <grad e_i, grad e_j>, M_ij = <e_i, e_j>    */
+/* for piecewise bilinear (2-D) / trilinear (3-D) basis functions e_i on the */
+/* grid cells: e_i is 1 at node i, 0 at every other node, and multilinear on */
+/* each cell.  The cells tile the unit square/cube (node indices -1..m per   */
+/* axis); nodes outside the mask are Dirichlet zeros, so K and M are the     */
+/* principal submatrices of the full-grid matrices on the dofs.              */
+/* ======================================================================== */
+
+/* 1-D integrals over one cell [0, h] of the two linear hats (local nodes 0
+ * and 1): int e_a e_b = h/3 (a = b) or h/6; int e_a' e_b' = 1/h or -1/h. */
+static double hat_mass(int a, int b, double h) { return (a == b) ? h / 3.0 : h / 6.0; }
+static double hat_stiff(int a, int b, double h) { return (a == b) ? 1.0 / h : -1.0 / h; }
+
+/* Integrals over one cell of the products of two multilinear basis
+ * functions with local corners a, b in {0,1}^dim: the mass is the product of
+ * the 1-D mass integrals, the stiffness sums over the axis d carrying the
+ * derivative (1-D stiffness along d, 1-D mass along the others). */
+static void cell_integrals(int dim, const int* a, const int* b, double h, double* k, double* m) {
+  double mass = 1.0, stiff = 0.0;
+  for (int d = 0; d < dim; ++d) mass *= hat_mass(a[d], b[d], h);
+  for (int d = 0; d < dim; ++d) {
+    double t = hat_stiff(a[d], b[d], h);
+    for (int e = 0; e < dim; ++e)
+      if (e != d) t *= hat_mass(a[e], b[e], h);
+    stiff += t;
+  }
+  *k = stiff;
+  *m = mass;
+}
+
+/* CSR of K and M (same pattern: every node of the 3^dim box around a dof
+ * that is itself a dof), columns ascending.  rowptr has n+1 entries, col,
+ * valK, valM room for 3^dim * n.  Each entry sums the cell integrals over
+ * the cells that hold both nodes.  Returns nnz. */
+int64_t oracle_assemble_fem(const int32_t* idx, int dim, const int64_t* ext, double h,
+                            int64_t* rowptr, int32_t* col, double* valK, double* valM) {
+  const int64_t nx = ext[0], ny = ext[1], nz = (dim == 3) ? ext[2] : 1;
+  int64_t nnz = 0, row = 0;
+  for (int64_t z = 0; z < nz; ++z)
+    for (int64_t y = 0; y < ny; ++y)
+      for (int64_t x = 0; x < nx; ++x) {
+        const int64_t g = x + nx * (y + ny * z);
+        if (idx[g] < 0) continue;
+        rowptr[row] = nnz;
+        const int64_t p[3] = {x, y, z};
+        const int zlo = (dim == 3) ? -1 : 0, zhi = (dim == 3) ? 1 : 0;
+        for (int oz = zlo; oz <= zhi; ++oz)
+          for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+              const int64_t q[3] = {x + ox, y + oy, z + oz};
+              if (q[0] < 0 || q[0] >= nx || q[1] < 0 || q[1] >= ny || q[2] < 0 || q[2] >= nz) continue;
+              const int32_t c = idx[q[0] + nx * (q[1] + ny * q[2])];
+              if (c < 0) continue;
+              /* cells (lower corner s) that contain both p and q: per axis
+               * s_d in [max(p_d, q_d) - 1, min(p_d, q_d)] */
+              double K = 0.0, M = 0.0;
+              int64_t lo[3], hi[3];
+              for (int d = 0; d < 3; ++d) {
+                const int64_t mx = p[d] > q[d] ? p[d] : q[d], mn = p[d] < q[d] ? p[d] : q[d];
+                lo[d] = mx - 1;
+                hi[d] = mn;
+              }
+              if (dim == 2) { lo[2] = hi[2] = 0; }
+              for (int64_t sz = lo[2]; sz <= hi[2]; ++sz)
+                for (int64_t sy = lo[1]; sy <= hi[1]; ++sy)
+                  for (int64_t sx = lo[0]; sx <= hi[0]; ++sx) {
+                    const int64_t s[3] = {sx, sy, sz};
+                    int a[3], b[3];
+                    for (int d = 0; d < 3; ++d) {
+                      a[d] = (int)(p[d] - s[d]);
+                      b[d] = (int)(q[d] - s[d]);
+                    }
+                    double kk, mm;
+                    cell_integrals(dim, a, b, h, &kk, &mm);
+                    K += kk;
+                    M += mm;
+                  }
+              col[nnz] = c;
+              valK[nnz] = K;
+              valM[nnz] = M;
+              ++nnz;
+            }
+        ++row;
+      }
+  rowptr[row] = nnz;
+  return nnz;
+}
+
+/* Dense Cholesky M = L L^T (lower triangle of M read, L written to the
+ * lower triangle of Lo, zeros above).  Column by column:
+ * l_jj = sqrt(m_jj - sum_k l_jk^2), l_ij = (m_ij - sum_k l_ik l_jk) / l_jj. */
+static int dense_cholesky(int64_t n, const double* M, int64_t ldm, double* Lo, int64_t ldl) {
+  for (int64_t j = 0; j < n; ++j) {
+    for (int64_t i = 0; i < j; ++i) Lo[i + j * ldl] = 0.0;
+    double s = M[j + j * ldm];
+    for (int64_t k = 0; k < j; ++k) s -= Lo[j + k * ldl] * Lo[j + k * ldl];
+    if (!(s > 0.0)) return ORACLE_EZEROPIVOT;
+    const double ljj = sqrt(s);
+    Lo[j + j * ldl] = ljj;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = j + 1; i < n; ++i) {
+      double t = M[i + j * ldm];
+      for (int64_t k = 0; k < j; ++k) t -= Lo[i + k * ldl] * Lo[j + k * ldl];
+      Lo[i + j * ldl] = t / ljj;
+    }
+  }
+  return ORACLE_OK;
+}
+
+/* Generalised eigendecomposition K Phi = M Phi diag(theta), Phi^T M Phi = I,
+ * theta ascending (K symmetric, M symmetric positive definite, both dense
+ * with full storage).  Reduction to the standard problem: M = L L^T,
+ * C = L^-1 K L^-T, C = Z diag(theta) Z^T (oracle_eig_full), Phi = L^-T Z. */
+int oracle_eig_pencil(int64_t n, const double* K, int64_t ldk, const double* M, int64_t ldm,
+                      double* theta, double* Phi, int64_t ldp) {
+  if (n < 1 || ldk < n || ldm < n || ldp < n) return ORACLE_EINVAL;
+  double* L = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+  double* C = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+  if (!L || !C) { free(L); free(C); return ORACLE_ENOMEM; }
+  int rc = dense_cholesky(n, M, ldm, L, n);
+  if (rc == ORACLE_OK) {
+    /* Y = L^-1 K (forward substitution on every column of K) */
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < n; ++c) {
+      double* y = &C[c * n];
+      for (int64_t i = 0; i < n; ++i) {
+        double t = K[i + c * ldk];
+        for (int64_t k = 0; k < i; ++k) t -= L[i + k * n] * y[k];
+        y[i] = t / L[i + i * n];
+      }
+    }
+    /* C = Y L^-T = (L^-1 Y^T)^T: forward substitution on every row of Y */
+    double* T = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    if (!T) rc = ORACLE_ENOMEM;
+    if (rc == ORACLE_OK) {
+#pragma omp parallel for schedule(static)
+      for (int64_t r = 0; r < n; ++r) {
+        double* t = &T[r * n];  /* column r of T = row r of Y L^-T */
+        for (int64_t i = 0; i < n; ++i) {
+          double s = C[r + i * n];
+          for (int64_t k = 0; k < i; ++k) s -= L[i + k * n] * t[k];
+          t[i] = s / L[i + i * n];
+        }
+      }
+      /* C(r, i) = T(i, r), symmetrised (C is symmetric up to rounding) */
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t r = 0; r < n; ++r) C[r + i * n] = 0.5 * (T[i + r * n] + T[r + i * n]);
+      free(T);
+      rc = oracle_eig_full(n, C, n, theta, Phi, ldp);
+    }
+    if (rc == ORACLE_OK) {
+      /* Phi = L^-T Z: back substitution on every column */
+#pragma omp parallel for schedule(static)
+      for (int64_t c = 0; c < n; ++c) {
+        double* z = &Phi[c * ldp];
+        for (int64_t i = n - 1; i >= 0; --i) {
+          double t = z[i];
+          for (int64_t k = i + 1; k < n; ++k) t -= L[k + i * n] * z[k];
+          z[i] = t / L[i + i * n];
+        }
+      }
+    }
+  }
+  free(L);
+  free(C);
+  return rc;
+}
+
+/* Number of generalised eigenvalues below sigma: the negative pivots of the
+ * LDL^T factorisation of K - sigma M (Sylvester's law of inertia for the
+ * congruence L^-1 (K - sigma M) L^-T = C - sigma I).  K and M share the CSR
+ * pattern. */
+int64_t oracle_count_below_pencil(int64_t n, const int64_t* rowptr, const int32_t* col,
+                                  const double* valK, const double* valM, double sigma) {
+  const int64_t nnz = rowptr[n];
+  double* v = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  if (!v) return ORACLE_ENOMEM;
+  for (int64_t p = 0; p < nnz; ++p) v[p] = valK[p] - sigma * valM[p];
+  const int64_t r = oracle_count_below(n, rowptr, col, v, 0.0);
+  free(v);
+  return r;
+}
+
+/* Spectral apply of the generalised problem, the sum v after eq.
+ * (discrete_laplace) with the M-inner product: <f, phi_k> = phi_k^T M f for
+ * the nodal vector f, so W = Phi^T (M F) and u_j = Phi (theta^{-alpha_j/2} .*
+ * W(:, f_j)).  M in CSR. */
+int oracle_frac_apply_mass(int64_t n, const double* Phi, int64_t ldp, const double* theta,
+                           const int64_t* rowptr, const int32_t* col, const double* valM,
+                           const double* F, int64_t ldf, int64_t m, const int32_t* pair_f,
+                           const double* pair_alpha, int64_t k, double* U, int64_t ldu) {
+  if (n < 0 || m < 0 || k < 0 || ldp < n || ldf < n || ldu < n) return ORACLE_EINVAL;
+  for (int64_t j = 0; j < k; ++j)
+    if (pair_f[j] < 0 || pair_f[j] >= m) return ORACLE_EINVAL;
+  if (n == 0 || k == 0) return ORACLE_OK;
+  double* B = (double*)malloc(sizeof(double) * (size_t)n * (size_t)(m ? m : 1));
+  if (!B) return ORACLE_ENOMEM;
+  for (int64_t c = 0; c < m; ++c) oracle_spmv(n, rowptr, col, valM, &F[c * ldf], &B[c * n]);
+  const int rc = oracle_frac_apply(n, Phi, ldp, theta, B, n, m, pair_f, pair_alpha, k, U, ldu);
+  free(B);
+  return rc;
 }

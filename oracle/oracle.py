@@ -68,6 +68,15 @@ def _load():
             lib.oracle_frac_diffusion.restype = ctypes.c_int
             lib.oracle_frac_diffusion.argtypes = [_i64, _p, _i64, _p, _p, _i64, _i64, _p, _p, _p, _dbl,
                                                   _i64, _p, _i64]
+            lib.oracle_assemble_fem.restype = _i64
+            lib.oracle_assemble_fem.argtypes = [_p, ctypes.c_int, _p, _dbl, _p, _p, _p, _p]
+            lib.oracle_eig_pencil.restype = ctypes.c_int
+            lib.oracle_eig_pencil.argtypes = [_i64, _p, _i64, _p, _i64, _p, _p, _i64]
+            lib.oracle_count_below_pencil.restype = _i64
+            lib.oracle_count_below_pencil.argtypes = [_i64, _p, _p, _p, _p, _dbl]
+            lib.oracle_frac_apply_mass.restype = ctypes.c_int
+            lib.oracle_frac_apply_mass.argtypes = [_i64, _p, _i64, _p, _p, _p, _p, _p, _i64, _i64, _p, _p, _i64,
+                                                   _p, _i64]
             _lib = lib
     return _lib
 
@@ -242,6 +251,71 @@ def frac_diffusion(V: np.ndarray, lam: np.ndarray, U0: np.ndarray, pair_f, pair_
     return U
 
 
+def assemble_fem(mask: np.ndarray, h: float):
+    """Returns (idx, K, M): the stiffness and mass matrices of bilinear (2-D) /
+    trilinear (3-D) elements on the grid cells, Dirichlet zero outside the
+    mask (Sec. II eq. discrete_laplace, K_ij = <grad e_i, grad e_j>,
+    M_ij = <e_i, e_j>), as two CSR matrices with the same pattern."""
+    lib = _load()
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    dim = mask.ndim
+    ext = np.array(list(reversed(mask.shape)) + [1] * (3 - dim), dtype=np.int64)
+    idx = np.empty(mask.size, np.int32)
+    n = lib.oracle_number_dofs(_ptr(mask), mask.size, _ptr(idx))
+    rowptr = np.empty(n + 1, np.int64)
+    cap = max(1, 3 ** dim * n)
+    col = np.empty(cap, np.int32)
+    vk = np.empty(cap, np.float64)
+    vm = np.empty(cap, np.float64)
+    nnz = lib.oracle_assemble_fem(_ptr(idx), dim, _ptr(ext), float(h), _ptr(rowptr), _ptr(col), _ptr(vk), _ptr(vm))
+    col = col[:nnz].copy()
+    return idx, CSR(n, rowptr, col, vk[:nnz].copy()), CSR(n, rowptr.copy(), col.copy(), vm[:nnz].copy())
+
+
+def eig_pencil(K: np.ndarray, M: np.ndarray):
+    """K Phi = M Phi diag(theta), Phi^T M Phi = I, theta ascending (Cholesky
+    reduction of the generalised problem of Sec. II eq. discrete_laplace)."""
+    n = K.shape[0]
+    K = np.asfortranarray(K, dtype=np.float64)
+    M = np.asfortranarray(M, dtype=np.float64)
+    theta = np.empty(n)
+    Phi = np.empty((n, n), order="F")
+    rc = _load().oracle_eig_pencil(n, _ptr(K), n, _ptr(M), n, _ptr(theta), _ptr(Phi), n)
+    if rc != 0:
+        raise RuntimeError(f"oracle_eig_pencil failed ({rc})")
+    return theta, Phi
+
+
+def count_below_pencil(K: CSR, M: CSR, sigma: float) -> int:
+    """#{theta_i < sigma}: negative pivots of LDL^T(K - sigma M)."""
+    if not (np.array_equal(K.rowptr, M.rowptr) and np.array_equal(K.col, M.col)):
+        raise ValueError("K and M must share the CSR pattern")
+    c = _load().oracle_count_below_pencil(K.n, _ptr(K.rowptr), _ptr(K.col), _ptr(K.val), _ptr(M.val),
+                                          float(sigma))
+    if c < 0:
+        raise RuntimeError(f"oracle_count_below_pencil failed ({c})")
+    return int(c)
+
+
+def frac_apply_mass(Phi: np.ndarray, theta: np.ndarray, M: CSR, F: np.ndarray, pair_f, pair_alpha) -> np.ndarray:
+    """u_j = Phi diag(theta^{-alpha_j/2}) Phi^T M F[:, pair_f[j]]: the apply
+    of the generalised problem with the M-inner product."""
+    Phi = np.asfortranarray(Phi, dtype=np.float64)
+    n = Phi.shape[0]
+    F = np.asfortranarray(F.reshape(n, -1), dtype=np.float64)
+    m = F.shape[1]
+    pf = np.ascontiguousarray(pair_f, np.int32)
+    pa = np.ascontiguousarray(pair_alpha, np.float64)
+    k = pf.shape[0]
+    theta = np.ascontiguousarray(theta, np.float64)
+    U = np.empty((n, k), order="F")
+    rc = _load().oracle_frac_apply_mass(n, _ptr(Phi), n, _ptr(theta), _ptr(M.rowptr), _ptr(M.col), _ptr(M.val),
+                                        _ptr(F), n, m, _ptr(pf), _ptr(pa), k, _ptr(U), n)
+    if rc != 0:
+        raise RuntimeError(f"oracle_frac_apply_mass failed ({rc})")
+    return U
+
+
 def solve(mask: np.ndarray, h: float, F: np.ndarray, pair_f, pair_alpha):
     """Whole path on the CPU: assemble, decompose, apply.  Returns (lam, V, U)."""
     _, A = assemble(mask, h)
@@ -251,4 +325,5 @@ def solve(mask: np.ndarray, h: float, F: np.ndarray, pair_f, pair_alpha):
 
 
 __all__ = ["build", "CSR", "num_threads", "assemble", "spmv", "tridiagonalize", "tridiag_eig",
-           "eig_full", "eig_jacobi", "count_below", "band_solve", "frac_apply", "frac_diffusion", "solve"]
+           "eig_full", "eig_jacobi", "count_below", "band_solve", "frac_apply", "frac_diffusion", "assemble_fem",
+           "eig_pencil", "count_below_pencil", "frac_apply_mass", "solve"]

@@ -35,6 +35,17 @@ int oracle_frac_diffusion(int64_t n, const double* V, int64_t ldv, const double*
                           const double* pair_alpha, const double* pair_t, double mu, int64_t k,
                           double* U, int64_t ldu);
 
+int64_t oracle_assemble_fem(const int32_t* idx, int dim, const int64_t* ext, double h, int64_t* rowptr,
+                            int32_t* col, double* valK, double* valM);
+int oracle_eig_pencil(int64_t n, const double* K, int64_t ldk, const double* M, int64_t ldm,
+                      double* theta, double* Phi, int64_t ldp);
+int64_t oracle_count_below_pencil(int64_t n, const int64_t* rowptr, const int32_t* col,
+                                  const double* valK, const double* valM, double sigma);
+int oracle_frac_apply_mass(int64_t n, const double* Phi, int64_t ldp, const double* theta,
+                           const int64_t* rowptr, const int32_t* col, const double* valM,
+                           const double* F, int64_t ldf, int64_t m, const int32_t* pair_f,
+                           const double* pair_alpha, int64_t k, double* U, int64_t ldu);
+
 static int failures = 0;
 #define CHECK(cond)                                                   \
   do {                                                                \
@@ -67,7 +78,55 @@ static void dense_from_csr(int64_t n, const int64_t* rowptr, const int32_t* col,
     for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) A[i + (int64_t)col[p] * n] = val[p];
 }
 
+/* The finite-element generalised problem on the same mask. */
+static void run_fem(const uint8_t* mask, int dim, const int64_t ext[3], double h) {
+  const int64_t ngrid = ext[0] * ext[1] * ext[2];
+  int32_t* idx = malloc(sizeof(int32_t) * (size_t)ngrid);
+  const int64_t n = oracle_number_dofs(mask, ngrid, idx);
+  const int64_t cap = (dim == 3 ? 27 : 9) * (n > 0 ? n : 1);
+  int64_t* rowptr = malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int32_t* col = malloc(sizeof(int32_t) * (size_t)cap);
+  double* vk = malloc(sizeof(double) * (size_t)cap);
+  double* vm = malloc(sizeof(double) * (size_t)cap);
+  const int64_t nnz = oracle_assemble_fem(idx, dim, ext, h, rowptr, col, vk, vm);
+  CHECK(nnz >= n && nnz <= cap);
+  if (n > 0) {
+    double* K = malloc(sizeof(double) * (size_t)(n * n));
+    double* M = malloc(sizeof(double) * (size_t)(n * n));
+    double* Phi = malloc(sizeof(double) * (size_t)(n * n));
+    double* th = malloc(sizeof(double) * (size_t)n);
+    dense_from_csr(n, rowptr, col, vk, K);
+    dense_from_csr(n, rowptr, col, vm, M);
+    CHECK(oracle_eig_pencil(n, K, n, M, n, th, Phi, n) == 0);
+    CHECK(oracle_count_below_pencil(n, rowptr, col, vk, vm, 0.5 * th[0]) == 0);
+    CHECK(oracle_count_below_pencil(n, rowptr, col, vk, vm, 2.0 * th[n - 1]) == n);
+    double* F = malloc(sizeof(double) * (size_t)(2 * n));
+    double* U = malloc(sizeof(double) * (size_t)(3 * n));
+    for (int64_t i = 0; i < 2 * n; ++i) F[i] = cos(0.7 * (double)i);
+    int32_t pf[3] = {1, 0, 1};
+    double pa[3] = {1.0, 0.0, 2.0};
+    CHECK(oracle_frac_apply_mass(n, Phi, n, th, rowptr, col, vm, F, n, 2, pf, pa, 3, U, n) == 0);
+    int32_t bad[1] = {-1};
+    CHECK(oracle_frac_apply_mass(n, Phi, n, th, rowptr, col, vm, F, n, 2, bad, pa, 1, U, n) != 0);
+    /* an indefinite "mass" matrix has no Cholesky factor */
+    for (int64_t i = 0; i < n * n; ++i) M[i] = -M[i];
+    CHECK(oracle_eig_pencil(n, K, n, M, n, th, Phi, n) != 0);
+    free(K);
+    free(M);
+    free(Phi);
+    free(th);
+    free(F);
+    free(U);
+  }
+  free(idx);
+  free(rowptr);
+  free(col);
+  free(vk);
+  free(vm);
+}
+
 static void run_problem(const uint8_t* mask, int dim, const int64_t ext[3], double h) {
+  run_fem(mask, dim, ext, h);
   int64_t* rowptr;
   int32_t* col;
   double* val;
