@@ -8,10 +8,11 @@
 // different problems can be resident at the same time) with its own stream,
 // workspace, status word and host thread issuing its launches.  Problems are
 // dealt largest first to the least-loaded worker (cost ~ n^3); each runs the
-// FP64 route (band width 32: half the bulge-chasing step latency of 64 for
-// these sizes) and then the spectral apply of its pairs.  The caller's stream
-// waits for every worker; device errors of the workers are merged into the
-// context's status word.
+// FP64 route, or the mixed route (FP32 stages + refinement) when the problem
+// carries its CSR, with band width 32 (half the bulge-chasing step latency of
+// 64 for these sizes), and then the spectral apply of its pairs.  The
+// caller's stream waits for every worker; device errors of the workers are
+// merged into the context's status word.
 #include <algorithm>
 #include <thread>
 #include <vector>
@@ -132,7 +133,13 @@ extern "C" int fraclap_solve_batched(fraclap_ctx* ctx, const fraclap_problem* pr
   {
     std::vector<std::thread> threads;
     threads.reserve(W);
-    for (int w = 1; w < W; ++w) threads.emplace_back(run, w);
+    for (int w = 1; w < W; ++w) {
+      try {
+        threads.emplace_back(run, w);
+      } catch (...) {  // no thread to be had: this worker's problems run here
+        run(w);
+      }
+    }
     run(0);
     for (auto& t : threads) t.join();
   }
