@@ -348,6 +348,17 @@ int fraclap_set_refine_tau(fraclap_ctx* ctx, double tau);
  * (kept to cross-check the first). */
 int fraclap_set_tensor_route(fraclap_ctx* ctx, int route);
 
+/* Failure detection of the bounded device waits, without a fault: one CTA
+ * waits, through the library's own primitives, on an event that nothing
+ * produces -- which = 0: the grid barrier of the cooperative kernels (one CTA
+ * arriving where two are expected); which = 1: an mbarrier of the
+ * tensor-core kernels with no arrival.  The wait gives up after the
+ * context's limit (fraclap_opts.wait_timeout_s), the kernel records
+ * FRACLAP_ERR_TIMEOUT in the device status and returns, so the next
+ * fraclap_sync reports -4 and the context stays usable.  Asynchronous on
+ * `stream`; returns FRACLAP_ERR_INVALID_ARG for any other `which`. */
+int fraclap_wait_selftest(fraclap_ctx* ctx, int which, fraclap_stream_t stream);
+
 /* C = alpha op(A) op(B) + beta C with FP64-accurate products formed on the
  * BF16 tensor cores by Ozaki's error-free splitting into `slices` 8-bit slices
  * per row/column (7 slices: full FP64 accuracy; fewer: about 8*slices bits

@@ -41,6 +41,7 @@ SIGNATURES = {
     "fraclap_refine_stats": (_i32, [_p, _p, _i32]),
     "fraclap_set_tensor_route": (_i32, [_p, _i32]),
     "fraclap_set_refine_tau": (_i32, [_p, _dbl]),
+    "fraclap_wait_selftest": (_i32, [_p, _i32, _p]),
     "fraclap_dgemm_ozaki_workspace_bytes": (_sz, [_i64, _i64, _i64, _i32]),
     "fraclap_dgemm_ozaki": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64,
                                    _i32, _p, _sz, _p]),
@@ -159,6 +160,11 @@ class Context:
     def set_tensor_route(self, route: int):
         """1: tcgen05 + TMA slice products (default); 0: mma.sync."""
         self.check(self.lib.fraclap_set_tensor_route(self.handle, int(route)))
+
+    def wait_selftest(self, which: int, stream=None):
+        """Drives one bounded device wait (0: grid barrier, 1: mbarrier) into
+        its time limit; the next sync raises FraclapError(-4)."""
+        self.check(self.lib.fraclap_wait_selftest(self.handle, int(which), ctypes.c_void_p(_stream(stream))))
 
     def launch_count(self) -> int:
         return int(self.lib.fraclap_launch_count(self.handle))
