@@ -222,7 +222,8 @@ __global__ void unsafe_spans(const double* S, int64_t lds, const double* R, int6
     const double num = fmax(fabs(s + lt[j] * r), fabs(s + lt[i] * r));
     const int a = min(rank[i], rank[j]), b = max(rank[i], rank[j]);
     const bool inner = big && big[a] >= 0 && big[a] == big[b];
-    if ((!inner && g <= dl) || num > tau * g) atomicMax(reach + a, b);
+    // equal estimates always join (the first-order formula would divide by zero)
+    if ((!inner && g <= dl) || num > tau * g || g == 0.0) atomicMax(reach + a, b);
   }
 }
 
