@@ -9,6 +9,7 @@ Pinned functions (see ``tests/test_oracle_*.py``): assembly, Householder +
 implicit-QR eigensolver, Jacobi, inertia counting, banded direct solve,
 spectral apply, fractional diffusion, and the finite-element generalised
 problem (assembly of K and M, Cholesky-reduced eigensolver, inertia of
-K - sigma M, apply in the M-inner product).  No function here is unpinned.
+K - sigma M, apply in the M-inner product), Sturm counts and bisection on
+the tridiagonal form, and the greedy spectrum partitioner of Sec. III-D.  No function here is unpinned.
 """
 from .oracle import *  # noqa: F401,F403

@@ -20,7 +20,8 @@
  *     apply takes the M-inner product.
  *   - Sec. III-D-2 (exact eigenvalue counting): the number of eigenvalues
  *     below sigma equals the number of negative pivots of the LDL^T
- *     factorisation of A - sigma I (Sylvester's law of inertia).
+ *     factorisation of A - sigma I (Sylvester's law of inertia); the same
+ *     count on the tridiagonal T (Sturm sequence) and bisection on it.
  *
  * The eigendecomposition is the plain textbook route, written from the
  * mathematics: Householder reduction to tridiagonal form with the orthogonal
@@ -780,4 +781,56 @@ int oracle_frac_apply_mass(int64_t n, const double* Phi, int64_t ldp, const doub
   const int rc = oracle_frac_apply(n, Phi, ldp, theta, B, n, m, pair_f, pair_alpha, k, U, ldu);
   free(B);
   return rc;
+}
+
+/* ======================================================================== */
+/* Inertia of a symmetric tridiagonal T (d[0..n-1], off-diagonal e[0..n-2]) */
+/* and bisection (Sec. III-D-2 applied to T = Q^T A Q, which is congruent   */
+/* to A, so the counts are those of A).                                     */
+/* ======================================================================== */
+
+/* Number of eigenvalues of T strictly below sigma: the negative pivots of
+ * T - sigma I = L D L^T, q_0 = d_0 - sigma, q_i = d_i - sigma - e_{i-1}^2 / q_{i-1}.
+ * An exact zero pivot is replaced by a tiny negative number (sigma moved up by
+ * an amount far below the resolution of any eigenvalue). */
+int64_t oracle_sturm_count(int64_t n, const double* d, const double* e, double sigma) {
+  if (n < 1) return ORACLE_EINVAL;
+  int64_t neg = 0;
+  double q = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    q = (i == 0) ? d[0] - sigma : d[i] - sigma - e[i - 1] * e[i - 1] / q;
+    if (q == 0.0) q = -1e-300;
+    neg += (q < 0.0);
+  }
+  return neg;
+}
+
+/* Eigenvalues number k0..k1 (0-based, ascending) of T by bisection on the
+ * Sturm count, starting from the Gershgorin interval; each stops when the
+ * interval holds no representable midpoint or is within 2 eps of its
+ * magnitude.  lam receives k1 - k0 + 1 values. */
+int oracle_bisect(int64_t n, const double* d, const double* e, int64_t k0, int64_t k1, double* lam) {
+  if (n < 1 || k0 < 0 || k1 >= n || k0 > k1) return ORACLE_EINVAL;
+  double glo = d[0], ghi = d[0];
+  for (int64_t i = 0; i < n; ++i) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+    if (d[i] - r < glo) glo = d[i] - r;
+    if (d[i] + r > ghi) ghi = d[i] + r;
+  }
+  const double pad = 2.220446049250313e-16 * (fabs(glo) + fabs(ghi)) + 1e-300;
+  glo -= pad;
+  ghi += pad;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = k0; k <= k1; ++k) {
+    double lo = glo, hi = ghi;  /* count(lo) <= k < count(hi) */
+    for (int it = 0; it < 4096; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (hi - lo <= 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi))) break;
+      if (oracle_sturm_count(n, d, e, mid) > k) hi = mid;
+      else lo = mid;
+    }
+    lam[k - k0] = 0.5 * (lo + hi);
+  }
+  return ORACLE_OK;
 }

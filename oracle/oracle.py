@@ -77,6 +77,10 @@ def _load():
             lib.oracle_frac_apply_mass.restype = ctypes.c_int
             lib.oracle_frac_apply_mass.argtypes = [_i64, _p, _i64, _p, _p, _p, _p, _p, _i64, _i64, _p, _p, _i64,
                                                    _p, _i64]
+            lib.oracle_sturm_count.restype = _i64
+            lib.oracle_sturm_count.argtypes = [_i64, _p, _p, _dbl]
+            lib.oracle_bisect.restype = ctypes.c_int
+            lib.oracle_bisect.argtypes = [_i64, _p, _p, _i64, _i64, _p]
             _lib = lib
     return _lib
 
@@ -316,6 +320,110 @@ def frac_apply_mass(Phi: np.ndarray, theta: np.ndarray, M: CSR, F: np.ndarray, p
     return U
 
 
+def sturm_count(d: np.ndarray, e: np.ndarray, sigma: float) -> int:
+    """#{eigenvalues of the tridiagonal (d, e) below sigma}: negative pivots of
+    LDL^T(T - sigma I) (Sylvester's law of inertia, Sec. III-D-2)."""
+    d = np.ascontiguousarray(d, np.float64)
+    ee = np.zeros(max(d.shape[0], 1))
+    ee[: d.shape[0] - 1] = e[: d.shape[0] - 1]
+    c = _load().oracle_sturm_count(d.shape[0], _ptr(d), _ptr(ee), float(sigma))
+    if c < 0:
+        raise RuntimeError(f"oracle_sturm_count failed ({c})")
+    return int(c)
+
+
+def bisect(d: np.ndarray, e: np.ndarray, k0: int, k1: int) -> np.ndarray:
+    """Eigenvalues k0..k1 (0-based, ascending) of the tridiagonal (d, e) by
+    bisection on the Sturm count."""
+    d = np.ascontiguousarray(d, np.float64)
+    n = d.shape[0]
+    ee = np.zeros(max(n, 1))
+    ee[: n - 1] = e[: n - 1]
+    lam = np.empty(max(k1 - k0 + 1, 0))
+    rc = _load().oracle_bisect(n, _ptr(d), _ptr(ee), int(k0), int(k1), _ptr(lam))
+    if rc != 0:
+        raise RuntimeError(f"oracle_bisect failed ({rc})")
+    return lam
+
+
+def _split_for_equal_loads(points, counts, n, P):
+    """New split points for P equal loads under the piecewise-constant density
+    that the counts at `points` describe: the cumulative count is linear
+    between known points, and split j sits where it reaches j n / P."""
+    out = []
+    for j in range(1, P):
+        target = j * n / P
+        i = int(np.searchsorted(counts, target, side="left"))
+        i = min(max(i, 1), len(points) - 1)
+        c0, c1 = counts[i - 1], counts[i]
+        x0, x1 = points[i - 1], points[i]
+        out.append(x0 if c1 == c0 else x0 + (target - c0) / (c1 - c0) * (x1 - x0))
+    return np.array(out)
+
+
+def greedy_partition(count_below_fn, n: int, rho: float, P: int, n_a: int = 7, n_b: int = 0,
+                     n_c: int = 10, imbalance: float = 0.25):
+    """Spectrum slicing of Sec. III-D ("greedy partitioning"): split [0, rho]
+    into P subintervals holding about n / P eigenvalues each.
+
+    count_below_fn(sigma) is the exact count #{lambda < sigma} (one
+    factorisation per call).  Start from P equally long subintervals; then
+    n_a times: count at every split, read the counts as a piecewise-constant
+    density of states, and move the splits to where that density gives equal
+    loads; the best partition seen (smallest largest load) is kept.  Then up
+    to n_b local passes: every pair of neighbouring subintervals whose loads
+    differ by more than `imbalance` x n / P moves its shared split by a
+    binary search of n_c counts towards an even pair (first the pairs
+    starting at even positions, then the odd ones).
+    Returns (splits, loads, history): splits has P - 1 increasing points,
+    loads the P exact counts, history the largest load after each step."""
+    ideal = n / P
+    splits = rho * np.arange(1, P) / P
+
+    def loads_of(s):
+        c = np.array([count_below_fn(x) for x in s], dtype=np.int64)
+        return c, np.diff(np.concatenate([[0], c, [n]]))
+
+    counts, loads = loads_of(splits)
+    best = (loads.max(), splits.copy(), loads.copy())
+    history = [int(loads.max())]
+    for _ in range(n_a):
+        pts = np.concatenate([[0.0], splits, [rho]])
+        cum = np.concatenate([[0], counts, [n]]).astype(np.float64)
+        splits = _split_for_equal_loads(pts, cum, n, P)
+        counts, loads = loads_of(splits)
+        history.append(int(loads.max()))
+        if loads.max() < best[0]:
+            best = (loads.max(), splits.copy(), loads.copy())
+    splits, loads = best[1].copy(), best[2].copy()
+    for _ in range(n_b):
+        changed = False
+        for parity in (0, 1):
+            for a in range(parity, P - 1, 2):
+                if abs(int(loads[a]) - int(loads[a + 1])) <= imbalance * ideal:
+                    continue
+                lo = splits[a - 1] if a > 0 else 0.0
+                hi = splits[a + 1] if a + 1 < P - 1 else rho
+                left = 0 if a == 0 else count_below_fn(lo)
+                want = left + (loads[a] + loads[a + 1]) / 2.0
+                x0, x1 = lo, hi
+                for _ in range(n_c):
+                    mid = 0.5 * (x0 + x1)
+                    if count_below_fn(mid) < want:
+                        x0 = mid
+                    else:
+                        x1 = mid
+                splits[a] = 0.5 * (x0 + x1)
+                c = count_below_fn(splits[a])
+                tot = loads[a] + loads[a + 1]
+                loads[a], loads[a + 1] = c - left, tot - (c - left)
+                changed = True
+        history.append(int(loads.max()))
+        if not changed:
+            break
+    return splits, loads, history
+
+
 def solve(mask: np.ndarray, h: float, F: np.ndarray, pair_f, pair_alpha):
     """Whole path on the CPU: assemble, decompose, apply.  Returns (lam, V, U)."""
     _, A = assemble(mask, h)
@@ -326,4 +434,4 @@ def solve(mask: np.ndarray, h: float, F: np.ndarray, pair_f, pair_alpha):
 
 __all__ = ["build", "CSR", "num_threads", "assemble", "spmv", "tridiagonalize", "tridiag_eig",
            "eig_full", "eig_jacobi", "count_below", "band_solve", "frac_apply", "frac_diffusion", "assemble_fem",
-           "eig_pencil", "count_below_pencil", "frac_apply_mass", "solve"]
+           "eig_pencil", "count_below_pencil", "frac_apply_mass", "sturm_count", "bisect", "greedy_partition", "solve"]

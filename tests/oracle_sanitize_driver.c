@@ -46,6 +46,9 @@ int oracle_frac_apply_mass(int64_t n, const double* Phi, int64_t ldp, const doub
                            const double* F, int64_t ldf, int64_t m, const int32_t* pair_f,
                            const double* pair_alpha, int64_t k, double* U, int64_t ldu);
 
+int64_t oracle_sturm_count(int64_t n, const double* d, const double* e, double sigma);
+int oracle_bisect(int64_t n, const double* d, const double* e, int64_t k0, int64_t k1, double* lam);
+
 static int failures = 0;
 #define CHECK(cond)                                                   \
   do {                                                                \
@@ -155,6 +158,14 @@ static void run_problem(const uint8_t* mask, int dim, const int64_t ext[3], doub
   double* W = malloc(sizeof(double) * (size_t)(n * n));
   memcpy(W, A, sizeof(double) * (size_t)(n * n));
   CHECK(oracle_tridiagonalize(n, W, n, d, e, V, n) == 0);
+  {
+    double* tl = malloc(sizeof(double) * (size_t)n);
+    CHECK(oracle_bisect(n, d, e, 0, n - 1, tl) == 0);
+    CHECK(oracle_sturm_count(n, d, e, tl[0] - 1.0) == 0);
+    CHECK(oracle_sturm_count(n, d, e, tl[n - 1] + 1.0) == n);
+    CHECK(oracle_bisect(n, d, e, 0, n, tl) != 0);
+    free(tl);
+  }
   CHECK(oracle_tridiag_eig(n, d, e, V, n, n, 30 * n + 30) == 0);
   CHECK(oracle_eig_full(n, A, n, lam, V, n) == 0);
   CHECK(oracle_eig_jacobi(n, A, n, lam2, V2, n, 100) == 0);
