@@ -44,7 +44,8 @@ enum {
   FRACLAP_ERR_TIMEOUT = -4,       /* a bounded device-side wait expired */
   FRACLAP_ERR_ALLOC = -5,         /* a context-owned workspace allocation failed */
   FRACLAP_ERR_CUDA = -6,          /* a CUDA runtime call failed (see fraclap_last_error) */
-  FRACLAP_ERR_UNSUPPORTED = -7    /* a size or option outside what this build handles */
+  FRACLAP_ERR_UNSUPPORTED = -7,   /* a size or option outside what this build handles */
+  FRACLAP_ERR_IO = -8             /* a file could not be written or read, or is not a valid checkpoint */
 };
 
 /* Options; zero fields take the defaults in brackets. */
@@ -221,6 +222,39 @@ int frac_apply_noalloc(const double* V_dev, int64_t ldv, const double* lambda_de
                        const double* F_dev, int64_t ldf, int64_t m, const int32_t* pair_f_dev,
                        const double* pair_alpha_dev, int64_t k, double* U_dev, int64_t ldu,
                        int32_t* status_dev, fraclap_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Checkpoint of a decomposition.  The method computes the eigenpairs once
+ * and reuses them for every forcing, order and time (Sec. II), so
+ * (n, lambda, V) can be kept in a file, tagged with the grid it belongs to.
+ * HOST buffers: these calls do file I/O only; the caller copies V to and from
+ * the device.  The file is little-endian whatever the host, ends with an
+ * FNV-1a-64 checksum of its contents, and is written to "<path>.partial" and
+ * renamed, so a failed save never leaves a truncated checkpoint at `path`.
+ *
+ * fraclap_mask_hash: FNV-1a-64 of (dim, ext, h, mask bytes read as 0/1);
+ *   mask_host uint8[ext0*ext1*(dim == 3 ? ext2 : 1)]; returns 0 for invalid
+ *   arguments, never 0 otherwise.
+ * fraclap_save_decomposition: lambda_host double[n], V_host double[ldv*n]
+ *   (ldv >= n; stored packed); dim 2 or 3 with ext and h describing the grid,
+ *   or dim 0 for none; mask_hash 0 = none.  FRACLAP_ERR_IO if the file cannot
+ *   be written.
+ * fraclap_load_decomposition: two calls.  With lambda_host == NULL it reads
+ *   and checks the header (every out pointer may be NULL) and returns n, the
+ *   grid and the stored mask hash; with lambda_host double[n] and V_host
+ *   double[ldv*n] (ldv >= n) it also reads the payload.  FRACLAP_ERR_IO for a
+ *   missing, truncated or corrupted file (bad magic, version, size or
+ *   checksum; the buffers' contents are then unspecified);
+ *   FRACLAP_ERR_INVALID_ARG if expect_mask_hash is nonzero and differs from
+ *   the stored hash (the file belongs to another domain).
+ * ---------------------------------------------------------------------- */
+uint64_t fraclap_mask_hash(const uint8_t* mask_host, int dim, const int64_t ext[3], double h);
+int fraclap_save_decomposition(const char* path, int64_t n, const double* lambda_host,
+                               const double* V_host, int64_t ldv, int dim, const int64_t ext[3],
+                               double h, uint64_t mask_hash);
+int fraclap_load_decomposition(const char* path, int64_t* n_out, int* dim_out, int64_t ext_out[3],
+                               double* h_out, uint64_t* mask_hash_out, double* lambda_host,
+                               double* V_host, int64_t ldv, uint64_t expect_mask_hash);
 
 /* ------------------------------------------------------------------------
  * Stage entry points (the steps eig_full chains), for stage-level checks.

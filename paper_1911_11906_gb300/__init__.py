@@ -26,4 +26,7 @@ from ._binding import (  # noqa: F401
     solve,
     solve_batched,
     default_context,
+    mask_hash,
+    save_decomposition,
+    load_decomposition,
 )

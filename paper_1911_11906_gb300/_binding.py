@@ -42,6 +42,9 @@ SIGNATURES = {
     "fraclap_set_tensor_route": (_i32, [_p, _i32]),
     "fraclap_set_refine_tau": (_i32, [_p, _dbl]),
     "fraclap_wait_selftest": (_i32, [_p, _i32, _p]),
+    "fraclap_mask_hash": (ctypes.c_uint64, [_p, _i32, _p, _dbl]),
+    "fraclap_save_decomposition": (_i32, [ctypes.c_char_p, _i64, _p, _p, _i64, _i32, _p, _dbl, ctypes.c_uint64]),
+    "fraclap_load_decomposition": (_i32, [ctypes.c_char_p, _p, _p, _p, _p, _p, _p, _p, _i64, ctypes.c_uint64]),
     "fraclap_dgemm_ozaki_workspace_bytes": (_sz, [_i64, _i64, _i64, _i32]),
     "fraclap_dgemm_ozaki": (_i32, [_p, _i32, _i32, _i64, _i64, _i64, _dbl, _p, _i64, _p, _i64, _dbl, _p, _i64,
                                    _i32, _p, _sz, _p]),
@@ -487,3 +490,73 @@ def solve(mask: torch.Tensor, h: float, F: torch.Tensor, pair_f, pair_alpha, ctx
     lam, V = eig_full(asm["A"], ctx=ctx)
     U = frac_apply(V, lam, F, pair_f, pair_alpha, ctx=ctx)
     return lam, V, U
+
+
+# ----------------------------------------------------------------------------
+# checkpoint of a decomposition (host-side file I/O in the library)
+# ----------------------------------------------------------------------------
+def _host_mask(mask):
+    m = mask.detach().cpu().numpy() if isinstance(mask, torch.Tensor) else np.asarray(mask)
+    m = np.ascontiguousarray(m, dtype=np.uint8)
+    if m.ndim not in (2, 3):
+        raise ValueError("mask must be 2-D [y, x] or 3-D [z, y, x]")
+    ext = np.array(list(reversed(m.shape)) + [1] * (3 - m.ndim), dtype=np.int64)
+    return m, ext
+
+
+def _check_io(lib, rc: int, what: str):
+    if rc != 0:
+        raise FraclapError(rc, f"{what}: {lib.fraclap_strerror(rc).decode()}")
+
+
+def mask_hash(mask, h: float) -> int:
+    """FNV-1a-64 of the grid (dimension, extents, h) and the mask, as stored
+    in a checkpoint."""
+    lib = load_library()
+    m, ext = _host_mask(mask)
+    return int(lib.fraclap_mask_hash(m.ctypes.data_as(ctypes.c_void_p), m.ndim,
+                                     ext.ctypes.data_as(ctypes.c_void_p), float(h)))
+
+
+def save_decomposition(path: str, lam, V, mask=None, h: float = 0.0) -> None:
+    """Writes (n, lambda, V) to `path` (V is copied to the host), tagged with
+    the grid of `mask` and h when given."""
+    lib = load_library()
+    lam_h = np.ascontiguousarray((lam.detach().cpu().numpy() if isinstance(lam, torch.Tensor) else lam), np.float64)
+    V_h = np.asfortranarray((V.detach().cpu().numpy() if isinstance(V, torch.Tensor) else V), np.float64)
+    n = lam_h.shape[0]
+    if V_h.shape != (n, n):
+        raise ValueError("V must be n x n")
+    if mask is not None:
+        m, ext = _host_mask(mask)
+        dim, mh = m.ndim, mask_hash(m, h)
+    else:
+        ext, dim, mh = np.zeros(3, np.int64), 0, 0
+    rc = lib.fraclap_save_decomposition(os.fsencode(path), n, lam_h.ctypes.data_as(ctypes.c_void_p),
+                                        V_h.ctypes.data_as(ctypes.c_void_p), max(n, 1), dim,
+                                        ext.ctypes.data_as(ctypes.c_void_p), float(h), mh)
+    _check_io(lib, rc, f"save_decomposition({path})")
+
+
+def load_decomposition(path: str, mask=None, h: float | None = None, device=None):
+    """Reads (lambda, V) from `path` onto `device` (default: the current CUDA
+    device if there is one, else the host); V is column-major.  With `mask`
+    and h given, the file must belong to that grid."""
+    lib = load_library()
+    expect = mask_hash(mask, h) if mask is not None else 0
+    n = ctypes.c_int64(0)
+    rc = lib.fraclap_load_decomposition(os.fsencode(path), ctypes.byref(n), None, None, None, None, None, None, 0,
+                                        expect)
+    _check_io(lib, rc, f"load_decomposition({path})")
+    nn = n.value
+    lam_h = np.empty(max(nn, 1))
+    V_h = np.empty((max(nn, 1), max(nn, 1)), order="F")
+    rc = lib.fraclap_load_decomposition(os.fsencode(path), None, None, None, None, None,
+                                        lam_h.ctypes.data_as(ctypes.c_void_p), V_h.ctypes.data_as(ctypes.c_void_p),
+                                        max(nn, 1), expect)
+    _check_io(lib, rc, f"load_decomposition({path})")
+    if device is None:
+        device = torch.device("cuda") if torch.cuda.is_available() else torch.device("cpu")
+    lam = torch.from_numpy(lam_h[:nn].copy()).to(device)
+    V = torch.from_numpy(np.ascontiguousarray(V_h[:nn, :nn].T)).to(device).t()
+    return lam, V

@@ -207,6 +207,7 @@ extern "C" const char* fraclap_strerror(int code) {
     case FRACLAP_ERR_ALLOC: return "workspace allocation failed";
     case FRACLAP_ERR_CUDA: return "CUDA runtime error";
     case FRACLAP_ERR_UNSUPPORTED: return "unsupported size or option";
+    case FRACLAP_ERR_IO: return "file I/O error or invalid checkpoint";
     default: return "unknown error";
   }
 }

@@ -57,7 +57,7 @@ def test_binding_table_matches_header():
 def test_error_strings(lib):
     lib.fraclap_strerror.restype = ctypes.c_char_p
     seen = set()
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         s = lib.fraclap_strerror(code)
         assert s and s not in seen
         seen.add(s)
