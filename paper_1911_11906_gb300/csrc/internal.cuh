@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 
@@ -91,16 +92,30 @@ enum Stage : int {
   kStageCount = 15
 };
 
-// Records CUDA events around a stage on `st` when profiling is on.
+// NVTX range names of the stages ("fraclap:" + the name the binding reports).
+inline const char* stage_range_name(int s) {
+  static const char* names[kStageCount] = {
+      "fraclap:assemble",      "fraclap:band_reduction", "fraclap:bulge_chasing",  "fraclap:tridiag_dc",
+      "fraclap:back_q2",       "fraclap:back_q1",        "fraclap:apply",          "fraclap:refine",
+      "fraclap:residual_gemm", "fraclap:refine_norms",   "fraclap:refine_update",  "fraclap:refine_sort",
+      "fraclap:refine_clusters", "fraclap:refine_big_clusters", "fraclap:slice_products"};
+  return (s >= 0 && s < kStageCount) ? names[s] : "fraclap";
+}
+
+// Marks a stage with an NVTX range (host timeline, always; free without a
+// tool attached) and, when profiling is on, records CUDA events around it
+// on `st`.
 struct StageTimer {
   fraclap_ctx* ctx;
   int stage;
   cudaStream_t st;
   cudaEvent_t e0 = nullptr;
   StageTimer(fraclap_ctx* c, int s, cudaStream_t stream) : ctx(c), stage(s), st(stream) {
+    nvtxRangePushA(stage_range_name(s));
     if (ctx->profiling && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, st);
   }
   ~StageTimer() {
+    nvtxRangePop();
     if (!e0) return;
     cudaEvent_t e1;
     if (cudaEventCreate(&e1) == cudaSuccess) {
@@ -118,15 +133,22 @@ struct StageSpan {
   cudaStream_t st;
   int stage = -1;
   cudaEvent_t e0 = nullptr;
+  bool range_open = false;
   StageSpan(fraclap_ctx* c, cudaStream_t s) : ctx(c), st(s) {}
   void start(int id) {
     stop();
+    nvtxRangePushA(stage_range_name(id));
+    range_open = true;
     if (!ctx->profiling) return;
     stage = id;
     if (cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, st);
     else e0 = nullptr;
   }
   void stop() {
+    if (range_open) {
+      nvtxRangePop();
+      range_open = false;
+    }
     if (!e0) return;
     cudaEvent_t e1;
     if (cudaEventCreate(&e1) == cudaSuccess) {
