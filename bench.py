@@ -135,6 +135,30 @@ def eig_flops(n: int) -> float:
 
 
 # ----------------------------------------------------------------------------
+# metrics log: one JSONL record per timed route of a bench line
+# ----------------------------------------------------------------------------
+def jsonl_records(line: dict) -> list:
+    """Per-route records {config, n, precision, steps, seconds, tflops,
+    frac_of_peak, err_*} of a bench line (the headline route carries the
+    kernel roofline as well)."""
+    out = []
+    cfg = line.get("config", {})
+    for route, r in (line.get("paths") or {}).items():
+        acc = r.get("accuracy", {})
+        rec = {"config": cfg.get("workload"), "n": cfg.get("n"), "precision": route, "steps": line.get("steps"),
+               "seconds": round(r["ms_per_step"] / 1e3, 6), "solves_per_s": r.get("solves_per_s"),
+               "eig_seconds": r.get("eig_s"), "tflops": r.get("eig_tflops_credited_fp64"),
+               "frac_of_peak": r.get("eig_frac_of_fp64_peak"),
+               "err_u_alpha2": acc.get("u_rel_l2_alpha2_vs_cg_max"),
+               "err_resid": acc.get("eig_residual_sampled_max"), "err_orth": acc.get("orth_sampled_max"),
+               "err_trace": acc.get("trace_rel_err"), "stage_ms": r.get("stage_ms")}
+        if route == (cfg.get("path") or route) and line.get("roofline"):
+            rec["roofline"] = line["roofline"]
+        out.append(rec)
+    return out
+
+
+# ----------------------------------------------------------------------------
 # replicas: every rank runs the whole workload on its own GPU (weak scaling)
 # ----------------------------------------------------------------------------
 def max_over_ranks(values, world: int, device=None) -> list:
@@ -362,6 +386,10 @@ def run_gpu(args, rank, world, local_rank):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     print(json.dumps(line), flush=True)
+    if args.jsonl:
+        with open(args.jsonl, "a") as fh:
+            for rec in jsonl_records(line):
+                fh.write(json.dumps(rec) + "\n")
 
 
 def _measured_peak(key):
@@ -676,6 +704,8 @@ def main():
     ap.add_argument("--product-only", type=int, default=0, metavar="N",
                     help="profiling aid: run only FP64-accurate slice products N x N x N (R = X^T X "
                          "shape), --steps times after --warmup, and print their CUDA-event times")
+    ap.add_argument("--jsonl", default="", metavar="PATH",
+                    help="also append one JSONL metrics record per timed route to PATH")
     ap.add_argument("--workload", default="ellipse128",
                     choices=["ellipse128", "batched256", "apply192", "diffusion192"],
                     help="ellipse128: the headline workload; batched256, apply192 and diffusion192: the "

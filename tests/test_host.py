@@ -214,3 +214,20 @@ def test_ncu_launch_list_summary(tmp_path):
     assert lines[1].split()[:3] == ["k2", "2", "0.006"] and lines[1].endswith("60.00%")
     assert lines[2].split()[:3] == ["k1<float,", "4>", "2"] and lines[2].endswith("40.00%")
     assert lines[-1].split()[:3] == ["TOTAL", "4", "0.010"]
+
+
+def test_bench_jsonl_records():
+    sys.path.insert(0, ROOT)
+    import bench
+    line = {"steps": 3, "config": {"workload": "w", "n": 10, "path": "mixed"},
+            "roofline": {"frac": 0.4},
+            "paths": {"fp64": {"ms_per_step": 2000.0, "solves_per_s": 64.0, "eig_s": 1.9,
+                               "eig_tflops_credited_fp64": 0.5, "eig_frac_of_fp64_peak": 0.4,
+                               "accuracy": {"orth_sampled_max": 1e-15}, "stage_ms": {"apply": 1.0}},
+                      "mixed": {"ms_per_step": 500.0, "solves_per_s": 256.0, "eig_s": 0.45,
+                                "accuracy": {"u_rel_l2_alpha2_vs_cg_max": 1e-14}}}}
+    recs = bench.jsonl_records(line)
+    assert [r["precision"] for r in recs] == ["fp64", "mixed"]
+    assert recs[0]["seconds"] == 2.0 and recs[0]["err_orth"] == 1e-15 and "roofline" not in recs[0]
+    assert recs[1]["roofline"] == {"frac": 0.4} and recs[1]["err_u_alpha2"] == 1e-14
+    assert bench.jsonl_records({}) == []
