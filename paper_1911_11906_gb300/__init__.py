@@ -30,3 +30,4 @@ from ._binding import (  # noqa: F401
     save_decomposition,
     load_decomposition,
 )
+from . import autotune  # noqa: E402,F401  (schedule autotuner with a persistent cache)
