@@ -192,6 +192,36 @@ int frac_diffusion(fraclap_ctx* ctx, const double* V_dev, int64_t ldv, const dou
                    size_t work_bytes, fraclap_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * CUDA-graph form of the apply: frac_apply (pair_t_dev == NULL) or
+ * frac_diffusion (pair_t_dev given, with mu) captured once, on a private
+ * stream, into an instantiated CUDA graph, so that repeated solves with new
+ * contents of the SAME buffers (new forcings in F_dev, new orders or times in
+ * the pair arrays, a new decomposition in V_dev/lambda_dev) cost one graph
+ * launch instead of the GEMM, scaling and slicing launches one by one.
+ *
+ *  Arguments as for frac_diffusion; the product route (FP64 or BF16 slices)
+ *  is the context's setting at creation.  work_dev is REQUIRED (a
+ *  caller-owned workspace of fraclap_apply_workspace_bytes_ctx bytes: the
+ *  context's own may be reallocated by later calls).  The graph keeps every
+ *  pointer it was created with: the buffers, the workspace and the context
+ *  (its status word receives NOT_SPD / INVALID_ARG from a launch, read by
+ *  fraclap_sync) must outlive it, and launches of one graph must not overlap.
+ * fraclap_graph_launch: one replay on `stream` (asynchronous).
+ * fraclap_graph_kernels: the number of kernels in the graph (-1 for NULL);
+ *  each launch adds it to the context's launch count.
+ * fraclap_graph_destroy: frees the graph (NULL is a no-op).
+ * ---------------------------------------------------------------------- */
+typedef struct fraclap_graph fraclap_graph;
+int fraclap_apply_graph_create(fraclap_ctx* ctx, const double* V_dev, int64_t ldv,
+                               const double* lambda_dev, int64_t n, const double* F_dev, int64_t ldf,
+                               int64_t m, const int32_t* pair_f_dev, const double* pair_alpha_dev,
+                               const double* pair_t_dev, double mu, int64_t k, double* U_dev,
+                               int64_t ldu, void* work_dev, size_t work_bytes, fraclap_graph** out);
+int fraclap_graph_launch(fraclap_graph* g, fraclap_stream_t stream);
+long long fraclap_graph_kernels(const fraclap_graph* g);
+void fraclap_graph_destroy(fraclap_graph* g);
+
+/* ------------------------------------------------------------------------
  * frac_apply_noalloc —frac_apply for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a deployment variant.
  * It serves code that runs where cudaMalloc is not available to it: inside a

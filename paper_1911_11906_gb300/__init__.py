@@ -18,6 +18,7 @@ from ._binding import (  # noqa: F401
     eig_full_mixed,
     frac_apply,
     frac_diffusion,
+    ApplyGraph,
     tridiagonalize,
     tridiag_eig,
     dgemm,

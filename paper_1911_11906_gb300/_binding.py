@@ -42,6 +42,11 @@ SIGNATURES = {
     "fraclap_set_tensor_route": (_i32, [_p, _i32]),
     "fraclap_set_refine_tau": (_i32, [_p, _dbl]),
     "fraclap_wait_selftest": (_i32, [_p, _i32, _p]),
+    "fraclap_apply_graph_create": (_i32, [_p, _p, _i64, _p, _i64, _p, _i64, _i64, _p, _p, _p, _dbl, _i64, _p, _i64,
+                                          _p, _sz, _p]),
+    "fraclap_graph_launch": (_i32, [_p, _p]),
+    "fraclap_graph_kernels": (ctypes.c_longlong, [_p]),
+    "fraclap_graph_destroy": (None, [_p]),
     "fraclap_mask_hash": (ctypes.c_uint64, [_p, _i32, _p, _dbl]),
     "fraclap_save_decomposition": (_i32, [ctypes.c_char_p, _i64, _p, _p, _i64, _i32, _p, _dbl, ctypes.c_uint64]),
     "fraclap_load_decomposition": (_i32, [ctypes.c_char_p, _p, _p, _p, _p, _p, _p, _p, _i64, ctypes.c_uint64]),
@@ -326,6 +331,58 @@ def frac_diffusion(V: torch.Tensor, lam: torch.Tensor, U0: torch.Tensor, pair_f,
     if sync:
         ctx.sync(stream)
     return U
+
+
+class ApplyGraph:
+    """frac_apply (or frac_diffusion, when pair_t is given) captured once into
+    a CUDA graph.  Later solves change the CONTENTS of the same buffers
+    (self.F, self.pair_f, self.pair_alpha, self.pair_t, V, lam) and call
+    launch(); the result is self.U.  Inputs must be CUDA tensors; pair
+    arrays are copied to the device once, here."""
+
+    def __init__(self, V: torch.Tensor, lam: torch.Tensor, F: torch.Tensor, pair_f, pair_alpha, pair_t=None,
+                 mu: float = 1.0, ctx: Context | None = None, out: torch.Tensor | None = None):
+        self.ctx = ctx or default_context()
+        self.V = _f64_colmajor(V, "V")
+        self.lam = lam.contiguous()
+        self.F = _f64_colmajor(F, "F")
+        n, dev = self.V.shape[0], self.V.device
+        self.pair_f = torch.as_tensor(pair_f, dtype=torch.int32).to(dev).contiguous()
+        self.pair_alpha = torch.as_tensor(pair_alpha, dtype=torch.float64).to(dev).contiguous()
+        self.pair_t = None if pair_t is None else torch.as_tensor(pair_t, dtype=torch.float64).to(dev).contiguous()
+        k, m = self.pair_f.numel(), self.F.shape[1]
+        if self.pair_alpha.numel() != k or (self.pair_t is not None and self.pair_t.numel() != k):
+            raise ValueError("pair arrays differ in length")
+        self.U = out if out is not None else empty_colmajor(n, k, dev)
+        nbytes = self.ctx.lib.fraclap_apply_workspace_bytes_ctx(self.ctx.handle, n, m, k)
+        self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+        self.handle = ctypes.c_void_p()
+        torch.cuda.synchronize(dev)  # the buffers above are ready before the capture reads their addresses
+        self.ctx.check(self.ctx.lib.fraclap_apply_graph_create(
+            self.ctx.handle, _ptr(self.V), _ld(self.V), _ptr(self.lam), n, _ptr(self.F), _ld(self.F), m,
+            _ptr(self.pair_f), _ptr(self.pair_alpha), _ptr(self.pair_t), float(mu), k, _ptr(self.U), _ld(self.U),
+            _ptr(self.workspace), self.workspace.numel(), ctypes.byref(self.handle)))
+
+    @property
+    def kernels(self) -> int:
+        return int(self.ctx.lib.fraclap_graph_kernels(self.handle))
+
+    def launch(self, stream=None, sync: bool = True) -> torch.Tensor:
+        self.ctx.check(self.ctx.lib.fraclap_graph_launch(self.handle, ctypes.c_void_p(_stream(stream))))
+        if sync:
+            self.ctx.sync(stream)
+        return self.U
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self.ctx.lib.fraclap_graph_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tridiagonalize(A: torch.Tensor, want_q: bool = True, ctx: Context | None = None, stream=None):

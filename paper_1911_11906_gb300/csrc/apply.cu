@@ -230,3 +230,82 @@ extern "C" int frac_apply_noalloc(const double* V_dev, int64_t ldv, const double
   d = GemmDesc{n, k, n, V_dev, ldv, C, n, U_dev, ldu, nullptr, 0, nullptr, 0, 0, 1.0, 0.0};
   return gemm(&local, false, false, kGemmPlain, d, 1, st);
 }
+
+// ----------------------------------------------------------------------------
+// The spectral apply captured once into a CUDA graph: every later solve with
+// new contents of the same buffers is a single graph launch instead of the
+// GEMM, scaling and slicing launches one by one.
+// ----------------------------------------------------------------------------
+struct fraclap_graph {
+  fraclap_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;  // kernels in the graph (added to the context's launch count per launch)
+};
+
+extern "C" int fraclap_apply_graph_create(fraclap_ctx* ctx, const double* V_dev, int64_t ldv,
+                                          const double* lambda_dev, int64_t n, const double* F_dev,
+                                          int64_t ldf, int64_t m, const int32_t* pair_f_dev,
+                                          const double* pair_alpha_dev, const double* pair_t_dev, double mu,
+                                          int64_t k, double* U_dev, int64_t ldu, void* work_dev,
+                                          size_t work_bytes, fraclap_graph** out) {
+  if (!ctx || !out) return FRACLAP_ERR_INVALID_ARG;
+  *out = nullptr;
+  FL_CHECK(ctx, work_dev != nullptr, FRACLAP_ERR_INVALID_ARG,
+           "apply_graph: a graph needs a caller-owned workspace (the context's may be reallocated)");
+  FL_CHECK(ctx, std::isfinite(mu), FRACLAP_ERR_INVALID_ARG, "apply_graph: mu is not finite");
+  cudaStream_t s = nullptr;
+  FL_CUDA(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(s);
+    return set_error(ctx, FRACLAP_ERR_CUDA, "apply_graph: begin capture: %s", cudaGetErrorString(e));
+  }
+  const long long before = ctx->launches;
+  const int rc = spectral_apply(ctx, pair_t_dev ? "apply_graph(diffusion)" : "apply_graph", V_dev, ldv,
+                                lambda_dev, n, F_dev, ldf, m, pair_f_dev, pair_alpha_dev, pair_t_dev, mu, k,
+                                U_dev, ldu, work_dev, work_bytes, s);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s, &g);
+  cudaStreamDestroy(s);
+  if (rc != 0 || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    ctx->launches = before;
+    if (rc != 0) return rc;
+    return set_error(ctx, FRACLAP_ERR_CUDA, "apply_graph: end capture: %s", cudaGetErrorString(e));
+  }
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    ctx->launches = before;
+    return set_error(ctx, FRACLAP_ERR_CUDA, "apply_graph: instantiate: %s", cudaGetErrorString(e));
+  }
+  fraclap_graph* G = new fraclap_graph;
+  G->ctx = ctx;
+  G->graph = g;
+  G->exec = x;
+  G->kernels = ctx->launches - before;
+  ctx->launches = before;  // counted when launched
+  *out = G;
+  return 0;
+}
+
+extern "C" int fraclap_graph_launch(fraclap_graph* g, fraclap_stream_t stream) {
+  if (!g || !g->exec) return FRACLAP_ERR_INVALID_ARG;
+  FL_CUDA(g->ctx, cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+  g->ctx->launches += g->kernels;
+  return 0;
+}
+
+extern "C" long long fraclap_graph_kernels(const fraclap_graph* g) { return g ? g->kernels : -1; }
+
+extern "C" void fraclap_graph_destroy(fraclap_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
