@@ -711,6 +711,13 @@ def main():
                     help="ellipse128: the headline workload; batched256, apply192 and diffusion192: the "
                          "batched, apply-at-scale and diffusion-at-scale workloads, one JSON line each")
     args = ap.parse_args()
+    if args.workload != "ellipse128" and args.impl == "fraclap":
+        # single-GPU workloads: under torchrun, rank 0 runs them on its own GPU
+        # and prints the one line; the other ranks leave without work
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     if args.workload == "batched256":
         run_batched_bench(args)
         return
