@@ -203,6 +203,35 @@ def _f64_colmajor(t: torch.Tensor, name: str) -> torch.Tensor:
     return t
 
 
+def _dev(t, dtype, name: str, device, numel: int | None = None) -> torch.Tensor:
+    """A contiguous CUDA tensor of `dtype` on `device` (and `numel` long when
+    given); anything else is refused, so that no host pointer and no short
+    buffer ever reaches a kernel."""
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or t.device != device:
+        raise TypeError(f"{name} must be a {dtype} CUDA tensor on {device}")
+    t = t.contiguous()
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must hold {numel} elements, not {t.numel()}")
+    return t
+
+
+def _out(t: torch.Tensor, dtype, name: str, device, rows: int, cols: int) -> torch.Tensor:
+    """A caller-provided output, written in place: column-major, `dtype`, on
+    `device`, of shape (rows, cols)."""
+    if (not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or t.device != device
+            or tuple(t.shape) != (rows, cols) or (rows > 1 and cols > 0 and t.stride(0) != 1)):
+        raise TypeError(f"{name} must be a column-major {dtype} CUDA tensor of shape ({rows}, {cols}) on {device}")
+    return t
+
+
+def _ws(t: torch.Tensor, device) -> torch.Tensor:
+    """A caller-provided device workspace (uint8, contiguous, on `device`)."""
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.uint8 or not t.is_cuda or t.device != device \
+            or not t.is_contiguous():
+        raise TypeError(f"workspace must be a contiguous uint8 CUDA tensor on {device}")
+    return t
+
+
 def _ld(t: torch.Tensor) -> int:
     return max(t.stride(1), t.shape[0], 1) if t.dim() == 2 else max(t.shape[0], 1)
 
@@ -250,6 +279,8 @@ def eig_full(A: torch.Tensor, ctx: Context | None = None, stream=None, workspace
     if workspace is None:
         nbytes = ctx.lib.fraclap_eig_workspace_bytes(ctx.handle, n)
         workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=A.device)
+    else:
+        workspace = _ws(workspace, A.device)
     st = ctypes.c_void_p(_stream(stream))
     ctx.check(ctx.lib.eig_full(ctx.handle, _ptr(A), n, _ld(A), _ptr(lam), _ptr(V), max(n, 1),
                                _ptr(workspace), workspace.numel(), None, st))
@@ -266,11 +297,16 @@ def eig_full_mixed(A: torch.Tensor, rowptr: torch.Tensor, col: torch.Tensor, val
     ctx = ctx or default_context()
     A = _f64_colmajor(A, "A")
     n = A.shape[0]
+    rowptr = _dev(rowptr, torch.int64, "rowptr", A.device, n + 1)
+    col = _dev(col, torch.int32, "col", A.device)
+    val = _dev(val, torch.float64, "val", A.device, col.numel())
     lam = torch.empty(n, dtype=torch.float64, device=A.device)
     V = empty_colmajor(n, n, A.device)
     if workspace is None:
         nbytes = ctx.lib.fraclap_eig_mixed_workspace_bytes(ctx.handle, n)
         workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=A.device)
+    else:
+        workspace = _ws(workspace, A.device)
     st = ctypes.c_void_p(_stream(stream))
     ctx.check(ctx.lib.eig_full_mixed(ctx.handle, _ptr(A), n, _ld(A), _ptr(rowptr), _ptr(col), _ptr(val),
                                      int(refine_iters), _ptr(lam), _ptr(V), max(n, 1), _ptr(workspace),
@@ -292,10 +328,15 @@ def frac_apply(V: torch.Tensor, lam: torch.Tensor, F: torch.Tensor, pair_f, pair
     pf = torch.as_tensor(pair_f, dtype=torch.int32).to(dev).contiguous()
     pa = torch.as_tensor(pair_alpha, dtype=torch.float64).to(dev).contiguous()
     k, m = pf.numel(), F.shape[1]
-    U = out if out is not None else empty_colmajor(n, k, dev)
+    if pa.numel() != k:
+        raise ValueError("pair_f and pair_alpha differ in length")
+    lam = _dev(lam, torch.float64, "lam", dev, n)
+    U = _out(out, torch.float64, "out", dev, n, k) if out is not None else empty_colmajor(n, k, dev)
     if workspace is None:
         nbytes = ctx.lib.fraclap_apply_workspace_bytes_ctx(ctx.handle, n, m, k)
         workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    else:
+        workspace = _ws(workspace, dev)
     st = ctypes.c_void_p(_stream(stream))
     ctx.check(ctx.lib.frac_apply(ctx.handle, _ptr(V), _ld(V), _ptr(lam.contiguous()), n, _ptr(F), _ld(F), m,
                                  _ptr(pf), _ptr(pa), k, _ptr(U), _ld(U), _ptr(workspace), workspace.numel(), st))
@@ -320,10 +361,13 @@ def frac_diffusion(V: torch.Tensor, lam: torch.Tensor, U0: torch.Tensor, pair_f,
     k, m = pf.numel(), U0.shape[1]
     if pa.numel() != k or pt.numel() != k:
         raise ValueError("pair_f, pair_alpha and pair_t differ in length")
-    U = out if out is not None else empty_colmajor(n, k, dev)
+    lam = _dev(lam, torch.float64, "lam", dev, n)
+    U = _out(out, torch.float64, "out", dev, n, k) if out is not None else empty_colmajor(n, k, dev)
     if workspace is None:
         nbytes = ctx.lib.fraclap_apply_workspace_bytes_ctx(ctx.handle, n, m, k)
         workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    else:
+        workspace = _ws(workspace, dev)
     st = ctypes.c_void_p(_stream(stream))
     ctx.check(ctx.lib.frac_diffusion(ctx.handle, _ptr(V), _ld(V), _ptr(lam.contiguous()), n, _ptr(U0), _ld(U0), m,
                                      _ptr(pf), _ptr(pa), _ptr(pt), float(mu), k, _ptr(U), _ld(U),
@@ -344,16 +388,16 @@ class ApplyGraph:
                  mu: float = 1.0, ctx: Context | None = None, out: torch.Tensor | None = None):
         self.ctx = ctx or default_context()
         self.V = _f64_colmajor(V, "V")
-        self.lam = lam.contiguous()
         self.F = _f64_colmajor(F, "F")
         n, dev = self.V.shape[0], self.V.device
+        self.lam = _dev(lam, torch.float64, "lam", dev, n)
         self.pair_f = torch.as_tensor(pair_f, dtype=torch.int32).to(dev).contiguous()
         self.pair_alpha = torch.as_tensor(pair_alpha, dtype=torch.float64).to(dev).contiguous()
         self.pair_t = None if pair_t is None else torch.as_tensor(pair_t, dtype=torch.float64).to(dev).contiguous()
         k, m = self.pair_f.numel(), self.F.shape[1]
         if self.pair_alpha.numel() != k or (self.pair_t is not None and self.pair_t.numel() != k):
             raise ValueError("pair arrays differ in length")
-        self.U = out if out is not None else empty_colmajor(n, k, dev)
+        self.U = _out(out, torch.float64, "out", dev, n, k) if out is not None else empty_colmajor(n, k, dev)
         nbytes = self.ctx.lib.fraclap_apply_workspace_bytes_ctx(self.ctx.handle, n, m, k)
         self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
         self.handle = ctypes.c_void_p()
@@ -405,7 +449,11 @@ def tridiagonalize(A: torch.Tensor, want_q: bool = True, ctx: Context | None = N
 def tridiag_eig(d: torch.Tensor, e: torch.Tensor, ctx: Context | None = None, stream=None):
     """Divide-and-conquer eigensolver of the symmetric tridiagonal (d, e)."""
     ctx = ctx or default_context()
+    if not isinstance(d, torch.Tensor) or not d.is_cuda:
+        raise TypeError("d must be a float64 CUDA tensor")
+    d = _dev(d, torch.float64, "d", d.device)
     n = d.numel()
+    e = _dev(e, torch.float64, "e", d.device, max(n - 1, 0))
     lam = torch.empty(n, dtype=torch.float64, device=d.device)
     Z = empty_colmajor(n, n, d.device)
     nbytes = ctx.lib.fraclap_tridiag_workspace_bytes(ctx.handle, n)
@@ -430,6 +478,8 @@ def dgemm(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, alpha=
     if C is None:
         C = empty_colmajor(m, n, A.device)
         beta = 0.0
+    else:
+        C = _out(C, torch.float64, "C", A.device, m, n)
     st = ctypes.c_void_p(_stream(stream))
     ctx.check(ctx.lib.fraclap_dgemm(ctx.handle, int(trans_a), int(trans_b), m, n, k, float(alpha), _ptr(A),
                                     _ld(A), _ptr(B), _ld(B), float(beta), _ptr(C), _ld(C), st))
@@ -455,6 +505,8 @@ def sgemm(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, alpha=
     if C is None:
         C = torch.zeros((n, m), dtype=torch.float32, device=A.device).t()
         beta = 0.0
+    else:
+        C = _out(C, torch.float32, "C", A.device, m, n)
     ws = ctx.lib.fraclap_sgemm_workspace_bytes(m, n, k)
     work = torch.empty(ws, dtype=torch.uint8, device=A.device)
     st = ctypes.c_void_p(_stream(stream))
@@ -503,9 +555,11 @@ def solve_batched(problems, workers: int = 0, ctx: Context | None = None, stream
             arr[i].U_dev, arr[i].ldu = U.data_ptr(), _ld(U)
         arr[i].n, arr[i].k = n, k
         if pr.get("rowptr") is not None and n:
-            keep += [pr["rowptr"], pr["col"], pr["val"]]
-            arr[i].rowptr_dev, arr[i].col_dev, arr[i].val_dev = (pr["rowptr"].data_ptr(), pr["col"].data_ptr(),
-                                                                 pr["val"].data_ptr())
+            rp = _dev(pr["rowptr"], torch.int64, f"problem {i}: rowptr", dev, n + 1)
+            cl = _dev(pr["col"], torch.int32, f"problem {i}: col", dev)
+            vl = _dev(pr["val"], torch.float64, f"problem {i}: val", dev, cl.numel())
+            keep += [rp, cl, vl]
+            arr[i].rowptr_dev, arr[i].col_dev, arr[i].val_dev = rp.data_ptr(), cl.data_ptr(), vl.data_ptr()
             arr[i].refine_iters = int(pr.get("refine_iters", 6))
         if n:
             keep.append(A)
@@ -531,6 +585,8 @@ def dgemm_ozaki(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, 
     if C is None:
         C = empty_colmajor(m, n, A.device)
         beta = 0.0
+    else:
+        C = _out(C, torch.float64, "C", A.device, m, n)
     nbytes = ctx.lib.fraclap_dgemm_ozaki_workspace_bytes(m, n, k, slices)
     ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=A.device)
     st = ctypes.c_void_p(_stream(stream))

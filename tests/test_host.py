@@ -231,3 +231,34 @@ def test_bench_jsonl_records():
     assert recs[0]["seconds"] == 2.0 and recs[0]["err_orth"] == 1e-15 and "roofline" not in recs[0]
     assert recs[1]["roofline"] == {"frac": 0.4} and recs[1]["err_u_alpha2"] == 1e-14
     assert bench.jsonl_records({}) == []
+
+
+def test_public_calls_refuse_host_tensors():
+    """No CPU fallback: the compute entry points raise on host tensors (or,
+    without a GPU, when the context cannot be created) instead of computing
+    anything on the CPU."""
+    torch = pytest.importorskip("torch")
+    import paper_1911_11906_gb300 as F
+    A = torch.eye(4, dtype=torch.float64)
+    lam = torch.ones(4, dtype=torch.float64)
+    Fm = torch.ones(4, 1, dtype=torch.float64)
+    calls = [lambda: F.eig_full(A), lambda: F.frac_apply(A, lam, Fm, [0], [1.0]),
+             lambda: F.frac_diffusion(A, lam, Fm, [0], [1.0], [0.1]), lambda: F.dgemm(A, A),
+             lambda: F.fd_assemble(torch.ones(3, 3, dtype=torch.uint8), 0.25)]
+    for call in calls:
+        with pytest.raises((TypeError, F.FraclapError, RuntimeError)):
+            call()
+
+
+def test_binding_input_guards():
+    """The binding's guards refuse host tensors, wrong dtypes, short buffers
+    and row-major outputs before any pointer reaches the library."""
+    torch = pytest.importorskip("torch")
+    from paper_1911_11906_gb300 import _binding as B
+    dev = torch.device("cuda", 0)
+    for call in (lambda: B._dev(torch.ones(3), torch.float32, "x", dev),
+                 lambda: B._dev(torch.ones(3, dtype=torch.int32), torch.float32, "x", dev),
+                 lambda: B._out(torch.ones(3, 2, dtype=torch.float64), torch.float64, "out", dev, 3, 2),
+                 lambda: B._ws(torch.empty(8, dtype=torch.uint8), dev)):
+        with pytest.raises(TypeError):
+            call()
