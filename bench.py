@@ -12,14 +12,20 @@ eigenvalues bracketed by inertia counts at +-1e-11, sampled orthogonality
 129 MB L2, so no flush is needed between steps.
 
 Printed value: fractional solves per second (128 solves per step, each
-including its share of the decomposition), whole job over all ranks.
+including its share of the decomposition), whole job over all ranks.  The
+mixed route counts only when its eigenvalues and all 128 solutions agree
+with the FP64 route's to 1e-11 / 1e-10.  The line also carries, under
+"configs", the other single-GPU workloads (square48, batched256, apply192)
+with their accuracy against the oracle, and, under "cpu_baseline", the FP64
+CPU oracle timed on one whole step of this workload on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fraclap|reference]
-                  [--path both|fp64|mixed]
+                  [--path both|fp64|mixed] [--workload NAME] [--no-configs]
 
 --impl reference times the FP64 CPU oracle (the plain statement of the
-method, test infrastructure) on a bounded sample of the same workload on the
-host cores.
+method, test infrastructure) on whole steps of the same workload on the host
+cores; one step takes minutes, so it stops after the first step that ends
+past a one-minute budget and prints how many steps it timed.
 """
 from __future__ import annotations
 
@@ -184,6 +190,8 @@ def whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
 FP32_PEAK_TFLOPS = 152 * 2.070e9 * 128 * 2 / 1e12
 REFINE_ITERS = 6
 BAND = {"fp64": 64, "mixed": 64}
+# wall-clock budget of the oracle arm: whole steps are timed until one ends past it
+REFERENCE_BUDGET_S = 60.0
 
 
 def ozaki_bf16_flops(n: int, slices: int = 8) -> float:
@@ -211,7 +219,7 @@ def refine_slice_counts(iterations: int, cap: int) -> list:
 OZAKI_DRAM_BYTES_PER_FLOP = (12.866905e9 + 1.060005e9) / (36 * 2.0 * 4096 ** 3)
 
 
-def run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier):
+def run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier, steps=None, warmup=None):
     import torch
     n = p.n
     if path == "fp64":
@@ -230,7 +238,9 @@ def run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier):
         F.frac_apply(V, lam, Fd, pf, pa, ctx=ctx, out=U, workspace=app_ws, sync=sync_status)
         return lam, V
 
-    for _ in range(args.warmup):
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    for _ in range(warmup):
         lam, V = step(sync_status=True)
     torch.cuda.synchronize()
     ctx.set_profiling(True)
@@ -243,20 +253,20 @@ def run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         lam, V = step()
     e1.record()
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    launches = (ctx.launch_count() - launches0) // args.steps
+    ms = e0.elapsed_time(e1) / steps
+    launches = (ctx.launch_count() - launches0) // steps
     stages = ctx.stage_times()
     ctx.set_profiling(False)
     ctx.sync()
     rstats = ctx.refine_stats() if path == "mixed" else []
     return {"ms": ms, "launches": launches, "stages": stages, "clocks": clk, "lam": lam, "V": V,
-            "refine": rstats, "step": step}
+            "refine": rstats, "step": step, "steps": steps, "warmup": warmup}
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -280,13 +290,33 @@ def run_gpu(args, rank, world, local_rank):
     barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
     paths = ["fp64", "mixed"] if args.path == "both" else [args.path]
     results = {}
+    band = dict(BAND)
+    band_src = {pth: "fixed" for pth in band}
+    if "mixed" in paths and not args.no_autotune:
+        from paper_1911_11906_gb300 import autotune
+        band["mixed"] = autotune.best_band_width(n, "mixed")
+        band_src["mixed"] = "autotuner (cache %s)" % autotune.default_cache_path()
     for path in paths:
-        ctx = F.Context(band_width=BAND[path])
+        ctx = F.Context(band_width=band[path])
         app_ws = torch.empty(ctx.lib.fraclap_apply_workspace_bytes(n, Fd.shape[1], k), dtype=torch.uint8, device=dev)
-        r = run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier)
+        # the FP64 route is the comparison when both run: fewer timed steps (it is 6x slower)
+        short = path == "fp64" and len(paths) > 1
+        r = run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier,
+                     steps=min(args.steps, 2) if short else None, warmup=min(args.warmup, 3) if short else None)
         r["ctx"] = ctx
+        r["U"] = U.clone()
         r["acc"] = check_accuracy(F, ctx, p, mask, r["lam"], U, r["V"], Fd) if rank == 0 else {}
         results[path] = r
+    if rank == 0 and "fp64" in results and "mixed" in results:
+        # the mixed route against the plain FP64 route on every solve and eigenvalue
+        acc = results["mixed"]["acc"]
+        Um, Ud = results["mixed"]["U"], results["fp64"]["U"]
+        acc["u_rel_l2_vs_fp64_route_max"] = float((torch.linalg.norm(Um - Ud, dim=0)
+                                                   / torch.linalg.norm(Ud, dim=0)).max())
+        lm, ld = results["mixed"]["lam"], results["fp64"]["lam"]
+        acc["lambda_rel_vs_fp64_route_max"] = float(((lm - ld).abs() / ld.abs()).max())
+        acc["meets_fp64_bar"] = bool(acc["meets_fp64_bar"] and acc["u_rel_l2_vs_fp64_route_max"] <= 1e-10
+                                     and acc["lambda_rel_vs_fp64_route_max"] <= 1e-11)
     # headline: the fastest path whose accuracy checks pass
     ok = [pth for pth in paths if rank != 0 or results[pth]["acc"].get("meets_fp64_bar", False)]
     head = min(ok or paths, key=lambda pth: results[pth]["ms"])
@@ -317,7 +347,7 @@ def run_gpu(args, rank, world, local_rank):
         return
 
     stages = R["stages"]
-    b = BAND[head]
+    b = band[head]
     if head == "fp64":
         q2_ms, q2_cnt = stages["back_q2"]
         dur = q2_ms / max(q2_cnt, 1)
@@ -368,21 +398,32 @@ def run_gpu(args, rank, world, local_rank):
     }
     for pth, r in results.items():
         st = r["stages"]
-        eig_ms = sum(st[s][0] for s in eig_stages) / args.steps
+        eig_ms = sum(st[s][0] for s in eig_stages) / r["steps"]
         line["paths"][pth] = {
             "ms_per_step": round(r["ms"], 3), "solves_per_s": round(k / (r["ms"] * 1e-3), 4),
+            "steps_timed": r["steps"], "warmup": r["warmup"],
             "eig_s": round(eig_ms / 1e3, 4),
             "eig_tflops_credited_fp64": round(eig_flops(n) / (eig_ms * 1e-3) / 1e12, 4),
             "eig_frac_of_fp64_peak": round(eig_flops(n) / (eig_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
-            "apply_s": round(st["apply"][0] / args.steps / 1e3, 5),
-            "stage_ms": {s: round(v[0] / args.steps, 3) for s, v in st.items()},
+            "apply_s": round(st["apply"][0] / r["steps"] / 1e3, 5),
+            "stage_ms": {s: round(v[0] / r["steps"], 3) for s, v in st.items()},
             "gpu_launches": int(r["launches"]),
             "accuracy": r["acc"],
-            "band_width": BAND[pth],
+            "band_width": band[pth], "band_width_source": band_src[pth],
         }
         if r["refine"]:
             line["paths"][pth]["refine_iterations"] = len(r["refine"])
             line["paths"][pth]["refine_last"] = {kk: float("%.3e" % vv) for kk, vv in r["refine"][-1].items()}
+    if world == 1 and not args.no_configs:
+        # the other workloads, a few timed steps each (W = 3), with their accuracy against the oracle
+        sub_w, sub_k = max(3, min(args.warmup, 3)), min(args.steps, 3)
+        line["configs"] = {}
+        for name, fn in (("square48", lambda: run_square_bench(args, steps=sub_k, warmup=sub_w)),
+                         ("batched256", lambda: run_batched_bench(args, steps=sub_k, warmup=sub_w)),
+                         ("apply192", lambda: run_apply_bench(args, steps=sub_k, warmup=sub_w))):
+            sub = fn()
+            sub.pop("metric", None)
+            line["configs"][name] = sub
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     print(json.dumps(line), flush=True)
@@ -470,63 +511,67 @@ def check_accuracy(F, ctx, p, mask, lam, U, V, Fd):
 # ----------------------------------------------------------------------------
 # the CPU oracle (baseline / reference arm)
 # ----------------------------------------------------------------------------
-def _oracle_sample():
-    """A bounded sample of the workload for the CPU oracle: the same
-    generator on a 72 x 72 grid (n ~ 2800), scaled to the full workload by
-    the n^3 cost of the eigendecomposition."""
-    from paper_1911_11906_gb300 import inputs as I
-    return I.ellipse_problem(72, n_ellipses=6, n_forcings=16, seed=1000)
-
-
-def cpu_baseline(p_full, sample=None):
+def oracle_step(p):
+    """One step of the workload through the FP64 CPU oracle: assembly, the
+    full eigendecomposition (Householder + implicit QR) and the spectral
+    apply of every solve.  Returns the wall seconds."""
     import oracle as O
-    s = sample or _oracle_sample()
     t0 = time.perf_counter()
-    O.solve(s.mask, s.h, s.F, s.pair_f, s.pair_alpha)
-    t = time.perf_counter() - t0
-    scale = (p_full.n / s.n) ** 3
-    est = t * scale
-    return {"value": round(len(p_full.pair_f) / est, 6), "unit": "solves/s", "cores": O.num_threads(),
-            "kind": "oracle",
-            "sample": f"oracle solve (Householder + implicit QR, spectral apply) of the same generator on a "
-                      f"72x72 grid, n={s.n}, {t:.2f} s, scaled by (n_full/n_sample)^3 = {scale:.2f} "
-                      f"to n={p_full.n}"}
+    O.solve(p.mask, p.h, p.F, p.pair_f, p.pair_alpha)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(p):
+    """The oracle timed on the host cores on one whole step of the workload
+    itself (n = 8810, 128 solves): measured, not scaled from a smaller grid."""
+    import oracle as O
+    t = oracle_step(p)
+    return {"value": round(len(p.pair_f) / t, 6), "unit": "solves/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"one full step of the workload: oracle solve (assembly, Householder + implicit QR "
+                      f"eigendecomposition, spectral apply) of the ellipse128 grid itself, n={p.n}, "
+                      f"{len(p.pair_f)} solves, {t:.1f} s wall"}
 
 
 def run_reference(args, rank, world):
+    """The oracle arm.  One step of the workload takes minutes on the host
+    cores, so it times whole steps until the first one that ends past
+    REFERENCE_BUDGET_S (at least one, at most --steps), without warm-up, and
+    prints the number of steps it really timed."""
     if rank != 0:
         return
     import oracle as O
     p = _workload()
-    s = _oracle_sample()
-    for _ in range(min(args.warmup, 1)):
-        O.solve(s.mask, s.h, s.F, s.pair_f, s.pair_alpha)
     times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        O.solve(s.mask, s.h, s.F, s.pair_f, s.pair_alpha)
-        times.append(time.perf_counter() - t0)
-    t = statistics.median(times) * (p.n / s.n) ** 3
+    t_start = time.perf_counter()
+    while len(times) < max(1, args.steps):
+        times.append(oracle_step(p))
+        if time.perf_counter() - t_start > REFERENCE_BUDGET_S:
+            break
+    t = statistics.mean(times)
     value = len(p.pair_f) / t
     line = {
         "metric": METRIC, "impl": "reference", "value": round(value, 6), "unit": "solves/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 1),
+        "n_gpus": world, "steps": len(times), "warmup": 0, "steps_requested": args.steps,
+        "warmup_requested": args.warmup, "ms_per_step": round(t * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded masked grid and polynomial forcings)",
         "config": _config(p, {"parallelism": "host cores (OpenMP)"}),
         "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": O.num_threads(), "kind": "oracle",
-                         "sample": f"each step: oracle solve on the 72x72 sample (n={s.n}), "
-                                   f"scaled by (n/n_sample)^3 to n={p.n}"},
+                         "sample": f"{len(times)} whole step(s) of the workload itself (n={p.n}, "
+                                   f"{len(p.pair_f)} solves each), no warm-up: one step takes minutes, so the "
+                                   f"{args.steps} requested steps are cut after {REFERENCE_BUDGET_S:.0f} s"},
         "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def _timed_line(args, metric, unit, per_step_units, step, ctx, extra):
+def _timed_line(args, metric, unit, per_step_units, step, ctx, extra, steps=None, warmup=None):
     """Warm-up, then K timed steps between CUDA events on the current stream
     (clocks sampled meanwhile); returns the common JSON fields."""
     import torch
-    for _ in range(args.warmup):
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     launches0 = ctx.launch_count()
@@ -534,27 +579,85 @@ def _timed_line(args, metric, unit, per_step_units, step, ctx, extra):
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
     ctx.sync()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     line = {"metric": metric, "value": round(per_step_units / (ms * 1e-3), 4), "unit": unit, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "steps": steps, "warmup": warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "data": "synthetic (seeded masked grids and forcings)",
-            "gpu_launches": (ctx.launch_count() - launches0) // args.steps, "clocks": clk}
+            "gpu_launches": (ctx.launch_count() - launches0) // steps, "clocks": clk}
     line.update(extra)
     return line
 
 
-def run_batched_bench(args):
+def _worst(acc_list):
+    """Worst value per key over several accuracy dicts (booleans: all true)."""
+    worst = {}
+    for acc in acc_list:
+        for key, v in acc.items():
+            worst[key] = (worst.get(key, True) and v) if isinstance(v, bool) else max(worst.get(key, 0.0), v)
+    return worst
+
+
+def _u_rel(U, U_o):
+    """Largest relative L2 error over the columns of U against U_o (host arrays)."""
+    return float(np.max(np.linalg.norm(U - U_o, axis=0) / np.linalg.norm(U_o, axis=0)))
+
+
+def run_square_bench(args, steps=None, warmup=None):
+    """The plain FP64 method on the 48 x 48 unit square (n = 2304, h = 1/49):
+    one step = assembly, eig_full and frac_apply of 5 forcings x 4 orders
+    (20 solves); compared with the oracle's whole solve on the host."""
+    import torch
+    import oracle as O
+    import paper_1911_11906_gb300 as F
+    from paper_1911_11906_gb300 import inputs as I
+    p = I.square_problem(48)
+    ctx = F.Context(band_width=32)
+    mask = torch.from_numpy(p.mask).cuda()
+    Fd = torch.from_numpy(np.ascontiguousarray(p.F.T)).cuda().t()
+    pf = torch.from_numpy(p.pair_f.astype(np.int32)).cuda()
+    pa = torch.from_numpy(p.pair_alpha.astype(np.float64)).cuda()
+    ws = torch.empty(ctx.lib.fraclap_eig_workspace_bytes(ctx.handle, p.n), dtype=torch.uint8, device="cuda")
+    U = F._binding.empty_colmajor(p.n, len(p.pair_f), "cuda")
+    state = {}
+
+    def step():
+        asm = F.fd_assemble(mask, p.h, ctx=ctx)
+        state["lam"], V = F.eig_full(asm["A"], ctx=ctx, workspace=ws, sync=False)
+        F.frac_apply(V, state["lam"], Fd, pf, pa, ctx=ctx, out=U, sync=False)
+
+    line = _timed_line(args, "fractional solves/s, plain FP64 method (square48, n=2304)", "solves/s",
+                       len(p.pair_f), step, ctx,
+                       {"dtype": "f64", "config": {"workload": "square48: 48x48 unit square, h=1/49, n=2304, "
+                                                               "sin(pi x) sin(pi y) + 4 cubic forcings x 4 alpha",
+                                                   "n": p.n, "band_width": 32,
+                                                   "l2_policy": "no flush (42 MB matrix, L2-resident)"}},
+                       steps=steps, warmup=warmup)
+    lam_o, _, U_o = O.solve(p.mask, p.h, p.F, p.pair_f, p.pair_alpha)
+    lam_g = state["lam"].cpu().numpy()
+    line["accuracy_vs_oracle"] = {"lambda_rel_max": float(np.max(np.abs(lam_g - lam_o) / lam_o)),
+                                  "u_rel_l2_max": _u_rel(U.cpu().numpy(), U_o)}
+    line["accuracy_vs_oracle"]["meets_fp64_bar"] = bool(line["accuracy_vs_oracle"]["lambda_rel_max"] <= 1e-11
+                                                        and line["accuracy_vs_oracle"]["u_rel_l2_max"] <= 1e-10)
+    return line
+
+
+def run_batched_bench(args, steps=None, warmup=None):
     """Many small problems: 256 masked grids (side U{20..64}, n 150..2559), each
     with 8 forcings x 4 orders; one step = fraclap_solve_batched over all of
-    them (mixed route, 16 workers), assembly included, inputs resident."""
+    them (mixed route), assembly included, inputs resident.  The number of
+    concurrent workers comes from the autotuner (measured on this batch on
+    first use, then cached).  Four sampled problems are compared with the
+    oracle's whole solve."""
     import torch
+    import oracle as O
     import paper_1911_11906_gb300 as F
+    from paper_1911_11906_gb300 import autotune
     from paper_1911_11906_gb300 import inputs as I
     probs = I.batched_problems(256)
     ctx = F.Context()
@@ -564,41 +667,52 @@ def run_batched_bench(args):
                       "pair_alpha": p.pair_alpha, "F": torch.from_numpy(np.ascontiguousarray(p.F.T)).cuda().t()})
     state = {}
 
-    def step():
+    def assemble_all():
         batch = []
         for it in items:
             asm = F.fd_assemble(it["mask"], it["h"], ctx=ctx)
             batch.append({"A": asm["A"], "rowptr": asm["rowptr"], "col": asm["col"], "val": asm["val"],
                           "F": it["F"], "pair_f": it["pair_f"], "pair_alpha": it["pair_alpha"]})
-        state["out"] = F.solve_batched(batch, workers=16, ctx=ctx)
+        return batch
+
+    workers = 16 if args.no_autotune else autotune.best_workers(assemble_all())
+
+    def step():
+        state["out"] = F.solve_batched(assemble_all(), workers=workers, ctx=ctx)
 
     line = _timed_line(args, "batched problems/s: 256 masked grids (n 150..2559), eigendecomposition + 32 solves each",
                        "problems/s", len(probs), step, ctx,
                        {"dtype": "f32+f64-refined",
                         "config": {"workload": "batched256: 256 ellipse grids, side U{20..64}, 8 forcings x 4 alpha",
                                    "n_min": int(min(p.n for p in probs)), "n_max": int(max(p.n for p in probs)),
-                                   "n_mean": float(np.mean([p.n for p in probs])), "workers": 16,
-                                   "route": "mixed per problem", "l2_policy": "no flush (many small problems)"}})
-    # evidence on a sample of problems (GPU only; the oracle checks are in the tests)
-    worst = {}
+                                   "n_mean": float(np.mean([p.n for p in probs])), "workers": workers,
+                                   "workers_source": "fixed" if args.no_autotune else "autotuner",
+                                   "route": "mixed per problem", "l2_policy": "no flush (many small problems)"}},
+                       steps=steps, warmup=warmup)
+    accs = []
     for q in (0, 85, 170, 255):
         p, (lam, V, U) = probs[q], state["out"][q]
-        acc = check_accuracy(F, ctx, p, items[q]["mask"], lam, U, V, items[q]["F"])
-        for key, v in acc.items():
-            worst[key] = (worst.get(key, True) and v) if isinstance(v, bool) else max(worst.get(key, 0.0), v)
-    line["accuracy_sampled_problems"] = worst
+        lam_o, _, U_o = O.solve(p.mask, p.h, p.F, p.pair_f, p.pair_alpha)
+        lam_g = lam.cpu().numpy()
+        accs.append({"lambda_rel_max": float(np.max(np.abs(lam_g - lam_o) / lam_o)),
+                     "u_rel_l2_max": _u_rel(U.cpu().numpy(), U_o)})
+    line["accuracy_vs_oracle_sampled_problems"] = _worst(accs)
+    line["accuracy_vs_oracle_sampled_problems"]["sampled"] = [0, 85, 170, 255]
     line["solves_per_s"] = round(line["value"] * 32, 2)
-    print(json.dumps(line), flush=True)
+    return line
 
 
-def run_apply_bench(args, diffusion=False):
+def run_apply_bench(args, diffusion=False, steps=None, warmup=None):
     """The apply at scale: 192 x 192 grid (n = 18278), 4096 distinct forcings
     with alpha ~ U(0.1, 1.9); (V, lambda) computed once beforehand; one step =
     frac_apply of all 4096 pairs with the products as 6 BF16 slices on the
-    tensor cores (FP64 products timed beside it).  With diffusion=True the
-    step is frac_diffusion instead: the 4096 columns are initial states
-    evolved to the paper's t = 0.4 with mu = 1."""
+    tensor cores (FP64 products timed beside it, and the same apply replayed
+    as one captured CUDA graph).  64 sampled pairs are compared with the
+    oracle's apply on the same (V, lambda).  With diffusion=True the step is
+    frac_diffusion instead: the 4096 columns are initial states evolved to the
+    paper's t = 0.4 with mu = 1."""
     import torch
+    import oracle as O
     import paper_1911_11906_gb300 as F
     from paper_1911_11906_gb300 import inputs as I
     p = I.apply_at_scale_problem()
@@ -613,6 +727,8 @@ def run_apply_bench(args, diffusion=False):
     k = len(p.pair_f)
     pt = torch.full((k,), 0.4, dtype=torch.float64, device=mask.device)
     U = F._binding.empty_colmajor(p.n, k, mask.device)
+    metric = ("fractional diffusion solves/s at <=1e-10 err vs FP64 (n=18278, t=0.4)" if diffusion else
+              "fractional solves/s at <=1e-10 err vs FP64 (apply at scale, n=18278)")
     lines = {}
     for slices in (0, 6):
         ctx.set_apply_slices(slices)
@@ -625,71 +741,62 @@ def run_apply_bench(args, diffusion=False):
             else:
                 F.frac_apply(V, lam, Fd, pf, pa, ctx=ctx, out=U, workspace=ws, sync=False)
 
-        metric = ("fractional diffusion solves/s at <=1e-10 err vs FP64 (n=18278, t=0.4)" if diffusion else
-                  "fractional solves/s at <=1e-10 err vs FP64 (apply at scale, n=18278)")
-        lines[slices] = _timed_line(args, metric, "solves/s", k, step, ctx, {})
+        lines[slices] = _timed_line(args, metric, "solves/s", k, step, ctx, {}, steps=steps, warmup=warmup)
         lines[slices]["U"] = U.clone()
+    # the same 6-slice apply captured once and replayed as one graph launch
+    ctx.set_apply_slices(6)
+    G = F.ApplyGraph(V, lam, Fd, pf, pa, pair_t=pt if diffusion else None, mu=1.0, ctx=ctx)
+    gline = _timed_line(args, metric, "solves/s", k, lambda: G.launch(sync=False), ctx, {}, steps=steps,
+                        warmup=warmup)
+    graph_rel = float((torch.linalg.norm(G.U - lines[6]["U"], dim=0) / torch.linalg.norm(lines[6]["U"], dim=0)).max())
+    graph = {"value": gline["value"], "ms_per_step": gline["ms_per_step"], "kernels": G.kernels,
+             "u_rel_l2_vs_direct_max": graph_rel}
+    G.close()
+    # the oracle on the same (V, lambda): 64 sampled pairs, both product routes
+    rng = np.random.default_rng(18278)
+    sample = np.sort(rng.choice(k, size=64, replace=False))
+    used, remap = np.unique(p.pair_f[sample], return_inverse=True)
+    V_h, lam_h = V.cpu().numpy(), lam.cpu().numpy()
     if diffusion:
-        d = lines[6].pop("U") - lines[0].pop("U")
-        rel = float((torch.linalg.norm(d, dim=0) / torch.linalg.norm(U, dim=0)).max())
+        U_o = O.frac_diffusion(V_h, lam_h, p.F[:, used], remap.astype(np.int32), p.pair_alpha[sample],
+                               np.full(64, 0.4), mu=1.0)
+    else:
+        U_o = O.frac_apply(V_h, lam_h, p.F[:, used], remap.astype(np.int32), p.pair_alpha[sample])
+    del V_h
+    idx = torch.from_numpy(sample).cuda()
+    err_o = {s_: _u_rel(lines[s_]["U"][:, idx].cpu().numpy(), U_o) for s_ in (0, 6)}
+    d = lines[6].pop("U") - lines[0].pop("U")
+    rel = float((torch.linalg.norm(d, dim=0) / torch.linalg.norm(U, dim=0)).max())
+    head = lines[6]
+    acc = {"u_rel_l2_vs_fp64_products_max": rel, "u_rel_l2_vs_oracle_sampled_max": err_o[6],
+           "fp64_products_u_rel_l2_vs_oracle_sampled_max": err_o[0], "oracle_sampled_pairs": 64}
+    if diffusion:
         # semigroup evidence on 8 states: S(0.3) S(0.1) u0 = S(0.4) u0, 6 slices
-        ctx.set_apply_slices(6)
         f8 = torch.arange(8, dtype=torch.int32, device=mask.device)
         half = F.frac_diffusion(V, lam, Fd, f8, pa[:8], torch.full((8,), 0.1, dtype=torch.float64,
                                                                    device=mask.device), ctx=ctx)
         two = F.frac_diffusion(V, lam, half, f8, pa[:8], torch.full((8,), 0.3, dtype=torch.float64,
                                                                     device=mask.device), ctx=ctx)
-        sg = float((torch.linalg.norm(two - U[:, :8], dim=0) / torch.linalg.norm(U[:, :8], dim=0)).max())
-        head = lines[6]
-        head.update({"dtype": "bf16 slices (6 per operand) into fp64",
-                     "config": {"workload": "diffusion192: 192x192 ellipse grid, n=%d, 4096 distinct initial "
-                                            "states, alpha~U(0.1,1.9), t=0.4, mu=1" % p.n,
-                                "n": p.n, "pairs": k, "products": "6 BF16 slices on tcgen05",
-                                "l2_policy": "inputs larger than L2 (V is %.1f GB)" % (8 * p.n * p.n / 1e9)},
-                     "fp64_products": {"value": lines[0]["value"], "ms_per_step": lines[0]["ms_per_step"]},
-                     "accuracy": {"u_rel_l2_vs_fp64_products_max": rel, "semigroup_rel_l2_max": sg,
-                                  "meets_1e-10": bool(rel <= 1e-10)}})
-        print(json.dumps(head), flush=True)
-        return
-    # alpha = 2 evidence: solve with the same V, lambda for 8 forcings, against CG
-    ctx.set_apply_slices(6)
-    f8 = torch.arange(8, dtype=torch.int32, device=mask.device)
-    U2 = F.frac_apply(V, lam, Fd, f8, torch.full((8,), 2.0, dtype=torch.float64, device=mask.device), ctx=ctx)
-    A = _csr(F, mask, p.h, ctx)
-    Ug = _cg(A, Fd[:, :8].contiguous())
-    err2 = float((torch.linalg.norm(U2 - Ug, dim=0) / torch.linalg.norm(Ug, dim=0)).max())
-    d = lines[6].pop("U") - lines[0].pop("U")
-    rel = float((torch.linalg.norm(d, dim=0) / torch.linalg.norm(U, dim=0)).max())
-    head = lines[6]
+        F.frac_diffusion(V, lam, Fd, pf, pa, pt, mu=1.0, ctx=ctx, out=U)
+        acc["semigroup_rel_l2_max"] = float((torch.linalg.norm(two - U[:, :8], dim=0)
+                                             / torch.linalg.norm(U[:, :8], dim=0)).max())
+        workload = ("diffusion192: 192x192 ellipse grid, n=%d, 4096 distinct initial states, alpha~U(0.1,1.9), "
+                    "t=0.4, mu=1" % p.n)
+    else:
+        # alpha = 2 evidence: solve with the same V, lambda for 8 forcings, against CG
+        f8 = torch.arange(8, dtype=torch.int32, device=mask.device)
+        U2 = F.frac_apply(V, lam, Fd, f8, torch.full((8,), 2.0, dtype=torch.float64, device=mask.device), ctx=ctx)
+        A = _csr(F, mask, p.h, ctx)
+        Ug = _cg(A, Fd[:, :8].contiguous())
+        acc["u_rel_l2_alpha2_vs_cg_max"] = float((torch.linalg.norm(U2 - Ug, dim=0) / torch.linalg.norm(Ug, dim=0)).max())
+        workload = "apply192: 192x192 ellipse grid, n=%d, 4096 distinct forcings, alpha~U(0.1,1.9)" % p.n
+    acc["meets_1e-10"] = bool(rel <= 1e-10 and err_o[6] <= 1e-10 and acc.get("u_rel_l2_alpha2_vs_cg_max", 0) <= 1e-10)
     head.update({"dtype": "bf16 slices (6 per operand) into fp64",
-                 "config": {"workload": "apply192: 192x192 ellipse grid, n=%d, 4096 distinct forcings, alpha~U(0.1,1.9)" % p.n,
-                            "n": p.n, "pairs": k, "products": "6 BF16 slices on tcgen05",
+                 "config": {"workload": workload, "n": p.n, "pairs": k, "products": "6 BF16 slices on tcgen05",
                             "l2_policy": "inputs larger than L2 (V is %.1f GB)" % (8 * p.n * p.n / 1e9)},
                  "fp64_products": {"value": lines[0]["value"], "ms_per_step": lines[0]["ms_per_step"]},
-                 "accuracy": {"u_rel_l2_vs_fp64_products_max": rel, "u_rel_l2_alpha2_vs_cg_max": err2,
-                              "meets_1e-10": bool(rel <= 1e-10 and err2 <= 1e-10)}})
-    print(json.dumps(head), flush=True)
-
-
-def run_product_only(args):
-    """The refinement's residual product X^T X (lower triangle, 7 slices) on a
-    seeded N x N matrix, alone: a small case for kernel captures."""
-    import torch
-    import paper_1911_11906_gb300 as F
-    n = args.product_only
-    g = torch.Generator(device="cpu").manual_seed(0)
-    X = (torch.randn(n, n, generator=g, dtype=torch.float64) / n ** 0.5).cuda()
-    C = torch.empty(n, n, dtype=torch.float64, device="cuda").t()
-    ctx = F.Context()
-    for it in range(args.warmup + args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        F.dgemm_ozaki(X.t(), X.t(), trans_a=True, C=C, ctx=ctx)
-        e1.record()
-        torch.cuda.synchronize()
-        if it >= args.warmup:
-            print(json.dumps({"product": f"{n}x{n}x{n}", "slices": 7, "ms": round(e0.elapsed_time(e1), 3)}),
-                  flush=True)
+                 "cuda_graph": graph, "accuracy": acc})
+    return head
 
 
 def main():
@@ -701,15 +808,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="both", choices=["both", "fp64", "mixed"],
                     help="eigendecomposition route(s) to time; the headline is the fastest that meets the FP64 bar")
-    ap.add_argument("--product-only", type=int, default=0, metavar="N",
-                    help="profiling aid: run only FP64-accurate slice products N x N x N (R = X^T X "
-                         "shape), --steps times after --warmup, and print their CUDA-event times")
     ap.add_argument("--jsonl", default="", metavar="PATH",
                     help="also append one JSONL metrics record per timed route to PATH")
     ap.add_argument("--workload", default="ellipse128",
-                    choices=["ellipse128", "batched256", "apply192", "diffusion192"],
-                    help="ellipse128: the headline workload; batched256, apply192 and diffusion192: the "
-                         "batched, apply-at-scale and diffusion-at-scale workloads, one JSON line each")
+                    choices=["ellipse128", "square48", "batched256", "apply192", "diffusion192"],
+                    help="ellipse128: the headline workload (its line also carries the square48, batched256 "
+                         "and apply192 results under 'configs'); the others: that workload alone, one line")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave the other workloads out of the headline line")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="fixed band width and worker count instead of the autotuner's")
     args = ap.parse_args()
     if args.workload != "ellipse128" and args.impl == "fraclap":
         # single-GPU workloads: under torchrun, rank 0 runs them on its own GPU
@@ -718,14 +826,14 @@ def main():
             return
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if args.workload == "square48":
+        print(json.dumps(run_square_bench(args)), flush=True)
+        return
     if args.workload == "batched256":
-        run_batched_bench(args)
+        print(json.dumps(run_batched_bench(args)), flush=True)
         return
     if args.workload in ("apply192", "diffusion192"):
-        run_apply_bench(args, diffusion=args.workload == "diffusion192")
-        return
-    if args.product_only > 0:
-        run_product_only(args)
+        print(json.dumps(run_apply_bench(args, diffusion=args.workload == "diffusion192")), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -237,6 +237,10 @@ void fraclap_graph_destroy(fraclap_graph* g);
  *  caller still owns every input and output.  status_dev: optional int32 on
  *  the device that receives FRACLAP_ERR_NOT_SPD (or INVALID_ARG for a pair
  *  index out of range) from the kernels; it is not cleared by the call.
+ *  With status_dev == NULL those device-side errors are NOT reported: the
+ *  kernels record them in a private word that nothing reads (the affected
+ *  columns of U are still zeroed), so pass a status word whenever lambda or
+ *  the pair indices are not known to be valid.
  *  Returns FRACLAP_ERR_UNSUPPORTED, launching nothing, when the scratch is
  *  too small: n*m rounded up to a multiple of 32, plus n*k, must not exceed
  *  FRACLAP_NOALLOC_MAX_DOUBLES, and k <= 65535.

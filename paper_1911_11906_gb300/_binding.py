@@ -192,14 +192,47 @@ def default_context() -> Context:
     return _default
 
 
-def _f64_colmajor(t: torch.Tensor, name: str) -> torch.Tensor:
-    """Returns a column-major (Fortran-order) float64 CUDA view: ld = t.stride(1)."""
-    if t.dtype != torch.float64 or not t.is_cuda:
+def colmajor_layout_ok(shape, strides) -> bool:
+    """True when a 2-D (rows, cols) layout can be handed to the library as a
+    column-major matrix with leading dimension strides[1]: unit row stride
+    and columns that do not overlap (strides[1] >= rows whenever there is
+    more than one column).  An expanded or otherwise overlapping view fails:
+    the library would read or write rows * cols elements through it."""
+    rows, cols = shape
+    if rows > 1 and cols > 0 and strides[0] != 1:
+        return False
+    if cols > 1 and strides[1] < max(rows, 1):
+        return False
+    return True
+
+
+def _f64_colmajor(t: torch.Tensor, name: str, rows: int | None = None, cols: int | None = None,
+                  device=None) -> torch.Tensor:
+    """Returns a column-major (Fortran-order) float64 CUDA view: ld = t.stride(1).
+    A view whose layout the library cannot walk (transposed, expanded) is
+    copied into a column-major one; rows/cols, when given, must match, and
+    device, when given, must be the tensor's device."""
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
         raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if device is not None and t.device != device:
+        raise TypeError(f"{name} must be on {device}, not {t.device}")
     if t.dim() == 1:
         t = t.unsqueeze(1)
-    if t.stride(0) != 1:
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be a matrix")
+    if (rows is not None and t.shape[0] != rows) or (cols is not None and t.shape[1] != cols):
+        raise ValueError(f"{name} must have shape ({rows if rows is not None else '*'}, "
+                         f"{cols if cols is not None else '*'}), not {tuple(t.shape)}")
+    if not colmajor_layout_ok(tuple(t.shape), t.stride()):
         t = t.t().contiguous().t()
+    return t
+
+
+def _square(t: torch.Tensor, name: str) -> torch.Tensor:
+    """A float64 CUDA matrix that must be square (n x n), column-major."""
+    t = _f64_colmajor(t, name)
+    if t.shape[0] != t.shape[1]:
+        raise ValueError(f"{name} must be square, not {tuple(t.shape)}")
     return t
 
 
@@ -219,8 +252,9 @@ def _out(t: torch.Tensor, dtype, name: str, device, rows: int, cols: int) -> tor
     """A caller-provided output, written in place: column-major, `dtype`, on
     `device`, of shape (rows, cols)."""
     if (not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or t.device != device
-            or tuple(t.shape) != (rows, cols) or (rows > 1 and cols > 0 and t.stride(0) != 1)):
-        raise TypeError(f"{name} must be a column-major {dtype} CUDA tensor of shape ({rows}, {cols}) on {device}")
+            or tuple(t.shape) != (rows, cols) or not colmajor_layout_ok((rows, cols), t.stride())):
+        raise TypeError(f"{name} must be a column-major {dtype} CUDA tensor of shape ({rows}, {cols}) on {device}"
+                        " with non-overlapping columns")
     return t
 
 
@@ -272,7 +306,7 @@ def eig_full(A: torch.Tensor, ctx: Context | None = None, stream=None, workspace
     """All eigenpairs of the symmetric matrix A (lower triangle read).
     Returns (lambda ascending, V column-major)."""
     ctx = ctx or default_context()
-    A = _f64_colmajor(A, "A")
+    A = _square(A, "A")
     n = A.shape[0]
     lam = torch.empty(n, dtype=torch.float64, device=A.device)
     V = empty_colmajor(n, n, A.device)
@@ -295,7 +329,7 @@ def eig_full_mixed(A: torch.Tensor, rowptr: torch.Tensor, col: torch.Tensor, val
     """Mixed-precision decomposition (FP32 stages + Ogita-Aishima refinement).
     A: dense lower triangle; (rowptr, col, val): the same matrix in CSR."""
     ctx = ctx or default_context()
-    A = _f64_colmajor(A, "A")
+    A = _square(A, "A")
     n = A.shape[0]
     rowptr = _dev(rowptr, torch.int64, "rowptr", A.device, n + 1)
     col = _dev(col, torch.int32, "col", A.device)
@@ -321,10 +355,10 @@ def frac_apply(V: torch.Tensor, lam: torch.Tensor, F: torch.Tensor, pair_f, pair
                workspace: torch.Tensor | None = None, sync: bool = True) -> torch.Tensor:
     """u_j = V diag(lam^{-alpha_j/2}) V^T F[:, pair_f[j]]; returns U (n x k, column-major)."""
     ctx = ctx or default_context()
-    V = _f64_colmajor(V, "V")
-    F = _f64_colmajor(F, "F")
+    V = _square(V, "V")
     n = V.shape[0]
     dev = V.device
+    F = _f64_colmajor(F, "F", rows=n, device=dev)
     pf = torch.as_tensor(pair_f, dtype=torch.int32).to(dev).contiguous()
     pa = torch.as_tensor(pair_alpha, dtype=torch.float64).to(dev).contiguous()
     k, m = pf.numel(), F.shape[1]
@@ -351,10 +385,10 @@ def frac_diffusion(V: torch.Tensor, lam: torch.Tensor, U0: torch.Tensor, pair_f,
     """u_j = V diag(exp(-mu lam^{alpha_j/2} t_j)) V^T U0[:, pair_f[j]]: the
     fractional diffusion solution at time t_j; returns U (n x k, column-major)."""
     ctx = ctx or default_context()
-    V = _f64_colmajor(V, "V")
-    U0 = _f64_colmajor(U0, "U0")
+    V = _square(V, "V")
     n = V.shape[0]
     dev = V.device
+    U0 = _f64_colmajor(U0, "U0", rows=n, device=dev)
     pf = torch.as_tensor(pair_f, dtype=torch.int32).to(dev).contiguous()
     pa = torch.as_tensor(pair_alpha, dtype=torch.float64).to(dev).contiguous()
     pt = torch.as_tensor(pair_t, dtype=torch.float64).to(dev).contiguous()
@@ -387,9 +421,9 @@ class ApplyGraph:
     def __init__(self, V: torch.Tensor, lam: torch.Tensor, F: torch.Tensor, pair_f, pair_alpha, pair_t=None,
                  mu: float = 1.0, ctx: Context | None = None, out: torch.Tensor | None = None):
         self.ctx = ctx or default_context()
-        self.V = _f64_colmajor(V, "V")
-        self.F = _f64_colmajor(F, "F")
+        self.V = _square(V, "V")
         n, dev = self.V.shape[0], self.V.device
+        self.F = _f64_colmajor(F, "F", rows=n, device=dev)
         self.lam = _dev(lam, torch.float64, "lam", dev, n)
         self.pair_f = torch.as_tensor(pair_f, dtype=torch.int32).to(dev).contiguous()
         self.pair_alpha = torch.as_tensor(pair_alpha, dtype=torch.float64).to(dev).contiguous()
@@ -432,7 +466,7 @@ class ApplyGraph:
 def tridiagonalize(A: torch.Tensor, want_q: bool = True, ctx: Context | None = None, stream=None):
     """A = Q T Q^T (two-stage reduction).  Returns (d, e, Q or None)."""
     ctx = ctx or default_context()
-    A = _f64_colmajor(A, "A")
+    A = _square(A, "A")
     n = A.shape[0]
     d = torch.empty(n, dtype=torch.float64, device=A.device)
     e = torch.empty(max(n - 1, 1), dtype=torch.float64, device=A.device)
@@ -471,10 +505,12 @@ def dgemm(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, alpha=
     """C = alpha op(A) op(B) + beta C on the library's FP64 GEMM engine."""
     ctx = ctx or default_context()
     A = _f64_colmajor(A, "A")
-    B = _f64_colmajor(B, "B")
+    B = _f64_colmajor(B, "B", device=A.device)
     m = A.shape[1] if trans_a else A.shape[0]
     k = A.shape[0] if trans_a else A.shape[1]
     n = B.shape[0] if trans_b else B.shape[1]
+    if (B.shape[1] if trans_b else B.shape[0]) != k:
+        raise ValueError(f"inner dimensions differ: op(A) is {m} x {k}, op(B) has {B.shape[1] if trans_b else B.shape[0]} rows")
     if C is None:
         C = empty_colmajor(m, n, A.device)
         beta = 0.0
@@ -495,13 +531,15 @@ def sgemm(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, alpha=
     form 2: only the lower triangle of C written."""
     ctx = ctx or default_context()
     for t, name in ((A, "A"), (B, "B")):
-        if t.dtype != torch.float32 or not t.is_cuda:
-            raise TypeError(f"{name} must be a float32 CUDA tensor")
-    A = A if A.stride(0) == 1 else A.t().contiguous().t()
-    B = B if B.stride(0) == 1 else B.t().contiguous().t()
+        if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2 or t.device != A.device:
+            raise TypeError(f"{name} must be a float32 CUDA matrix on A's device")
+    A = A if colmajor_layout_ok(tuple(A.shape), A.stride()) else A.t().contiguous().t()
+    B = B if colmajor_layout_ok(tuple(B.shape), B.stride()) else B.t().contiguous().t()
     m = A.shape[1] if trans_a else A.shape[0]
     k = A.shape[0] if trans_a else A.shape[1]
     n = B.shape[0] if trans_b else B.shape[1]
+    if (B.shape[1] if trans_b else B.shape[0]) != k:
+        raise ValueError("inner dimensions of op(A) and op(B) differ")
     if C is None:
         C = torch.zeros((n, m), dtype=torch.float32, device=A.device).t()
         beta = 0.0
@@ -536,7 +574,7 @@ def solve_batched(problems, workers: int = 0, ctx: Context | None = None, stream
     arr = (_Problem * max(len(problems), 1))()
     keep, out = [], []
     for i, pr in enumerate(problems):
-        A = _f64_colmajor(pr["A"], "A") if pr["A"].numel() else pr["A"]
+        A = _square(pr["A"], f"problem {i}: A") if pr["A"].numel() else pr["A"]
         n = int(pr["A"].shape[0])
         dev = pr["A"].device
         lam = torch.empty(n, dtype=torch.float64, device=dev)
@@ -544,7 +582,7 @@ def solve_batched(problems, workers: int = 0, ctx: Context | None = None, stream
         U = None
         k = 0
         if pr.get("pair_f") is not None and len(pr["pair_f"]) and n:
-            Fm = _f64_colmajor(pr["F"], "F")
+            Fm = _f64_colmajor(pr["F"], f"problem {i}: F", rows=n, device=dev)
             pf = torch.as_tensor(np.asarray(pr["pair_f"], dtype=np.int32)).to(dev)
             pa = torch.as_tensor(np.asarray(pr["pair_alpha"], dtype=np.float64)).to(dev)
             k = int(pf.numel())
@@ -578,10 +616,12 @@ def dgemm_ozaki(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, 
     """C = alpha op(A) op(B) + beta C, FP64-accurate from BF16 tensor-core slices."""
     ctx = ctx or default_context()
     A = _f64_colmajor(A, "A")
-    B = _f64_colmajor(B, "B")
+    B = _f64_colmajor(B, "B", device=A.device)
     m = A.shape[1] if trans_a else A.shape[0]
     k = A.shape[0] if trans_a else A.shape[1]
     n = B.shape[0] if trans_b else B.shape[1]
+    if (B.shape[1] if trans_b else B.shape[0]) != k:
+        raise ValueError(f"inner dimensions differ: op(A) is {m} x {k}, op(B) has {B.shape[1] if trans_b else B.shape[0]} rows")
     if C is None:
         C = empty_colmajor(m, n, A.device)
         beta = 0.0

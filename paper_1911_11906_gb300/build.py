@@ -62,6 +62,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
             for msg in ex.map(compile_one, jobs):
                 if verbose and msg:
                     print(msg)
+    if verbose:
+        print(f"compiled {len(jobs)} of {len(sources())} CUDA sources for sm_103a"
+              + (": " + " ".join(os.path.basename(j[0]) for j in jobs) if jobs else " (all objects current)"))
     objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in sources()]
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
@@ -70,6 +73,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stderr)
         os.replace(tmp, LIB)
+        if verbose:
+            print(f"linked {LIB}")
     return LIB
 
 

@@ -207,11 +207,11 @@ extern "C" int frac_apply_noalloc(const double* V_dev, int64_t ldv, const double
   if (m < 1 || !V_dev || !lambda_dev || !F_dev || !pair_f_dev || !pair_alpha_dev || !U_dev)
     return FRACLAP_ERR_INVALID_ARG;
   if (ldv < n || ldf < n || ldu < n) return FRACLAP_ERR_INVALID_ARG;
-  // the scratch holds W (n x m) and C (n x k), each starting on a 256-byte boundary
+  // the scratch holds W (n x m) and C (n x k), each starting on a 256-byte
+  // boundary; the bounds are checked before any product of sizes is formed
+  if (m > kNoAllocDoubles || k > 65535 || n > kNoAllocDoubles / (m + k)) return FRACLAP_ERR_UNSUPPORTED;
   const int64_t wlen = ((n * m + 31) / 32) * 32;
-  if (m > kNoAllocDoubles || k > 65535 || n > kNoAllocDoubles / (m + k) ||
-      wlen + n * k > kNoAllocDoubles)
-    return FRACLAP_ERR_UNSUPPORTED;
+  if (wlen + n * k > kNoAllocDoubles) return FRACLAP_ERR_UNSUPPORTED;
   double* scratch = nullptr;
   int32_t* own_status = nullptr;
   const int rc = noalloc_setup(&scratch, &own_status);
@@ -263,9 +263,14 @@ extern "C" int fraclap_apply_graph_create(fraclap_ctx* ctx, const double* V_dev,
     return set_error(ctx, FRACLAP_ERR_CUDA, "apply_graph: begin capture: %s", cudaGetErrorString(e));
   }
   const long long before = ctx->launches;
+  // no stage events inside the capture: events recorded there belong to the
+  // graph and could not be read back by fraclap_stage_times
+  const bool profiling = ctx->profiling;
+  ctx->profiling = false;
   const int rc = spectral_apply(ctx, pair_t_dev ? "apply_graph(diffusion)" : "apply_graph", V_dev, ldv,
                                 lambda_dev, n, F_dev, ldf, m, pair_f_dev, pair_alpha_dev, pair_t_dev, mu, k,
                                 U_dev, ldu, work_dev, work_bytes, s);
+  ctx->profiling = profiling;
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(s, &g);
   cudaStreamDestroy(s);

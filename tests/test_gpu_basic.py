@@ -174,17 +174,10 @@ def _f32_colmajor(a):
     return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32).T)).cuda().t()
 
 
-@pytest.mark.parametrize("route", [1, 0])
-@pytest.mark.parametrize("form", [0, 1, 2])
-@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
-@pytest.mark.parametrize("m,n,k", [(128, 64, 64), (130, 70, 300), (300, 257, 1000), (1000, 129, 64), (64, 40, 30)])
-def test_sgemm_fp32_accurate(route, form, ta, tb, m, n, k):
+def _sgemm_case(route, form, ta, tb, m, n, k):
     """FP32 GEMM (tensor-core route: three TF32 products; FMA route) against an
     FP64 product of the same FP32 inputs, relative to sum_k |a_ik| |b_kj|."""
     F = _F()
-    if form == 1:
-        if ta or m != k:
-            pytest.skip("symmetric A is square and untransposed")
     rng = np.random.default_rng(m * 7 + n * 3 + k + form)
     A = rng.standard_normal((k, m) if ta else (m, k)).astype(np.float32)
     if form == 1:
@@ -209,6 +202,25 @@ def test_sgemm_fp32_accurate(route, form, ta, tb, m, n, k):
     assert np.max(np.abs(got - ref) / scale) <= 4e-6
 
 
+@pytest.mark.parametrize("route", [1, 0])
+@pytest.mark.parametrize("form", [0, 2])
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("m,n,k", [(128, 64, 64), (130, 70, 300), (300, 257, 1000), (1000, 129, 64), (64, 40, 30)])
+def test_sgemm_fp32_accurate(route, form, ta, tb, m, n, k):
+    """Plain (form 0) and lower-triangular-C (form 2) FP32 products."""
+    _sgemm_case(route, form, ta, tb, m, n, k)
+
+
+@pytest.mark.parametrize("route", [1, 0])
+@pytest.mark.parametrize("tb", [False, True])
+@pytest.mark.parametrize("m,n", [(128, 64), (256, 96), (520, 130), (1000, 257), (64, 40)])
+def test_sgemm_fp32_symmetric_a(route, tb, m, n):
+    """Symmetric A read from its lower triangle (form 1, the SYMM of the band
+    reduction): square and untransposed by definition, garbage above the
+    diagonal that must not be read."""
+    _sgemm_case(route, 1, False, tb, m, n, m)
+
+
 @pytest.mark.parametrize("slices,tol", [(7, 1e-13), (5, 1e-10), (3, 1e-5)])
 def test_frac_apply_tensor_slices(square_small, slices, tol):
     """frac_apply with its products as BF16 slices on the tensor cores,
@@ -222,3 +234,30 @@ def test_frac_apply_tensor_slices(square_small, slices, tol):
     U = F.frac_apply(_colmajor(V), _cuda(lam), _colmajor(p.F), p.pair_f, p.pair_alpha, ctx=ctx).cpu().numpy()
     for j in range(U_o.shape[1]):
         assert np.linalg.norm(U[:, j] - U_o[:, j]) <= tol * np.linalg.norm(U_o[:, j])
+
+
+def test_binding_refuses_bad_shapes_and_devices():
+    """Shapes and devices the library cannot take are refused before any
+    call: a non-square V or A, forcings with the wrong row count or on the
+    host, an expanded (overlapping) output; a transposed or expanded input is
+    copied into a column-major one instead."""
+    import paper_1911_11906_gb300 as F
+    n = 6
+    V = torch.eye(n, dtype=torch.float64, device="cuda")
+    lam = torch.ones(n, dtype=torch.float64, device="cuda")
+    Fd = torch.ones(n, 2, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        F.frac_apply(V[:, :4], lam, Fd, [0], [1.0])
+    with pytest.raises(ValueError):
+        F.frac_apply(V, lam, Fd[:4], [0], [1.0])
+    with pytest.raises(TypeError):
+        F.frac_apply(V, lam, Fd.cpu(), [0], [1.0])
+    with pytest.raises(ValueError):
+        F.eig_full(torch.ones(n, n - 1, dtype=torch.float64, device="cuda"))
+    out = torch.empty(n, 1, dtype=torch.float64, device="cuda").expand(n, 2)
+    with pytest.raises(TypeError):
+        F.frac_apply(V, lam, Fd, [0, 1], [1.0, 1.0], out=out)
+    # an expanded input is read through a column-major copy: alpha = 0 returns it
+    col = torch.arange(n, dtype=torch.float64, device="cuda").unsqueeze(1).expand(n, 2)
+    U = F.frac_apply(V, lam, col, [0, 1], [0.0, 0.0])
+    assert torch.equal(U, col)

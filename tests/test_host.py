@@ -195,27 +195,6 @@ def test_reference_arm_other_ranks_do_nothing(capsys):
     assert capsys.readouterr().out == ""
 
 
-def test_ncu_launch_list_summary(tmp_path):
-    """The launch-list summary used for the committed profiles: per-kernel
-    launch counts, total device time and share, with ncu's name decoration
-    and units handled."""
-    from paper_1911_11906_gb300 import ncu_summary
-    hdr = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
-           '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n')
-    rows = [("void fraclap::<unnamed>::k1<float, 4>(float *, long)", "ns", "3,000"),
-            ("fraclap::<unnamed>::k2(double *)", "us", "1.5"),
-            ("void fraclap::<unnamed>::k1<float, 4>(float *, long)", "ns", "1000"),
-            ("fraclap::<unnamed>::k2(double *)", "ms", "0.0045")]
-    body = "".join(f'"{i}","1","p","h","{k}","1","7","(256, 1, 1)","(4, 1, 1)","0","10.3","x",'
-                   f'"gpu__time_duration.sum","{u}","{v}"\n' for i, (k, u, v) in enumerate(rows))
-    path = tmp_path / "l.csv"
-    path.write_text("==PROF== Connected\n" + hdr + body)
-    lines = ncu_summary.summarize([str(path)]).splitlines()
-    assert lines[1].split()[:3] == ["k2", "2", "0.006"] and lines[1].endswith("60.00%")
-    assert lines[2].split()[:3] == ["k1<float,", "4>", "2"] and lines[2].endswith("40.00%")
-    assert lines[-1].split()[:3] == ["TOTAL", "4", "0.010"]
-
-
 def test_bench_jsonl_records():
     sys.path.insert(0, ROOT)
     import bench
@@ -262,3 +241,27 @@ def test_binding_input_guards():
                  lambda: B._ws(torch.empty(8, dtype=torch.uint8), dev)):
         with pytest.raises(TypeError):
             call()
+
+
+def test_binding_layout_guard_refuses_overlapping_columns():
+    """The layout the binding hands to the library must be column-major with
+    non-overlapping columns: an expanded output (stride 0 along the columns)
+    or a column stride below the row count would make the library write or
+    read rows x cols elements through too little storage."""
+    torch = pytest.importorskip("torch")
+    from paper_1911_11906_gb300._binding import colmajor_layout_ok as ok
+    n, k = 5, 3
+    base = torch.empty(k, n, dtype=torch.float64).t()          # column-major n x k
+    assert ok(tuple(base.shape), base.stride())
+    expanded = torch.empty(n, 1, dtype=torch.float64).expand(n, k)
+    assert expanded.stride() == (1, 0) and not ok(tuple(expanded.shape), expanded.stride())
+    rowmajor = torch.empty(n, k, dtype=torch.float64)
+    assert not ok(tuple(rowmajor.shape), rowmajor.stride())
+    short = torch.empty(20, dtype=torch.float64).as_strided((n, k), (1, 2))  # columns overlap
+    assert not ok(tuple(short.shape), short.stride())
+    padded = torch.empty(k, n + 3, dtype=torch.float64).t()[:n]  # ld = n + 3 >= n
+    assert ok(tuple(padded.shape), padded.stride())
+    one_col = torch.empty(n, 1, dtype=torch.float64)           # a single column: any column stride
+    assert ok(tuple(one_col.shape), one_col.stride())
+    assert ok((1, k), (k, 1)) and ok((1, k), (1, 1))           # one row: columns one element apart
+    assert not ok((1, k), (1, 0))                               # ... but not all the same element

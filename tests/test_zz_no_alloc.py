@@ -3,8 +3,9 @@ device memory (code running inside another framework's memory pool, or
 latency-critical loops that cannot afford cudaMalloc's implicit device
 synchronisation).  Its scratch is a fixed array inside the library, shared
 by every call, so this test checks that two calls in a row, each through the
-C ABI, reproduce the allocating frac_apply entry point on different inputs
-(nothing stale from the first call may leak into the second), and that a
+C ABI, reproduce the allocating frac_apply entry point and the oracle's
+apply on different inputs (nothing stale from the first call may leak into
+the second), and that a
 problem too large for the array is refused without launching anything.
 
 This file is collected last on purpose: if it fails, a run that stops at the
@@ -67,6 +68,10 @@ def test_noalloc_matches_frac_apply_on_two_calls():
         got = U.cpu().numpy()
         for j in range(ref.shape[1]):
             assert np.linalg.norm(got[:, j] - ref[:, j]) <= 1e-13 * np.linalg.norm(ref[:, j])
+        # and the oracle's apply of the same (V, lambda): the definition of the result
+        U_o = O.frac_apply(V, lam, p.F, p.pair_f, p.pair_alpha)
+        for j in range(U_o.shape[1]):
+            assert np.linalg.norm(got[:, j] - U_o[:, j]) <= 1e-12 * np.linalg.norm(U_o[:, j])
 
 
 def test_noalloc_refuses_oversized_problems():
