@@ -272,6 +272,7 @@ def run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier, steps=
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_1911_11906_gb300 as F
+    from paper_1911_11906_gb300 import autotune
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -293,11 +294,15 @@ def run_gpu(args, rank, world, local_rank):
     band = dict(BAND)
     band_src = {pth: "fixed" for pth in band}
     if "mixed" in paths and not args.no_autotune:
-        from paper_1911_11906_gb300 import autotune
         band["mixed"] = autotune.best_band_width(n, "mixed")
         band_src["mixed"] = "autotuner (cache %s)" % autotune.default_cache_path()
+    sched = {}
+    if "mixed" in paths and not args.no_autotune:
+        sched = autotune.best_ozaki_schedule(n, slices=7)
     for path in paths:
         ctx = F.Context(band_width=band[path])
+        if path == "mixed" and sched:
+            autotune.apply_schedule(ctx, sched)
         app_ws = torch.empty(ctx.lib.fraclap_apply_workspace_bytes(n, Fd.shape[1], k), dtype=torch.uint8, device=dev)
         # the FP64 route is the comparison when both run: fewer timed steps (it is 6x slower)
         short = path == "fp64" and len(paths) > 1
@@ -411,6 +416,8 @@ def run_gpu(args, rank, world, local_rank):
             "accuracy": r["acc"],
             "band_width": band[pth], "band_width_source": band_src[pth],
         }
+        if pth == "mixed" and sched:
+            line["paths"][pth]["slice_product_schedule"] = dict(sched, source="autotuner")
         if r["refine"]:
             line["paths"][pth]["refine_iterations"] = len(r["refine"])
             line["paths"][pth]["refine_last"] = {kk: float("%.3e" % vv) for kk, vv in r["refine"][-1].items()}

@@ -439,6 +439,23 @@ int fraclap_dgemm_ozaki(fraclap_ctx* ctx, int trans_a, int trans_b, int64_t m, i
                         int64_t ldc, int slices, void* work_dev, size_t work_bytes,
                         fraclap_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Schedule knobs of a context (tile orders and digit widths; the results do
+ * not depend on them beyond rounding), measured and picked by the autotuner
+ * of the Python package.  fraclap_set_schedule returns FRACLAP_ERR_INVALID_ARG
+ * for an unknown knob or a value outside its range; fraclap_get_schedule
+ * returns the current value (or FRACLAP_ERR_INVALID_ARG).
+ *  FRACLAP_SCHED_OZAKI_GROUP: tile rows per raster group of the slice-product
+ *    kernel (fraclap_dgemm_ozaki, the refinement's residual products, the
+ *    sliced apply), 0..4096; 0 = every tile row in one group [8].
+ *  FRACLAP_SCHED_OZAKI_BITS: digit width of the slices when K > 256: 7
+ *    (exact chunks of 1024, ceil(8 s / 7) digits per operand) or 8 (exact
+ *    chunks of 256, s digits: fewer slice pairs, more chunk sums) [7].
+ * ---------------------------------------------------------------------- */
+enum { FRACLAP_SCHED_OZAKI_GROUP = 0, FRACLAP_SCHED_OZAKI_BITS = 1 };
+int fraclap_set_schedule(fraclap_ctx* ctx, int knob, int value);
+int fraclap_get_schedule(const fraclap_ctx* ctx, int knob);
+
 #ifdef __cplusplus
 }
 #endif

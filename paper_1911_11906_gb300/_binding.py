@@ -58,6 +58,8 @@ SIGNATURES = {
     "fraclap_solve_batched": (_i32, [_p, _p, _i32, _i32, _p]),
     "fraclap_apply_workspace_bytes_ctx": (ctypes.c_size_t, [_p, _i64, _i64, _i64]),
     "fraclap_set_apply_slices": (_i32, [_p, _i32]),
+    "fraclap_set_schedule": (_i32, [_p, _i32, _i32]),
+    "fraclap_get_schedule": (_i32, [_p, _i32]),
     "fraclap_sgemm": (_i32, [_p, _i32, _i32, _i32, _i64, _i64, _i64, ctypes.c_float, _p, _i64, _p, _i64,
                              ctypes.c_float, _p, _i64, _i32, _p, ctypes.c_size_t, _p]),
 }
@@ -164,6 +166,15 @@ class Context:
     def set_apply_slices(self, slices: int):
         """frac_apply products: 0 = FP64 engine; s = 1..8 BF16 slices on the tensor cores."""
         self.check(self.lib.fraclap_set_apply_slices(self.handle, int(slices)))
+
+    SCHEDULE_KNOBS = {"ozaki_group": 0, "ozaki_bits": 1}
+
+    def set_schedule(self, knob: str, value: int):
+        """Sets a schedule knob of the context (see SCHEDULE_KNOBS)."""
+        self.check(self.lib.fraclap_set_schedule(self.handle, self.SCHEDULE_KNOBS[knob], int(value)))
+
+    def get_schedule(self, knob: str) -> int:
+        return int(self.lib.fraclap_get_schedule(self.handle, self.SCHEDULE_KNOBS[knob]))
 
     def set_tensor_route(self, route: int):
         """1: tcgen05 + TMA slice products (default); 0: mma.sync."""

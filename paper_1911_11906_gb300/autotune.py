@@ -1,7 +1,8 @@
 """Autotuner for the library's schedule choices, with a persistent cache.
 
 A choice (the half-bandwidth b of the dense-to-band stage for a route and
-size, the number of concurrent workers of the batched solver) is measured
+size, the number of concurrent workers of the batched solver, the tile
+order and digit width of the slice-product kernel) is measured
 once per device and problem class: every candidate runs `reps` times after
 one untimed run, the median device time wins, and the result is kept in a
 JSON cache file so later processes reuse it without measuring.
@@ -159,3 +160,47 @@ def best_workers(problems: list, candidates=(4, 8, 16, 32), tuner: Autotuner | N
     ctx = B.Context()
     return tuner.choose("batched_workers", fields, candidates,
                         lambda w: _event_seconds(lambda: B.solve_batched(problems, workers=int(w), ctx=ctx)), reps)
+
+
+def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7, 8),
+                        tuner: Autotuner | None = None, reps: int = 2) -> dict:
+    """Tile order (raster group of tile rows) and digit width of the
+    slice-product kernel for the refinement's residual product X^T X of an
+    n x n X with `slices` BF16 slices, measured on a seeded matrix of that
+    size through fraclap_dgemm_ozaki.  Returns {"ozaki_group": G,
+    "ozaki_bits": w}; apply it with apply_schedule(ctx, ...)."""
+    import torch
+    from . import _binding as B
+    tuner = tuner or Autotuner()
+    cands = [f"{g}/{w}" for w in bits for g in groups]
+    fields = {"device": _device_name(), "n_bucket": size_bucket(n), "slices": int(slices)}
+    hit = tuner.lookup("ozaki_schedule", fields, cands)
+    if hit is None:
+        gen = torch.Generator(device="cpu").manual_seed(n)
+        X = (torch.randn(n, n, generator=gen, dtype=torch.float64) / n ** 0.5).cuda()
+        C = torch.empty(n, n, dtype=torch.float64, device="cuda").t()
+        ctx = B.Context()
+        ws = torch.empty(ctx.lib.fraclap_dgemm_ozaki_workspace_bytes(n, n, n, slices), dtype=torch.uint8,
+                         device="cuda")
+
+        def measure(c):
+            g, w = (int(x) for x in c.split("/"))
+            ctx.set_schedule("ozaki_group", g)
+            ctx.set_schedule("ozaki_bits", w)
+
+            def run():
+                import ctypes
+                st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+                ctx.check(ctx.lib.fraclap_dgemm_ozaki(ctx.handle, 1, 0, n, n, n, 1.0, B._ptr(X), n, B._ptr(X), n,
+                                                      0.0, B._ptr(C), n, int(slices), B._ptr(ws), ws.numel(), st))
+            return _event_seconds(run)
+
+        hit = tuner.choose("ozaki_schedule", fields, cands, measure, reps)
+    g, w = (int(x) for x in hit.split("/"))
+    return {"ozaki_group": g, "ozaki_bits": w}
+
+
+def apply_schedule(ctx, schedule: dict) -> None:
+    """Sets every knob of `schedule` ({knob: value}) on a binding Context."""
+    for knob, value in schedule.items():
+        ctx.set_schedule(knob, value)

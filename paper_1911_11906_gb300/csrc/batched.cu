@@ -54,7 +54,15 @@ int ensure_workers(fraclap_ctx* ctx, int W) {
   }
   if (!ctx->batch_start) FL_CUDA(ctx, cudaEventCreateWithFlags(&ctx->batch_start, cudaEventDisableTiming));
   const int share = std::max(8, ctx->sm_count / W);
-  for (int i = 0; i < W; ++i) ctx->workers[i]->sm_count = share;
+  for (int i = 0; i < W; ++i) {
+    fraclap_ctx* w = ctx->workers[i];
+    w->sm_count = share;
+    // the caller's settings of the kernels' routes and schedules hold for its workers
+    w->tensor_route = ctx->tensor_route;
+    w->refine_tau = ctx->refine_tau;
+    w->oz_group = ctx->oz_group;
+    w->oz_bits = ctx->oz_bits;
+  }
   return 0;
 }
 

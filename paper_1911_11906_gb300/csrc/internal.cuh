@@ -21,6 +21,8 @@ struct fraclap_ctx {
   int tensor_route = 1;          // slice products: 1 = tcgen05 + TMA, 0 = mma.sync
   double refine_tau = 1e-3;      // first-order coefficient above which a pair is clustered
   int apply_slices = 0;          // frac_apply products: 0 = FP64 engine, s = s BF16 slices (tensor cores)
+  int oz_group = 8;              // slice-product kernel: tile rows per raster group (0 = all rows)
+  int oz_bits = 7;               // slice-product kernel: digit width for K > 256 (7 or 8)
   void* tc_scratch = nullptr;    // split operands of the TF32 tensor-core route of FP32 GEMMs
   size_t tc_scratch_bytes = 0;   // (set by the caller of the FP32 stages, null otherwise)
   long long wait_cycles = 0;     // wait_timeout_s in SM clock cycles (upper bound)

@@ -221,11 +221,46 @@ constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(T
                               ((uint32_t)(TC_M >> 4) << 24);
 // 2^e for e in [-1022, 1023], from its bit pattern.
 __device__ __forceinline__ double pow2i(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+// Order of the output tiles over the CTAs: groups of G consecutive tile rows;
+// inside a group, the G rows of one tile column are consecutive CTAs, then
+// the next column.  The CTAs resident at one time then cover a G x (152 / G)
+// block of tiles, whose A rows and B columns L2 holds while every CTA of the
+// block streams them (in the plain order a wave spans every tile row, so each
+// slice pair re-streams all of A).  With `lower`, a group only has the columns
+// up to its last row: tiles entirely above the diagonal are not enumerated.
+// The host sizes the grid with the same count (ozaki_tile_count).
+__host__ __device__ inline int64_t ozaki_tile_count(int TM, int TN, int G, bool lower) {
+  int64_t tot = 0;
+  for (int g0 = 0; g0 < TM; g0 += G) {
+    const int Gg = (TM - g0 < G) ? TM - g0 : G;
+    tot += (int64_t)Gg * (lower ? ((g0 + Gg < TN) ? g0 + Gg : TN) : TN);
+  }
+  return tot;
+}
+__device__ __forceinline__ void ozaki_tile_of(int64_t idx, int TM, int TN, int G, bool lower, int* tm, int* tn) {
+  int64_t base = 0;
+  for (int g0 = 0; g0 < TM; g0 += G) {
+    const int Gg = (TM - g0 < G) ? TM - g0 : G;
+    const int ncol = lower ? ((g0 + Gg < TN) ? g0 + Gg : TN) : TN;
+    const int64_t cnt = (int64_t)Gg * ncol;
+    if (idx < base + cnt) {
+      const int r = (int)(idx - base);
+      *tn = r / Gg;
+      *tm = g0 + r % Gg;
+      return;
+    }
+    base += cnt;
+  }
+  *tm = TM;  // past the end: no tile
+  *tn = 0;
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const int* __restrict__ ea, const int* __restrict__ eb, int64_t M, int64_t N, int64_t Kp,
                 int s, int bits, int64_t chunk, double alpha, double beta, double* C, int64_t ldc,
-                int lower, long long limit,
+                int lower, int group, long long limit,
                 int32_t* status) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -234,7 +269,11 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * TC_M, n0 = (int64_t)blockIdx.y * TC_N;
+  const int TM = (int)((M + TC_M - 1) / TC_M), TN = (int)((N + TC_N - 1) / TC_N);
+  int tm, tn;
+  ozaki_tile_of((int64_t)blockIdx.x, TM, TN, group, lower != 0, &tm, &tn);
+  if (tm >= TM || tn >= TN) return;
+  const int64_t m0 = (int64_t)tm * TC_M, n0 = (int64_t)tn * TC_N;
   if (lower && m0 + TC_M - 1 < n0) return;  // whole CTA: tile above the diagonal
   const int nchunk = (int)((Kp + chunk - 1) / chunk);
 
@@ -471,7 +510,7 @@ int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t
   // slice width: 8 bits (exact chunks of 256) for short K, else 7 bits (exact
   // chunks of 1024) with one more slice for the same 8s bits: 3x fewer folds.
   int bits = 8, sl = s;
-  if (K > 256) {
+  if (K > 256 && ctx->oz_bits != 8) {
     bits = 7;
     sl = (8 * s + 6) / 7;
   }
@@ -492,9 +531,13 @@ int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t
              FRACLAP_ERR_CUDA, "ozaki_gemm: tensor map encoding failed");
     const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
     FL_CUDA(ctx, cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)cdiv(M, TC_M), (unsigned)cdiv(N, TC_N));
-    ozaki_tc_kernel<<<grid, TC_THREADS, smem, st>>>(ma, mb, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C,
-                                                    ldc, lower ? 1 : 0, ctx->wait_cycles, ctx->d_status);
+    const int TM = (int)cdiv(M, TC_M), TN = (int)cdiv(N, TC_N);
+    const int G = std::max(1, std::min(ctx->oz_group > 0 ? ctx->oz_group : TM, TM));
+    const int64_t tiles = ozaki_tile_count(TM, TN, G, lower);
+    FL_CHECK(ctx, tiles <= INT32_MAX, FRACLAP_ERR_UNSUPPORTED, "ozaki_gemm: too many tiles");
+    ozaki_tc_kernel<<<(unsigned)tiles, TC_THREADS, smem, st>>>(ma, mb, ea, eb, M, N, Kp, sl, bits, chunk, alpha,
+                                                               beta, C, ldc, lower ? 1 : 0, G, ctx->wait_cycles,
+                                                               ctx->d_status);
   } else {
     dim3 grid((unsigned)cdiv(M, OZ_BM), (unsigned)cdiv(N, OZ_BN));
     ozaki_kernel<<<grid, OZ_NT, 0, st>>>(SA, SB, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc, lower);
@@ -528,4 +571,29 @@ extern "C" int fraclap_dgemm_ozaki(fraclap_ctx* ctx, int trans_a, int trans_b, i
   FL_TRY(get_workspace(ctx, work_dev, work_bytes, ozaki_ws(m, n, k, slices) + 1024, &ar));
   return ozaki_gemm(ctx, trans_a != 0, trans_b != 0, m, n, k, alpha, A_dev, lda, B_dev, ldb, beta,
                     C_dev, ldc, slices, false, &ar, (cudaStream_t)stream);
+}
+
+extern "C" int fraclap_set_schedule(fraclap_ctx* ctx, int knob, int value) {
+  if (!ctx) return FRACLAP_ERR_INVALID_ARG;
+  switch (knob) {
+    case FRACLAP_SCHED_OZAKI_GROUP:
+      FL_CHECK(ctx, value >= 0 && value <= 4096, FRACLAP_ERR_INVALID_ARG, "set_schedule: group must be 0..4096");
+      ctx->oz_group = value;
+      return 0;
+    case FRACLAP_SCHED_OZAKI_BITS:
+      FL_CHECK(ctx, value == 7 || value == 8, FRACLAP_ERR_INVALID_ARG, "set_schedule: digit width must be 7 or 8");
+      ctx->oz_bits = value;
+      return 0;
+    default:
+      return set_error(ctx, FRACLAP_ERR_INVALID_ARG, "set_schedule: unknown knob %d", knob);
+  }
+}
+
+extern "C" int fraclap_get_schedule(const fraclap_ctx* ctx, int knob) {
+  if (!ctx) return FRACLAP_ERR_INVALID_ARG;
+  switch (knob) {
+    case FRACLAP_SCHED_OZAKI_GROUP: return ctx->oz_group;
+    case FRACLAP_SCHED_OZAKI_BITS: return ctx->oz_bits;
+    default: return FRACLAP_ERR_INVALID_ARG;
+  }
 }

@@ -71,3 +71,16 @@ def test_damaged_cache_starts_empty(tmp_path, monkeypatch):
 def test_size_buckets():
     assert A.size_bucket(8810) == A.size_bucket(8192) != A.size_bucket(16384)
     assert A.size_bucket(1) == 0 and A.size_bucket(0) == 0
+
+
+def test_apply_schedule_sets_every_knob():
+    class FakeCtx:
+        def __init__(self):
+            self.set = {}
+
+        def set_schedule(self, knob, value):
+            self.set[knob] = value
+
+    c = FakeCtx()
+    A.apply_schedule(c, {"ozaki_group": 8, "ozaki_bits": 7})
+    assert c.set == {"ozaki_group": 8, "ozaki_bits": 7}

@@ -32,3 +32,27 @@ def test_band_width_and_workers_are_tuned_and_cached(tmp_path):
                                                         "n_max_bucket": A.size_bucket(max(p["A"].shape[0] for p in probs)),
                                                         "n_sum_bucket": A.size_bucket(sum(p["A"].shape[0] for p in probs)),
                                                         "mixed": 0}, (2, 3)) == w
+
+
+def test_ozaki_schedule_is_tuned_cached_and_applied(tmp_path):
+    """The slice-product schedule (raster group, digit width) is measured
+    over the candidates, cached, answered from the cache by a second tuner,
+    and set on a context, whose products stay FP64-accurate."""
+    from paper_1911_11906_gb300 import autotune as A
+    import paper_1911_11906_gb300 as F
+    path = str(tmp_path / "tune.json")
+    sched = A.best_ozaki_schedule(640, groups=(0, 2), bits=(7, 8), tuner=A.Autotuner(path), reps=1)
+    assert sched["ozaki_group"] in (0, 2) and sched["ozaki_bits"] in (7, 8)
+    entries = json.load(open(path))["entries"]
+    (val,) = [v for k, v in entries.items() if k.startswith("ozaki_schedule:")]
+    assert set(val["seconds"]) == {"0/7", "2/7", "0/8", "2/8"}
+    assert A.best_ozaki_schedule(700, groups=(0, 2), bits=(7, 8), tuner=A.Autotuner(path)) == sched
+    ctx = F.Context()
+    A.apply_schedule(ctx, sched)
+    assert ctx.get_schedule("ozaki_group") == sched["ozaki_group"]
+    rng = np.random.default_rng(640)
+    X = rng.standard_normal((640, 300))
+    got = F.dgemm_ozaki(torch.from_numpy(X.T.copy()).cuda().t(), torch.from_numpy(X.T.copy()).cuda().t(),
+                        trans_a=True, ctx=ctx).cpu().numpy()
+    scale = np.abs(X).max(axis=0)[:, None] * np.abs(X).max(axis=0)[None, :] * 640
+    assert np.max(np.abs(got - X.T @ X) / scale) <= 1e-15

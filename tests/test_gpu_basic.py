@@ -139,6 +139,44 @@ def test_dgemm_ozaki_is_fp64_accurate(ta, tb, m, n, k):
     assert np.max(np.abs(got - ref) / (rowmax + 1e-300)) <= 1e-15
 
 
+@pytest.mark.parametrize("group,bits", [(0, 7), (1, 7), (3, 8), (8, 8), (8, 7)])
+@pytest.mark.parametrize("ta,m,n,k", [(True, 300, 260, 1000), (False, 520, 130, 2000), (True, 129, 385, 257)])
+def test_dgemm_ozaki_schedules_agree(group, bits, ta, m, n, k):
+    """Every tile order (raster group) and digit width gives an FP64-accurate
+    product (against math.fsum at sampled entries and the FP64 product
+    everywhere), and tile orders with the same digit width give the same
+    bits: only the order of the tiles over the CTAs differs."""
+    import math
+    F = _F()
+    rng = np.random.default_rng(m + 3 * n + k + group)
+    A = rng.standard_normal((k, m) if ta else (m, k))
+    B = rng.standard_normal((k, n))
+    opA = A.T if ta else A
+    ctx = F.Context(wait_timeout_s=2.0)
+    ctx.set_schedule("ozaki_group", group)
+    ctx.set_schedule("ozaki_bits", bits)
+    assert ctx.get_schedule("ozaki_group") == group and ctx.get_schedule("ozaki_bits") == bits
+    got = F.dgemm_ozaki(_colmajor(A), _colmajor(B), trans_a=ta, ctx=ctx).cpu().numpy()
+    scale = np.abs(opA).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * k
+    assert np.max(np.abs(got - opA @ B) / scale) <= 1e-15
+    for (i, j) in [(0, 0), (m - 1, n - 1), (m // 2, n // 3), (m - 1, 0)]:
+        assert abs(got[i, j] - math.fsum(opA[i, :] * B[:, j])) <= 4e-16 * scale[i, j]
+    ref_ctx = F.Context(wait_timeout_s=2.0)
+    ref_ctx.set_schedule("ozaki_group", 0)
+    ref_ctx.set_schedule("ozaki_bits", bits)
+    same = F.dgemm_ozaki(_colmajor(A), _colmajor(B), trans_a=ta, ctx=ref_ctx).cpu().numpy()
+    assert np.array_equal(got, same)
+
+
+def test_schedule_knobs_reject_bad_values():
+    F = _F()
+    ctx = F.Context()
+    for knob, bad in (("ozaki_group", -1), ("ozaki_bits", 6), ("ozaki_bits", 9)):
+        with pytest.raises(F.FraclapError):
+            ctx.set_schedule(knob, bad)
+    assert ctx.lib.fraclap_set_schedule(ctx.handle, 99, 1) == -1
+
+
 def test_dgemm_ozaki_fewer_slices_bound():
     F = _F()
     rng = np.random.default_rng(5)
