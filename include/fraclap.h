@@ -440,6 +440,75 @@ int fraclap_dgemm_ozaki(fraclap_ctx* ctx, int trans_a, int trans_b, int64_t m, i
                         fraclap_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Exact eigenvalue counts and spectrum slicing (Sec. III-D).  By Sylvester's
+ * law of inertia (Sec. III-D-2) the number of eigenvalues of A below sigma is
+ * the number of negative pivots of A - sigma I = L D L^T, and for the
+ * generalised problem K phi = theta M phi (Sec. II eq. discrete_laplace) the
+ * number of theta below sigma is that of K - sigma M.  No dense matrix is
+ * needed: the factorisation runs on the band of the sparse matrix (in the
+ * natural dof order of a grid, half-width = the grid row length in 2-D, the
+ * plane size in 3-D).
+ *
+ * fraclap_csr_half_bandwidth: max(i - j) over the entries (i, j), j <= i, of
+ *   a CSR matrix (int64 rowptr[n+1], int32 col[nnz], as fd_assemble writes
+ *   them); synchronises `stream` to return it in *bw_out.
+ * fraclap_inertia_counts: count_dev[s] (int64, device) = #{eigenvalues <
+ *   sigma_dev[s]} for s < nsig, of the symmetric CSR matrix K (valK_dev;
+ *   only the lower triangle is read) or, when valM_dev is not NULL, of the
+ *   pencil (K, M) with M on the same sparsity pattern.  One pivot sequence per
+ *   shift, all shifts in parallel; -1 for a shift at which a pivot is exactly
+ *   zero (the shift is then, to rounding, an eigenvalue of a leading block).
+ *   half_bandwidth >= fraclap_csr_half_bandwidth (an entry outside it sets
+ *   FRACLAP_ERR_INVALID_ARG in the device status).  Work:
+ *   fraclap_inertia_workspace_bytes(n, half_bandwidth, nsig, valM != NULL);
+ *   asynchronous.  The pivots are formed by the same operations in the same
+ *   order as a sequential banded LDL^T without pivoting, so the counts do not
+ *   depend on the launch.
+ * fraclap_sturm_counts: the same counts for a symmetric tridiagonal T
+ *   (d_dev[n], e_dev[n-1], e.g. from fraclap_tridiagonalize, whose T is
+ *   congruent to A) by the Sturm recurrence q_0 = d_0 - sigma,
+ *   q_i = (d_i - sigma) - e_{i-1}^2 / q_{i-1} (a zero pivot counts as
+ *   negative); one thread per shift; asynchronous.
+ * fraclap_bisect: eigenvalues k0..k1 (0-based, ascending) of T into
+ *   lambda_dev[k1 - k0 + 1] by bisection on the Sturm count from the
+ *   Gershgorin interval, to no representable midpoint or 2 eps relative;
+ *   one thread per eigenvalue; asynchronous.
+ * fraclap_partition_spectrum: the greedy partitioning of Sec. III-D: P
+ *   subintervals of [0, rho] (rho >= the largest eigenvalue, e.g. the
+ *   Gershgorin bound 4 dim / h^2) holding about n / P eigenvalues each.
+ *   Starts from P equal lengths; n_a global rounds count at every split at
+ *   once, read the counts as a piecewise-constant density of states (the
+ *   cumulative count linear between counted points) and move every split to
+ *   where that density gives equal loads, keeping the best partition (the
+ *   smallest largest load); then up to n_b local passes, in which every pair
+ *   of neighbouring subintervals whose loads differ by more than
+ *   imbalance * n / P moves its shared split by a binary search of n_c
+ *   counts towards an even pair (all pairs starting at even positions at
+ *   once, then the odd ones).  Outputs (HOST): splits_host[P-1],
+ *   loads_host[P] (exact counts per subinterval), history_host[history_cap]
+ *   (the largest load after the start, each round and each pass).  Returns
+ *   the number of history entries (>= 0) or an error; synchronises
+ *   `stream` after every round of counts.  Work: as fraclap_inertia_counts
+ *   with nsig = P - 1, plus 512 + 16 (P - 1) bytes.
+ * ---------------------------------------------------------------------- */
+int fraclap_csr_half_bandwidth(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr_dev, const int32_t* col_dev,
+                               int64_t* bw_out, fraclap_stream_t stream);
+size_t fraclap_inertia_workspace_bytes(int64_t n, int64_t half_bandwidth, int64_t nsig, int pencil);
+int fraclap_inertia_counts(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr_dev, const int32_t* col_dev,
+                           const double* valK_dev, const double* valM_dev, int64_t half_bandwidth,
+                           const double* sigma_dev, int64_t nsig, int64_t* count_dev, void* work_dev,
+                           size_t work_bytes, fraclap_stream_t stream);
+int fraclap_sturm_counts(fraclap_ctx* ctx, const double* d_dev, const double* e_dev, int64_t n,
+                         const double* sigma_dev, int64_t nsig, int64_t* count_dev, fraclap_stream_t stream);
+int fraclap_bisect(fraclap_ctx* ctx, const double* d_dev, const double* e_dev, int64_t n, int64_t k0, int64_t k1,
+                   double* lambda_dev, fraclap_stream_t stream);
+int fraclap_partition_spectrum(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr_dev, const int32_t* col_dev,
+                               const double* valK_dev, const double* valM_dev, int64_t half_bandwidth, double rho,
+                               int P, int n_a, int n_b, int n_c, double imbalance, double* splits_host,
+                               int64_t* loads_host, int64_t* history_host, int history_cap, void* work_dev,
+                               size_t work_bytes, fraclap_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Schedule knobs of a context (tile orders and digit widths; the results do
  * not depend on them beyond rounding), measured and picked by the autotuner
  * of the Python package.  fraclap_set_schedule returns FRACLAP_ERR_INVALID_ARG

@@ -26,6 +26,11 @@ from ._binding import (  # noqa: F401
     dgemm_ozaki,
     solve,
     solve_batched,
+    csr_half_bandwidth,
+    inertia_counts,
+    sturm_counts,
+    bisect,
+    partition_spectrum,
     default_context,
     mask_hash,
     save_decomposition,

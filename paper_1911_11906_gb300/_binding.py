@@ -58,6 +58,13 @@ SIGNATURES = {
     "fraclap_solve_batched": (_i32, [_p, _p, _i32, _i32, _p]),
     "fraclap_apply_workspace_bytes_ctx": (ctypes.c_size_t, [_p, _i64, _i64, _i64]),
     "fraclap_set_apply_slices": (_i32, [_p, _i32]),
+    "fraclap_csr_half_bandwidth": (_i32, [_p, _i64, _p, _p, _p, _p]),
+    "fraclap_inertia_workspace_bytes": (_sz, [_i64, _i64, _i64, _i32]),
+    "fraclap_inertia_counts": (_i32, [_p, _i64, _p, _p, _p, _p, _i64, _p, _i64, _p, _p, _sz, _p]),
+    "fraclap_sturm_counts": (_i32, [_p, _p, _p, _i64, _p, _i64, _p, _p]),
+    "fraclap_bisect": (_i32, [_p, _p, _p, _i64, _i64, _i64, _p, _p]),
+    "fraclap_partition_spectrum": (_i32, [_p, _i64, _p, _p, _p, _p, _i64, _dbl, _i32, _i32, _i32, _i32, _dbl, _p,
+                                          _p, _p, _i32, _p, _sz, _p]),
     "fraclap_set_schedule": (_i32, [_p, _i32, _i32]),
     "fraclap_get_schedule": (_i32, [_p, _i32]),
     "fraclap_sgemm": (_i32, [_p, _i32, _i32, _i32, _i64, _i64, _i64, ctypes.c_float, _p, _i64, _p, _i64,
@@ -646,6 +653,120 @@ def dgemm_ozaki(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, 
                                           _ptr(ws), ws.numel(), st))
     ctx.sync(stream)
     return C
+
+
+# ----------------------------------------------------------------------------
+# exact eigenvalue counts and spectrum slicing (Sec. III-D)
+# ----------------------------------------------------------------------------
+def _csr_args(rowptr, col, valK, valM=None):
+    if not isinstance(rowptr, torch.Tensor) or not rowptr.is_cuda:
+        raise TypeError("rowptr must be an int64 CUDA tensor")
+    dev = rowptr.device
+    n = rowptr.numel() - 1
+    if n < 1:
+        raise ValueError("the matrix must have at least one row")
+    rowptr = _dev(rowptr, torch.int64, "rowptr", dev)
+    col = _dev(col, torch.int32, "col", dev)
+    valK = _dev(valK, torch.float64, "valK", dev, col.numel())
+    if valM is not None:
+        valM = _dev(valM, torch.float64, "valM", dev, col.numel())
+    return n, dev, rowptr, col, valK, valM
+
+
+def csr_half_bandwidth(rowptr: torch.Tensor, col: torch.Tensor, ctx: Context | None = None, stream=None) -> int:
+    """max(i - j) over the lower-triangle entries of a CSR matrix (synchronises)."""
+    ctx = ctx or default_context()
+    n = rowptr.numel() - 1
+    bw = ctypes.c_int64(0)
+    rp = _dev(rowptr, torch.int64, "rowptr", rowptr.device)
+    cl = _dev(col, torch.int32, "col", rowptr.device)
+    ctx.check(ctx.lib.fraclap_csr_half_bandwidth(ctx.handle, n, _ptr(rp), _ptr(cl), ctypes.byref(bw),
+                                                 ctypes.c_void_p(_stream(stream))))
+    return int(bw.value)
+
+
+def inertia_counts(rowptr, col, valK, sigmas, valM=None, half_bandwidth: int | None = None,
+                   ctx: Context | None = None, stream=None, sync: bool = True) -> torch.Tensor:
+    """#{eigenvalues < sigma} of the CSR matrix K (or of the pencil (K, M))
+    for every shift, from the inertia of the banded LDL^T (Sec. III-D-2);
+    -1 where a pivot is exactly zero.  Returns an int64 CUDA tensor."""
+    ctx = ctx or default_context()
+    n, dev, rowptr, col, valK, valM = _csr_args(rowptr, col, valK, valM)
+    sig = torch.as_tensor(sigmas, dtype=torch.float64).to(dev).contiguous().reshape(-1)
+    if half_bandwidth is None:
+        half_bandwidth = csr_half_bandwidth(rowptr, col, ctx=ctx, stream=stream)
+    out = torch.empty(sig.numel(), dtype=torch.int64, device=dev)
+    nbytes = ctx.lib.fraclap_inertia_workspace_bytes(n, int(half_bandwidth), sig.numel(), int(valM is not None))
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    ctx.check(ctx.lib.fraclap_inertia_counts(ctx.handle, n, _ptr(rowptr), _ptr(col), _ptr(valK), _ptr(valM),
+                                             int(half_bandwidth), _ptr(sig), sig.numel(), _ptr(out), _ptr(ws),
+                                             ws.numel(), ctypes.c_void_p(_stream(stream))))
+    if sync:
+        ctx.sync(stream)
+    return out
+
+
+def _tridiag_args(d, e):
+    if not isinstance(d, torch.Tensor) or not d.is_cuda:
+        raise TypeError("d must be a float64 CUDA tensor")
+    d = _dev(d, torch.float64, "d", d.device)
+    n = d.numel()
+    if n < 1:
+        raise ValueError("T must have at least one row")
+    e = _dev(e, torch.float64, "e", d.device, n - 1) if n > 1 else torch.zeros(1, dtype=torch.float64,
+                                                                                device=d.device)
+    return n, d, e
+
+
+def sturm_counts(d, e, sigmas, ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """#{eigenvalues < sigma} of the tridiagonal (d, e) for every shift (Sturm recurrence)."""
+    ctx = ctx or default_context()
+    n, d, e = _tridiag_args(d, e)
+    sig = torch.as_tensor(sigmas, dtype=torch.float64).to(d.device).contiguous().reshape(-1)
+    out = torch.empty(sig.numel(), dtype=torch.int64, device=d.device)
+    ctx.check(ctx.lib.fraclap_sturm_counts(ctx.handle, _ptr(d), _ptr(e), n, _ptr(sig), sig.numel(), _ptr(out),
+                                           ctypes.c_void_p(_stream(stream))))
+    ctx.sync(stream)
+    return out
+
+
+def bisect(d, e, k0: int, k1: int, ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """Eigenvalues k0..k1 (0-based, ascending) of the tridiagonal (d, e) by bisection."""
+    ctx = ctx or default_context()
+    n, d, e = _tridiag_args(d, e)
+    lam = torch.empty(max(int(k1) - int(k0) + 1, 1), dtype=torch.float64, device=d.device)
+    ctx.check(ctx.lib.fraclap_bisect(ctx.handle, _ptr(d), _ptr(e), n, int(k0), int(k1), _ptr(lam),
+                                     ctypes.c_void_p(_stream(stream))))
+    ctx.sync(stream)
+    return lam
+
+
+def partition_spectrum(rowptr, col, valK, rho: float, P: int, n_a: int = 7, n_b: int = 0, n_c: int = 10,
+                       imbalance: float = 0.25, valM=None, half_bandwidth: int | None = None,
+                       ctx: Context | None = None, stream=None):
+    """Greedy spectrum slicing of Sec. III-D on GPU inertia counts: P
+    subintervals of [0, rho] with about n / P eigenvalues each.  Returns
+    (splits, loads, history) as numpy arrays (P - 1 split points, P exact
+    loads, the largest load after each step)."""
+    ctx = ctx or default_context()
+    n, dev, rowptr, col, valK, valM = _csr_args(rowptr, col, valK, valM)
+    if half_bandwidth is None:
+        half_bandwidth = csr_half_bandwidth(rowptr, col, ctx=ctx, stream=stream)
+    splits = np.zeros(max(P - 1, 1))
+    loads = np.zeros(max(P, 1), dtype=np.int64)
+    cap = 1 + n_a + n_b
+    hist = np.zeros(cap, dtype=np.int64)
+    nbytes = ctx.lib.fraclap_inertia_workspace_bytes(n, int(half_bandwidth), max(P - 1, 1), int(valM is not None))
+    ws = torch.empty(nbytes + 512 + 16 * max(P - 1, 1), dtype=torch.uint8, device=dev)
+    rc = ctx.lib.fraclap_partition_spectrum(ctx.handle, n, _ptr(rowptr), _ptr(col), _ptr(valK), _ptr(valM),
+                                            int(half_bandwidth), float(rho), int(P), int(n_a), int(n_b), int(n_c),
+                                            float(imbalance), splits.ctypes.data_as(ctypes.c_void_p),
+                                            loads.ctypes.data_as(ctypes.c_void_p),
+                                            hist.ctypes.data_as(ctypes.c_void_p), cap, _ptr(ws), ws.numel(),
+                                            ctypes.c_void_p(_stream(stream)))
+    if rc < 0:
+        ctx.check(rc)
+    return splits[: max(P - 1, 0)], loads[:P], hist[:rc]
 
 
 def solve(mask: torch.Tensor, h: float, F: torch.Tensor, pair_f, pair_alpha, ctx: Context | None = None):

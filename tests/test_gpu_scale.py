@@ -4,7 +4,8 @@ launch configuration of the benchmark (band width 64, refinement cap 6).
 
 The oracle decomposes the whole n = 8810 matrix once per module (minutes on
 the host cores), so both routes are compared with it entry by entry: every
-eigenvalue, every one of the 128 solutions, and the full residual and
+eigenvalue (where the two differ by more than 1e-11, the oracle's inertia
+counts decide), every one of the 128 solutions, and the full residual and
 orthogonality of all eigenpairs (formed on the GPU).  The checks that hold
 at any size ride along: every alpha = 2 solution against the oracle's
 banded direct solve, eigenvalue brackets from the oracle's inertia counts,
@@ -85,8 +86,18 @@ def test_full_size_workload(workload, route):
     U = F.frac_apply(V, lam, Fd, p.pair_f, p.pair_alpha, ctx=ctx).cpu().numpy()
     lam_h = lam.cpu().numpy()
     assert np.all(np.diff(lam_h) >= 0)
-    # every eigenvalue and every solution against the oracle's full decomposition
-    assert np.max(np.abs(lam_h - lam_o) / lam_o) <= 1e-11
+    # every eigenvalue against the oracle's full decomposition.  At n = 8810 the
+    # oracle's own rounding error reaches ~ sqrt(n) eps ||A||_2 ~ 1.4e-9 absolute,
+    # about 2.8e-11 of lambda_min, so where the two differ by more than 1e-11
+    # Sylvester's inertia (Sec. III-D-2) decides: the oracle's LDL^T counts must
+    # bracket the GPU eigenvalue at +-1e-11
+    err = np.abs(lam_h - lam_o) / lam_o
+    assert err.max() <= 1e-10, float(err.max())
+    off = np.nonzero(err > 1e-11)[0]
+    assert off.size <= 16, off.size
+    for i in off:
+        assert _bracketed(A, lam_h, int(i)), (int(i), float(err[i]))
+    # every solution against the oracle's
     err_u = np.linalg.norm(U - U_o, axis=0) / np.linalg.norm(U_o, axis=0)
     assert err_u.max() <= 1e-10, (int(err_u.argmax()), float(err_u.max()))
     for j, ref in refs.items():
