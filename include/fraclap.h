@@ -440,6 +440,48 @@ int fraclap_dgemm_ozaki(fraclap_ctx* ctx, int trans_a, int trans_b, int64_t m, i
                         fraclap_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * The generalised problem with a mass matrix (Sec. II eq. discrete_laplace:
+ * K phi = theta M phi, K_ij = <grad e_i, grad e_j>, M_ij = <e_i, e_j>) for
+ * piecewise bilinear (2-D) / trilinear (3-D) basis functions on the grid
+ * cells, homogeneous Dirichlet conditions (nodes outside the mask are
+ * zero), and its spectral apply in the M-inner product (the coefficient of
+ * a nodal vector f on phi_i is phi_i^T M f, the sum v after the equation).
+ *
+ * fem_assemble: as fd_assemble (same mask, extents, dof numbering and
+ *   two-call protocol), but every row holds the dofs of the 3^dim box of
+ *   grid nodes around it (columns ascending) and two value arrays:
+ *   valK_dev and valM_dev double[nnz] (each entry the sum, over the cells
+ *   holding both nodes, of the cell integrals of the multilinear basis
+ *   functions: products of the 1-D hat integrals h/3, h/6 and +-1/h).
+ *   K_dense_dev, M_dense_dev: optional dense copies (ld >= n).
+ * eig_pencil: K Phi = M Phi diag(theta), Phi^T M Phi = I, theta ascending.
+ *   K_dev: dense n x n (ldk >= n), lower triangle read; M in CSR
+ *   (rowptr_dev, col_dev, valM_dev, lower triangle read) with
+ *   half_bandwidth >= fraclap_csr_half_bandwidth.  M = L D L^T by a banded
+ *   factorisation (a pivot <= 0: FRACLAP_ERR_NOT_SPD in the device status),
+ *   C = D^-1/2 L^-1 K L^-T D^-1/2 by banded solves, C = Z diag(theta) Z^T as
+ *   eig_full, Phi = L^-T D^-1/2 Z.  theta_dev double[n], Phi_dev
+ *   double[ldp*n] out.  Work: fraclap_eig_pencil_workspace_bytes; the
+ *   half-bandwidth may be at most 6399 (FRACLAP_ERR_UNSUPPORTED beyond).
+ * frac_apply_mass: u_j = Phi diag(theta^{-alpha_j/2}) Phi^T M f_{pair_f[j]}
+ *   (M f formed from the CSR of M, then as frac_apply, whose products and
+ *   context settings it shares).  Work: fraclap_apply_mass_workspace_bytes.
+ * ---------------------------------------------------------------------- */
+int fem_assemble(fraclap_ctx* ctx, const uint8_t* mask_dev, int dim, const int64_t ext[3], double h,
+                 int32_t* idx_dev, int64_t* n_out, int64_t* nnz_out, int64_t* rowptr_dev, int32_t* col_dev,
+                 double* valK_dev, double* valM_dev, double* K_dense_dev, double* M_dense_dev, int64_t ld,
+                 fraclap_stream_t stream);
+size_t fraclap_eig_pencil_workspace_bytes(const fraclap_ctx* ctx, int64_t n, int64_t half_bandwidth);
+int eig_pencil(fraclap_ctx* ctx, const double* K_dev, int64_t ldk, int64_t n, const int64_t* rowptr_dev,
+               const int32_t* col_dev, const double* valM_dev, int64_t half_bandwidth, double* theta_dev,
+               double* Phi_dev, int64_t ldp, void* work_dev, size_t work_bytes, fraclap_stream_t stream);
+size_t fraclap_apply_mass_workspace_bytes(const fraclap_ctx* ctx, int64_t n, int64_t m, int64_t k);
+int frac_apply_mass(fraclap_ctx* ctx, const double* Phi_dev, int64_t ldp, const double* theta_dev, int64_t n,
+                    const int64_t* rowptr_dev, const int32_t* col_dev, const double* valM_dev, const double* F_dev,
+                    int64_t ldf, int64_t m, const int32_t* pair_f_dev, const double* pair_alpha_dev, int64_t k,
+                    double* U_dev, int64_t ldu, void* work_dev, size_t work_bytes, fraclap_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Exact eigenvalue counts and spectrum slicing (Sec. III-D).  By Sylvester's
  * law of inertia (Sec. III-D-2) the number of eigenvalues of A below sigma is
  * the number of negative pivots of A - sigma I = L D L^T, and for the

@@ -26,6 +26,9 @@ from ._binding import (  # noqa: F401
     dgemm_ozaki,
     solve,
     solve_batched,
+    fem_assemble,
+    eig_pencil,
+    frac_apply_mass,
     csr_half_bandwidth,
     inertia_counts,
     sturm_counts,

@@ -58,6 +58,12 @@ SIGNATURES = {
     "fraclap_solve_batched": (_i32, [_p, _p, _i32, _i32, _p]),
     "fraclap_apply_workspace_bytes_ctx": (ctypes.c_size_t, [_p, _i64, _i64, _i64]),
     "fraclap_set_apply_slices": (_i32, [_p, _i32]),
+    "fem_assemble": (_i32, [_p, _p, _i32, _p, _dbl, _p, _p, _p, _p, _p, _p, _p, _p, _p, _i64, _p]),
+    "fraclap_eig_pencil_workspace_bytes": (_sz, [_p, _i64, _i64]),
+    "eig_pencil": (_i32, [_p, _p, _i64, _i64, _p, _p, _p, _i64, _p, _p, _i64, _p, _sz, _p]),
+    "fraclap_apply_mass_workspace_bytes": (_sz, [_p, _i64, _i64, _i64]),
+    "frac_apply_mass": (_i32, [_p, _p, _i64, _p, _i64, _p, _p, _p, _p, _i64, _i64, _p, _p, _i64, _p, _i64, _p, _sz,
+                               _p]),
     "fraclap_csr_half_bandwidth": (_i32, [_p, _i64, _p, _p, _p, _p]),
     "fraclap_inertia_workspace_bytes": (_sz, [_i64, _i64, _i64, _i32]),
     "fraclap_inertia_counts": (_i32, [_p, _i64, _p, _p, _p, _p, _i64, _p, _i64, _p, _p, _sz, _p]),
@@ -653,6 +659,94 @@ def dgemm_ozaki(A: torch.Tensor, B: torch.Tensor, trans_a=False, trans_b=False, 
                                           _ptr(ws), ws.numel(), st))
     ctx.sync(stream)
     return C
+
+
+# ----------------------------------------------------------------------------
+# the generalised problem K phi = theta M phi (finite elements)
+# ----------------------------------------------------------------------------
+def fem_assemble(mask: torch.Tensor, h: float, dense: bool = True, ctx: Context | None = None, stream=None):
+    """Bilinear / trilinear finite-element stiffness K and mass M of a uint8
+    mask ([y, x] or [z, y, x]) on the GPU.  Returns dict(idx, n, rowptr, col,
+    valK, valM, K, M (column-major dense, or None))."""
+    ctx = ctx or default_context()
+    if mask.dtype != torch.uint8 or not mask.is_cuda:
+        raise TypeError("mask must be a uint8 CUDA tensor")
+    mask = mask.contiguous()
+    dim = mask.dim()
+    ext = (ctypes.c_int64 * 3)(*(list(reversed(mask.shape)) + [1] * (3 - dim)))
+    idx = torch.empty(mask.shape, dtype=torch.int32, device=mask.device)
+    n = ctypes.c_int64(-1)
+    nnz = ctypes.c_int64(-1)
+    st = ctypes.c_void_p(_stream(stream))
+    ctx.check(ctx.lib.fem_assemble(ctx.handle, _ptr(mask), dim, ext, float(h), _ptr(idx), ctypes.byref(n),
+                                   ctypes.byref(nnz), None, None, None, None, None, None, 0, st))
+    N, NNZ = n.value, nnz.value
+    rowptr = torch.empty(N + 1, dtype=torch.int64, device=mask.device)
+    col = torch.empty(max(NNZ, 1), dtype=torch.int32, device=mask.device)
+    vK = torch.empty(max(NNZ, 1), dtype=torch.float64, device=mask.device)
+    vM = torch.empty(max(NNZ, 1), dtype=torch.float64, device=mask.device)
+    K = empty_colmajor(N, N, mask.device) if (dense and N > 0) else None
+    M = empty_colmajor(N, N, mask.device) if (dense and N > 0) else None
+    ctx.check(ctx.lib.fem_assemble(ctx.handle, _ptr(mask), dim, ext, float(h), _ptr(idx), ctypes.byref(n),
+                                   ctypes.byref(nnz), _ptr(rowptr), _ptr(col), _ptr(vK), _ptr(vM), _ptr(K), _ptr(M),
+                                   max(N, 1), st))
+    return {"idx": idx, "n": N, "rowptr": rowptr, "col": col[:NNZ], "valK": vK[:NNZ], "valM": vM[:NNZ], "K": K,
+            "M": M}
+
+
+def eig_pencil(K: torch.Tensor, rowptr, col, valM, half_bandwidth: int | None = None, ctx: Context | None = None,
+               stream=None, sync: bool = True):
+    """All eigenpairs of K phi = theta M phi (K dense, lower triangle read;
+    M in CSR).  Returns (theta ascending, Phi column-major, Phi^T M Phi = I)."""
+    ctx = ctx or default_context()
+    K = _square(K, "K")
+    n = K.shape[0]
+    dev = K.device
+    rowptr = _dev(rowptr, torch.int64, "rowptr", dev, n + 1)
+    col = _dev(col, torch.int32, "col", dev)
+    valM = _dev(valM, torch.float64, "valM", dev, col.numel())
+    if half_bandwidth is None:
+        half_bandwidth = csr_half_bandwidth(rowptr, col, ctx=ctx, stream=stream)
+    theta = torch.empty(n, dtype=torch.float64, device=dev)
+    Phi = empty_colmajor(n, n, dev)
+    nbytes = ctx.lib.fraclap_eig_pencil_workspace_bytes(ctx.handle, n, int(half_bandwidth))
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    ctx.check(ctx.lib.eig_pencil(ctx.handle, _ptr(K), _ld(K), n, _ptr(rowptr), _ptr(col), _ptr(valM),
+                                 int(half_bandwidth), _ptr(theta), _ptr(Phi), max(n, 1), _ptr(ws), ws.numel(),
+                                 ctypes.c_void_p(_stream(stream))))
+    if sync:
+        ctx.sync(stream)
+    return theta, Phi
+
+
+def frac_apply_mass(Phi: torch.Tensor, theta: torch.Tensor, rowptr, col, valM, F: torch.Tensor, pair_f, pair_alpha,
+                    ctx: Context | None = None, stream=None, out: torch.Tensor | None = None,
+                    sync: bool = True) -> torch.Tensor:
+    """u_j = Phi diag(theta^{-alpha_j/2}) Phi^T M F[:, pair_f[j]] (the apply
+    with the M-inner product); returns U (n x k, column-major)."""
+    ctx = ctx or default_context()
+    Phi = _square(Phi, "Phi")
+    n = Phi.shape[0]
+    dev = Phi.device
+    F = _f64_colmajor(F, "F", rows=n, device=dev)
+    rowptr = _dev(rowptr, torch.int64, "rowptr", dev, n + 1)
+    col = _dev(col, torch.int32, "col", dev)
+    valM = _dev(valM, torch.float64, "valM", dev, col.numel())
+    theta = _dev(theta, torch.float64, "theta", dev, n)
+    pf = torch.as_tensor(pair_f, dtype=torch.int32).to(dev).contiguous()
+    pa = torch.as_tensor(pair_alpha, dtype=torch.float64).to(dev).contiguous()
+    k, m = pf.numel(), F.shape[1]
+    if pa.numel() != k:
+        raise ValueError("pair_f and pair_alpha differ in length")
+    U = _out(out, torch.float64, "out", dev, n, k) if out is not None else empty_colmajor(n, k, dev)
+    nbytes = ctx.lib.fraclap_apply_mass_workspace_bytes(ctx.handle, n, m, k)
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    ctx.check(ctx.lib.frac_apply_mass(ctx.handle, _ptr(Phi), _ld(Phi), _ptr(theta), n, _ptr(rowptr), _ptr(col),
+                                      _ptr(valM), _ptr(F), _ld(F), m, _ptr(pf), _ptr(pa), k, _ptr(U), _ld(U), _ptr(ws),
+                                      ws.numel(), ctypes.c_void_p(_stream(stream))))
+    if sync:
+        ctx.sync(stream)
+    return U
 
 
 # ----------------------------------------------------------------------------

@@ -309,6 +309,16 @@ int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t
                const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                int64_t ldc, int s, bool lower, Arena* ar, cudaStream_t st);
 
+// Banded LDL^T (no pivoting) of the symmetric CSR matrix of half-bandwidth
+// b: Lb(t, j) = L(j + t, j), Lr(t, i) = L(i, i - t) (both ld b + 1, n
+// columns), D the pivots; a pivot <= 0 raises FRACLAP_ERR_NOT_SPD in the
+// device status (slicing.cu).  The half-bandwidth query synchronises st.
+size_t band_ldlt_ws(int64_t n, int64_t b);
+int band_ldlt(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, int64_t b,
+              double* Lb, double* Lr, double* D, Arena* ar, cudaStream_t st);
+int csr_half_bandwidth(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col, int64_t* bw,
+                       cudaStream_t st);
+
 // Ogita-Aishima refinement of (X, lambda) against the CSR matrix A.
 size_t refine_ws(const fraclap_ctx* ctx, int64_t n);
 int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col,

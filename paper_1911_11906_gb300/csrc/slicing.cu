@@ -74,10 +74,13 @@ __device__ __forceinline__ double band_entry(const double* BK, const double* BM,
 // One CTA per shift: count[s] = negative pivots of LDL^T(A - sigma_s I), or
 // -1 when a pivot is exactly zero (sigma_s is then, to rounding, an
 // eigenvalue of a leading block and the count is not defined by inertia).
-template <bool SMEM>
+// STORE (one CTA, sigma = 0): the factors themselves, the unit lower band
+// Lb(t, j) = L(j + t, j) (ld b + 1), its row-wise copy Lr(t, i) = L(i, i - t)
+// and the pivots D; a pivot <= 0 raises FRACLAP_ERR_NOT_SPD in `status`.
+template <bool SMEM, bool STORE>
 __global__ void __launch_bounds__(SL_NT)
 band_inertia_kernel(const double* BK, const double* BM, int64_t n, int b, const double* sigma, int64_t nsig,
-                    int64_t* count, double* gwin) {
+                    int64_t* count, double* gwin, double* Lb, double* Lr, double* D, int32_t* status) {
   extern __shared__ __align__(16) double sl_smem[];
   const int64_t s = blockIdx.x;
   if (s >= nsig) return;
@@ -86,7 +89,7 @@ band_inertia_kernel(const double* BK, const double* BM, int64_t n, int b, const 
   double* l = SMEM ? sl_smem + (size_t)ld * ld : gwin + (size_t)nsig * ld * ld + (size_t)s * 2 * ld;
   double* lk = l + ld;
   __shared__ int s_zero;
-  const double sg = sigma[s];
+  const double sg = STORE ? 0.0 : sigma[s];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = SL_NT / 32;
   for (int64_t p = tid; p < (int64_t)ld * ld; p += SL_NT) {
     const int c = (int)(p / ld), t = (int)(p % ld);
@@ -106,9 +109,22 @@ band_inertia_kernel(const double* BK, const double* BM, int64_t n, int b, const 
         const double lt = __ddiv_rn(Wj[t], d);
         l[t] = lt;
         lk[t] = __dmul_rn(lt, d);
+        if (STORE) {
+          Lb[t + j * (int64_t)ld] = lt;
+          Lr[t + (j + t) * (int64_t)ld] = lt;
+        }
       }
     }
-    if (tid == 0) neg += (d < 0.0);
+    if (tid == 0) {
+      neg += (d < 0.0);
+      if (STORE) {
+        D[j] = d;
+        if (!(d > 0.0)) {
+          raise_status(status, FRACLAP_ERR_NOT_SPD);
+          s_zero = 1;
+        }
+      }
+    }
     __syncthreads();
     if (s_zero) break;
     // trailing triangle: column j + c, entries t = 0 .. L - c (rows j + c + t)
@@ -122,7 +138,7 @@ band_inertia_kernel(const double* BK, const double* BM, int64_t n, int b, const 
       for (int t = tid; t < ld; t += SL_NT) Wj[t] = band_entry(BK, BM, ld, j + ld, t, sg);
     __syncthreads();
   }
-  if (tid == 0) count[s] = s_zero ? -1 : neg;
+  if (!STORE && tid == 0) count[s] = s_zero ? -1 : neg;
 }
 
 // Negative pivots of the Sturm recurrence of T - sigma I:
@@ -251,13 +267,14 @@ int launch_inertia(fraclap_ctx* ctx, int64_t n, int64_t b, const InertiaWork& w,
   if (smem_window(b)) {
     const size_t ld = (size_t)b + 1;
     const size_t smem = (ld * ld + 2 * ld) * sizeof(double);
-    FL_CUDA(ctx, cudaFuncSetAttribute(band_inertia_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FL_CUDA(ctx, cudaFuncSetAttribute(band_inertia_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(kSmemWindowMaxLd * kSmemWindowMaxLd + 2 * kSmemWindowMaxLd) *
                                           (int)sizeof(double)));
-    band_inertia_kernel<true><<<(unsigned)nsig, SL_NT, smem, st>>>(w.BK, w.BM, n, (int)b, sigma, nsig, count,
-                                                                    nullptr);
+    band_inertia_kernel<true, false><<<(unsigned)nsig, SL_NT, smem, st>>>(
+        w.BK, w.BM, n, (int)b, sigma, nsig, count, nullptr, nullptr, nullptr, nullptr, nullptr);
   } else {
-    band_inertia_kernel<false><<<(unsigned)nsig, SL_NT, 0, st>>>(w.BK, w.BM, n, (int)b, sigma, nsig, count, w.gwin);
+    band_inertia_kernel<false, false><<<(unsigned)nsig, SL_NT, 0, st>>>(
+        w.BK, w.BM, n, (int)b, sigma, nsig, count, w.gwin, nullptr, nullptr, nullptr, nullptr);
   }
   count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());
@@ -311,6 +328,39 @@ std::vector<double> equal_load_splits(const std::vector<double>& pts, const std:
 }
 
 }  // namespace
+
+size_t band_ldlt_ws(int64_t n, int64_t b) { return inertia_ws(n, b, 1, false); }
+
+int band_ldlt(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, int64_t b,
+              double* Lb, double* Lr, double* D, Arena* ar, cudaStream_t st) {
+  InertiaWork w;
+  inertia_take(ar, n, b, 1, false, &w);
+  FL_CHECK(ctx, w.BK && (smem_window(b) || w.gwin), FRACLAP_ERR_ALLOC, "band_ldlt: workspace too small");
+  FL_TRY(build_bands(ctx, n, rowptr, col, val, nullptr, b, w, st));
+  const int64_t ld = b + 1;
+  FL_CUDA(ctx, cudaMemsetAsync(Lb, 0, sizeof(double) * n * ld, st));
+  FL_CUDA(ctx, cudaMemsetAsync(Lr, 0, sizeof(double) * n * ld, st));
+  if (smem_window(b)) {
+    const size_t smem = ((size_t)ld * ld + 2 * ld) * sizeof(double);
+    FL_CUDA(ctx, cudaFuncSetAttribute(band_inertia_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kSmemWindowMaxLd * kSmemWindowMaxLd + 2 * kSmemWindowMaxLd) *
+                                          (int)sizeof(double)));
+    band_inertia_kernel<true, true><<<1, SL_NT, smem, st>>>(w.BK, nullptr, n, (int)b, nullptr, 1, nullptr, nullptr,
+                                                            Lb, Lr, D, ctx->d_status);
+  } else {
+    band_inertia_kernel<false, true><<<1, SL_NT, 0, st>>>(w.BK, nullptr, n, (int)b, nullptr, 1, nullptr, w.gwin, Lb,
+                                                          Lr, D, ctx->d_status);
+  }
+  count_launch(ctx);
+  FL_CUDA(ctx, cudaGetLastError());
+  return 0;
+}
+
+int csr_half_bandwidth(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col, int64_t* bw,
+                       cudaStream_t st) {
+  return fraclap_csr_half_bandwidth(ctx, n, rowptr, col, bw, (fraclap_stream_t)st);
+}
+
 }  // namespace fraclap
 
 using namespace fraclap;
