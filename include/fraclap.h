@@ -562,8 +562,12 @@ int fraclap_partition_spectrum(fraclap_ctx* ctx, int64_t n, const int64_t* rowpt
  *  FRACLAP_SCHED_OZAKI_BITS: digit width of the slices when K > 256: 7
  *    (exact chunks of 1024, ceil(8 s / 7) digits per operand) or 8 (exact
  *    chunks of 256, s digits: fewer slice pairs, more chunk sums) [7].
+ *  FRACLAP_SCHED_FP32_STAGES: the FP32 products of eig_full_mixed's band
+ *    reduction and first back-transformation: 0 on the FP32 FMA kernel, 1 on
+ *    the tensor cores as three TF32 products (FP32-level accuracy, a few
+ *    2^-22 per product instead of 2^-24) [0].
  * ---------------------------------------------------------------------- */
-enum { FRACLAP_SCHED_OZAKI_GROUP = 0, FRACLAP_SCHED_OZAKI_BITS = 1 };
+enum { FRACLAP_SCHED_OZAKI_GROUP = 0, FRACLAP_SCHED_OZAKI_BITS = 1, FRACLAP_SCHED_FP32_STAGES = 2 };
 int fraclap_set_schedule(fraclap_ctx* ctx, int knob, int value);
 int fraclap_get_schedule(const fraclap_ctx* ctx, int knob);
 

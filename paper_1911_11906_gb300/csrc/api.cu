@@ -454,22 +454,27 @@ extern "C" int eig_full_mixed(fraclap_ctx* ctx, const double* A_dev, int64_t n, 
   float* Z = ar.take<float>(n * n);
   char* tcs = ar.take<char>(tf32_scratch_bytes(n));
   FL_CHECK(ctx, Z != nullptr && tcs != nullptr, FRACLAP_ERR_ALLOC, "eig_full_mixed: workspace too small");
-  FL_TRY(reduce<float>(ctx, A_dev, n, lda, &w, st));
+  {
+    // FP32 products of the band reduction on the tensor cores (three TF32
+    // products) when the context's schedule asks for it, else the FMA kernel
+    TcScratch lend(ctx, ctx->fp32_stages_tc ? tcs : nullptr, tf32_scratch_bytes(n));
+    FL_TRY(reduce<float>(ctx, A_dev, n, lda, &w, st));
+  }
   {
     StageTimer t(ctx, kStageTridiagDC, st);
     FL_TRY(stedc_run<float>(ctx, w.d, w.e, n, lambda_dev, Z, n, &ar, st));
   }
-  FL_TRY(back_transform<float>(ctx, n, &w, Z, n, st));
+  {
+    TcScratch lend(ctx, ctx->fp32_stages_tc ? tcs : nullptr, tf32_scratch_bytes(n));
+    FL_TRY(back_transform<float>(ctx, n, &w, Z, n, st));
+  }
   {
     StageTimer t(ctx, kStageRefine, st);
     widen<<<(unsigned)std::min<int64_t>(cdiv(n * n, 256), 152 * 16), 256, 0, st>>>(Z, n, V_dev, ldv);
     count_launch(ctx);
     FL_CUDA(ctx, cudaGetLastError());
     // The refinement's FP32 product X E runs on the tensor cores (three TF32
-    // products; its error is removed by the next iteration).  The FP32
-    // stages keep the FMA kernel: TF32 splitting in the band reduction or
-    // in Q1 raised the starting |I - X^T X| from 9e-6 to 1.5e-5 at n = 8810,
-    // which merged thousands of eigenvalues into one refinement cluster.
+    // products; its error is removed by the next iteration).
     TcScratch lend(ctx, tcs, tf32_scratch_bytes(n));
     Arena rar = ar;  // the refinement reuses everything after the FP32 stages
     FL_TRY(refine_run(ctx, n, rowptr_dev, col_dev, val_dev, V_dev, ldv, lambda_dev, refine_iters, &rar, st));

@@ -341,7 +341,8 @@ int gemm(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDescT<T>& 
   FL_CHECK(ctx, split_k <= 1 || d.beta == 1.0, FRACLAP_ERR_INVALID_ARG,
            "gemm: split-K accumulates into C (beta must be 1)");
   if constexpr (std::is_same<T, float>::value) {
-    if ((d.K > 0 || d.K2 > 0) && tf32_route_fits(ctx, mode, d, split_k)) return gemm_tf32x3(ctx, ta, tb, mode, d, st);
+    if ((d.K > 0 || d.K2 > 0) && tf32_route_fits(ctx, mode, d, split_k))
+      return gemm_tf32x3(ctx, ta, tb, mode, d, split_k, st);
   }
   if (d.K <= 0 && d.K2 <= 0) {  // C = beta C
     GemmDescT<T> z = d;

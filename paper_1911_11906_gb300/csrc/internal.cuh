@@ -23,6 +23,7 @@ struct fraclap_ctx {
   int apply_slices = 0;          // frac_apply products: 0 = FP64 engine, s = s BF16 slices (tensor cores)
   int oz_group = 8;              // slice-product kernel: tile rows per raster group (0 = all rows)
   int oz_bits = 7;               // slice-product kernel: digit width for K > 256 (7 or 8)
+  int fp32_stages_tc = 0;        // mixed route: FP32 band reduction and Q1 products on the tensor cores (TF32 x 3)
   void* tc_scratch = nullptr;    // split operands of the TF32 tensor-core route of FP32 GEMMs
   size_t tc_scratch_bytes = 0;   // (set by the caller of the FP32 stages, null otherwise)
   long long wait_cycles = 0;     // wait_timeout_s in SM clock cycles (upper bound)
@@ -221,10 +222,12 @@ int gemm(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDescT<T>& 
 // FP32 GEMM on the tensor cores (three TF32 products, FP32-level accuracy),
 // through the split-operand scratch in ctx->tc_scratch; gemm<float> takes
 // this route when tf32_route_fits (modes Plain, SymA, LowerC; M >= 128,
-// N >= 64, K + K2 >= 64, no split-K, tensor route 1, scratch large enough).
+// N >= 64, K + K2 >= 64, tensor route 1, scratch large enough; split-K with
+// beta = 1 adds into C with atomics, as the FMA kernels do).
 size_t tf32_split_bytes(int64_t M, int64_t N, int64_t K);
 bool tf32_route_fits(const fraclap_ctx* ctx, GemmMode mode, const GemmDescT<float>& d, int split_k);
-int gemm_tf32x3(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDescT<float>& d, cudaStream_t st);
+int gemm_tf32x3(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDescT<float>& d, int split_k,
+                cudaStream_t st);
 // Batched over a device array of descriptors; grid covers max_m x max_n tiles,
 // tiles outside a descriptor's M x N exit.  Descriptors with M, N or K <= 0
 // are skipped.

@@ -584,6 +584,10 @@ extern "C" int fraclap_set_schedule(fraclap_ctx* ctx, int knob, int value) {
       FL_CHECK(ctx, value == 7 || value == 8, FRACLAP_ERR_INVALID_ARG, "set_schedule: digit width must be 7 or 8");
       ctx->oz_bits = value;
       return 0;
+    case FRACLAP_SCHED_FP32_STAGES:
+      FL_CHECK(ctx, value == 0 || value == 1, FRACLAP_ERR_INVALID_ARG, "set_schedule: FP32 stage route must be 0 or 1");
+      ctx->fp32_stages_tc = value;
+      return 0;
     default:
       return set_error(ctx, FRACLAP_ERR_INVALID_ARG, "set_schedule: unknown knob %d", knob);
   }
@@ -594,6 +598,7 @@ extern "C" int fraclap_get_schedule(const fraclap_ctx* ctx, int knob) {
   switch (knob) {
     case FRACLAP_SCHED_OZAKI_GROUP: return ctx->oz_group;
     case FRACLAP_SCHED_OZAKI_BITS: return ctx->oz_bits;
+    case FRACLAP_SCHED_FP32_STAGES: return ctx->fp32_stages_tc;
     default: return FRACLAP_ERR_INVALID_ARG;
   }
 }

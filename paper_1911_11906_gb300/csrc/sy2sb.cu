@@ -282,9 +282,11 @@ panel_qr_cluster_kernel(T* P, int64_t ldp, int64_t m, int bw, T* Vout, int64_t l
 // T of the compact WY form from tau and the Gram matrix G = V^T V (bw x bw).
 // When every tau is nonzero, T^-1 = diag(1/tau) + strictly-upper(G)
 // (Schreiber and Van Loan's form of H_1 ... H_bw = I - V T V^T): T is that
-// triangle's inverse, one column per thread by back substitution, with no
-// barrier between steps.  Otherwise the column recurrence
-// T(i, i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i).  One CTA.
+// triangle's inverse, formed row by row from the bottom, X(i, j) =
+// -(1 / U(i, i)) sum_{i < k <= j} U(i, k) X(k, j), all columns of a row at
+// once and each sum split over four lanes (one barrier per row).  Otherwise
+// the column recurrence T(i, i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i).
+// One CTA of 256 threads.
 template <class T>
 __global__ void __launch_bounds__(PQR_NT) panel_t_kernel(const T* gram, const double* tau, int bw, T* Tf) {
   __shared__ double U[64][65];  // U(i, k), i <= k
@@ -306,14 +308,17 @@ __global__ void __launch_bounds__(PQR_NT) panel_t_kernel(const T* gram, const do
   }
   __syncthreads();
   if (!s_zero) {
-    for (int j = tid; j < bw; j += PQR_NT) {  // column j of U^-1
-      for (int i = j; i >= 0; --i) {
-        double sum = (i == j) ? 1.0 : 0.0;
-        for (int k = i + 1; k <= j; ++k) sum -= U[i][k] * Ts[k + j * bw];
-        Ts[i + j * bw] = sum / U[i][i];
-      }
+    static_assert(PQR_NT == 256, "four lanes per column of a 64-wide panel");
+    const int j = tid >> 2, part = tid & 3;  // column j, lanes 4j .. 4j + 3 of one warp
+    for (int i = bw - 1; i >= 0; --i) {
+      double sum = 0.0;
+      if (j > i && j < bw)
+        for (int k = i + 1 + part; k <= j; k += 4) sum += U[i][k] * Ts[k + j * bw];
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+      if (part == 0 && j < bw && j >= i) Ts[i + j * bw] = (j == i) ? 1.0 / U[i][i] : -sum / U[i][i];
+      __syncthreads();
     }
-    __syncthreads();
   } else {
     for (int i = 0; i < bw; ++i) {
       const double ti = tau[i];
@@ -497,6 +502,22 @@ int q1_apply_run(fraclap_ctx* ctx, const Stage1T<T>* s, int64_t n, int b, T* Z, 
                  int64_t ncols, T* W1, T* W2, cudaStream_t st) {
   int64_t voff = s->vtotal;
   using D = GemmDescT<T>;
+  if (sizeof(T) == 4 && ctx->tc_scratch) {
+    // tensor-core shapes (tall and wide products): W1^T = Z_r^T V (n x b),
+    // W2^T = W1^T T^T, Z_r -= V W2 -- the same three products, transposed
+    for (int64_t p = s->npanel - 1; p >= 0; --p) {
+      const int64_t j0 = p * b, m = n - j0 - b;
+      voff -= m * b;
+      const T* V = s->Vstore + voff;
+      const T* Tf = s->Tstore + p * b * b;
+      T* Zr = Z + (j0 + b);
+      FL_CUDA(ctx, cudaMemsetAsync(W1, 0, sizeof(T) * b * ncols, st));
+      FL_TRY(gemm<T>(ctx, true, false, kGemmPlain, D{ncols, b, m, Zr, ldz, V, m, W1, ncols, nullptr, 0, nullptr, 0, 0, 1.0, 1.0}, (int)std::min<int64_t>(cdiv(m, 1024), 16), st));
+      FL_TRY(gemm<T>(ctx, false, true, kGemmPlain, D{ncols, b, b, W1, ncols, Tf, b, W2, ncols, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
+      FL_TRY(gemm<T>(ctx, false, true, kGemmPlain, D{m, ncols, b, V, m, W2, ncols, Zr, ldz, nullptr, 0, nullptr, 0, 0, -1.0, 1.0}, 1, st));
+    }
+    return 0;
+  }
   for (int64_t p = s->npanel - 1; p >= 0; --p) {
     const int64_t j0 = p * b, m = n - j0 - b;
     voff -= m * b;

@@ -93,10 +93,12 @@ __global__ void __launch_bounds__(256) split_tf32(SplitSrc src, int64_t Kp, int 
   }
 }
 
+// Split-K: CTA z of gridDim.z takes the K-blocks [z kb_per, (z + 1) kb_per)
+// and adds alpha acc into C with atomics (the caller has scaled C by beta).
 __global__ void __launch_bounds__(TG_THREADS, 1)
 tf32_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t M,
-                 int64_t N, int64_t Kq, float alpha, float beta, float* C, int64_t ldc, int lower, long long limit,
-                 int32_t* status) {
+                 int64_t N, int64_t Kq, float alpha, float beta, float* C, int64_t ldc, int lower, int kb_per,
+                 long long limit, int32_t* status) {
   extern __shared__ __align__(1024) unsigned char tg_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tg_smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[TG_STAGES], empty_bar[TG_STAGES];
@@ -106,7 +108,11 @@ tf32_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.x * TG_M, n0 = (int64_t)blockIdx.y * TG_N;
   if (lower && m0 + TG_M - 1 < n0) return;  // whole tile above the diagonal
-  const int nkb = (int)(Kq / TG_KB);
+  const int nkb_all = (int)(Kq / TG_KB);
+  const int kb0 = (int)blockIdx.z * kb_per;
+  const int nkb = (kb0 + kb_per < nkb_all ? kb0 + kb_per : nkb_all) - kb0;  // this CTA's K-blocks
+  if (nkb <= 0) return;
+  const bool split = gridDim.z > 1;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < TG_STAGES; ++i) {
@@ -145,8 +151,8 @@ tf32_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         unsigned char* a = smem + st * TG_STAGE_BYTES;
         unsigned char* b = a + TG_A_BYTES;
         mbar_expect_tx(&full_bar[st], TG_STAGE_BYTES);
-        tma_load_2d(a, &mapA, &full_bar[st], kb * TG_KB, (int)m0);
-        tma_load_2d(b, &mapB, &full_bar[st], kb * TG_KB, (int)n0);
+        tma_load_2d(a, &mapA, &full_bar[st], (kb0 + kb) * TG_KB, (int)m0);
+        tma_load_2d(b, &mapB, &full_bar[st], (kb0 + kb) * TG_KB, (int)n0);
       }
       if (!ok) {
         atomicCAS(status, 0, FRACLAP_ERR_TIMEOUT);
@@ -216,7 +222,8 @@ tf32_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             if (col >= N || (lower && row < col)) continue;
             float* cp = C + row + col * ldc;
             const float v = alpha * __uint_as_float(r[j]);
-            *cp = (beta == 0.0f) ? v : v + beta * *cp;
+            if (split) atomicAdd(cp, v);
+            else *cp = (beta == 0.0f) ? v : v + beta * *cp;
           }
         }
       }
@@ -254,7 +261,8 @@ size_t tf32_split_bytes(int64_t M, int64_t N, int64_t K) {
 }
 
 bool tf32_route_fits(const fraclap_ctx* ctx, GemmMode mode, const GemmDescT<float>& d, int split_k) {
-  if (!ctx->tc_scratch || ctx->tensor_route != 1 || split_k > 1) return false;
+  if (!ctx->tc_scratch || ctx->tensor_route != 1) return false;
+  if (split_k > 1 && d.beta != 1.0) return false;
   if (mode != kGemmPlain && mode != kGemmSymA && mode != kGemmLowerC) return false;
   const int64_t Kt = d.K + (d.K2 > 0 ? d.K2 : 0);
   if (d.M < 128 || d.N < 64 || Kt < 64) return false;
@@ -262,7 +270,8 @@ bool tf32_route_fits(const fraclap_ctx* ctx, GemmMode mode, const GemmDescT<floa
   return tf32_split_bytes(d.M, d.N, Kt) <= ctx->tc_scratch_bytes;
 }
 
-int gemm_tf32x3(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDescT<float>& d, cudaStream_t st) {
+int gemm_tf32x3(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDescT<float>& d, int split_k,
+                cudaStream_t st) {
   const int64_t K2 = (d.K2 > 0) ? d.K2 : 0;
   const int64_t Kt = d.K + K2, Kp = pad32(Kt), Kq = 3 * Kp;
   float* Sa = reinterpret_cast<float*>(ctx->tc_scratch);
@@ -281,10 +290,13 @@ int gemm_tf32x3(fraclap_ctx* ctx, bool ta, bool tb, GemmMode mode, const GemmDes
            "gemm_tf32x3: tensor map encoding failed");
   const size_t smem = (size_t)TG_STAGES * TG_STAGE_BYTES + 1024;
   FL_CUDA(ctx, cudaFuncSetAttribute(tf32_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const dim3 grid((unsigned)cdiv(d.M, TG_M), (unsigned)cdiv(d.N, TG_N));
+  const int nkb = (int)(Kq / TG_KB);
+  const int splits = std::max(1, std::min(split_k, nkb));
+  const int kb_per = (int)cdiv(nkb, splits);
+  const dim3 grid((unsigned)cdiv(d.M, TG_M), (unsigned)cdiv(d.N, TG_N), (unsigned)cdiv(nkb, kb_per));
   FL_CHECK(ctx, grid.y <= 65535, FRACLAP_ERR_UNSUPPORTED, "gemm_tf32x3: N too large");
   tf32_gemm_kernel<<<grid, TG_THREADS, smem, st>>>(ma, mb, d.M, d.N, Kq, (float)d.alpha, (float)d.beta, d.C,
-                                                   d.ldc, mode == kGemmLowerC ? 1 : 0, ctx->wait_cycles,
+                                                   d.ldc, mode == kGemmLowerC ? 1 : 0, kb_per, ctx->wait_cycles,
                                                    ctx->d_status);
   count_launch(ctx);
   FL_CUDA(ctx, cudaGetLastError());

@@ -126,11 +126,13 @@ def _csr_cuda(A):
     return (torch.from_numpy(A.rowptr).cuda(), torch.from_numpy(A.col).cuda(), torch.from_numpy(A.val).cuda())
 
 
+@pytest.mark.parametrize("tc", [0, 1])
 @pytest.mark.parametrize("which,b,iters", [("square23", 32, 6), ("ellipse36", 32, 6), ("ellipse36", 64, 6),
                                             ("ellipse64", 32, 6), ("ellipse48", 16, 6), ("square9", 8, 6),
                                             ("cube6", 32, 6)])
-def test_eig_full_mixed_refined_vs_oracle(which, b, iters):
-    """FP32 stages + Ogita-Aishima refinement reach the FP64 tolerances."""
+def test_eig_full_mixed_refined_vs_oracle(which, b, iters, tc):
+    """FP32 stages (FMA kernel, or three TF32 products on the tensor cores
+    with tc = 1) + Ogita-Aishima refinement reach the FP64 tolerances."""
     F = _F()
     if which.startswith("square"):
         p = I.square_problem(int(which[6:]))
@@ -143,6 +145,7 @@ def test_eig_full_mixed_refined_vs_oracle(which, b, iters):
     D = A.dense()
     lam_o, V_o = O.eig_full(D)
     ctx = F.Context(band_width=b)
+    ctx.set_schedule("fp32_stages_tc", tc)
     lam, V = F.eig_full_mixed(_colmajor(D), *_csr_cuda(A), refine_iters=iters, ctx=ctx)
     lam, V = lam.cpu().numpy(), V.cpu().numpy()
     _check_decomposition(D, lam_o, lam, V)
@@ -155,13 +158,16 @@ def test_eig_full_mixed_refined_vs_oracle(which, b, iters):
     assert err <= 1e-10
 
 
-def test_eig_full_mixed_without_refinement_is_fp32_accurate():
+@pytest.mark.parametrize("tc", [0, 1])
+def test_eig_full_mixed_without_refinement_is_fp32_accurate(tc):
     F = _F()
     p = I.ellipse_problem(30, seed=3)
     _, A = O.assemble(p.mask, p.h)
     D = A.dense()
     lam_o, _ = O.eig_full(D)
-    lam, V = F.eig_full_mixed(_colmajor(D), *_csr_cuda(A), refine_iters=0)
+    ctx = F.Context()
+    ctx.set_schedule("fp32_stages_tc", tc)
+    lam, V = F.eig_full_mixed(_colmajor(D), *_csr_cuda(A), refine_iters=0, ctx=ctx)
     lam, V = lam.cpu().numpy(), V.cpu().numpy()
     assert np.max(np.abs(lam - lam_o)) <= 1e-4 * lam_o[-1]
     assert np.max(np.abs(V.T @ V - np.eye(A.n))) <= 1e-4

@@ -69,15 +69,17 @@ def full_residuals(Acsr, lam, V, fro_A):
     return res, orth
 
 
-@pytest.mark.parametrize("route", ["mixed", "fp64"])
+@pytest.mark.parametrize("route", ["mixed", "mixed-tc", "fp64"])
 def test_full_size_workload(workload, route):
     import paper_1911_11906_gb300 as F
     p, A, refs, lam_o, U_o = workload
     assert p.n == 8810
     ctx = F.Context(band_width=64)
+    if route == "mixed-tc":  # FP32 band reduction and Q1 on the tensor cores
+        ctx.set_schedule("fp32_stages_tc", 1)
     mask = torch.from_numpy(p.mask).cuda()
     asm = F.fd_assemble(mask, p.h, ctx=ctx)
-    if route == "mixed":
+    if route.startswith("mixed"):
         lam, V = F.eig_full_mixed(asm["A"], asm["rowptr"], asm["col"], asm["val"], refine_iters=6, ctx=ctx)
     else:
         lam, V = F.eig_full(asm["A"], ctx=ctx)
