@@ -202,21 +202,23 @@ def ozaki_bf16_flops(n: int, slices: int = 8) -> float:
     return 2.0 * pairs * n * (n * (n + 1) // 2)
 
 
-def refine_slice_counts(iterations: int, cap: int) -> list:
-    """7-bit slices per operand of the refinement's two residual products in
-    each iteration: 40, 48 and then 56 bits (5, 6, 7 slices of 8 bits), the
-    last allowed iteration always full."""
-    bits = []
+def refine_slice_counts(iterations: int, cap: int, digit_bits: int = 7) -> list:
+    """Digits per operand of the refinement's two residual products in each
+    iteration: 40, 48 and then 56 bits (5, 6, 7 slices of 8 bits), the last
+    allowed iteration always full; as 7-bit digits (ceil(8 s / 7)) or, with
+    digit_bits = 8, the slices themselves."""
+    out = []
     for it in range(iterations):
         s8 = 7 if it + 1 >= cap else (5 if it == 0 else (6 if it == 1 else 7))
-        bits.append((8 * s8 + 6) // 7)
-    return bits
+        out.append(s8 if digit_bits == 8 else (8 * s8 + 6) // 7)
+    return out
 
 
-# DRAM bytes per BF16 flop of ozaki_tc_kernel, from one ncu capture of the
-# 4096^3 product (12.87 GB read + 1.06 GB written for 36 x 2 x 4096^3 flop);
-# its tile re-streaming grows in proportion to the flops.
-OZAKI_DRAM_BYTES_PER_FLOP = (12.866905e9 + 1.060005e9) / (36 * 2.0 * 4096 ** 3)
+# DRAM bytes per BF16 flop of ozaki_tc_kernel from one ncu capture of the
+# 4096^3 product with the current kernel (None until captured: the tile order
+# changed since the last capture); its tile re-streaming grows in proportion
+# to the flops.
+OZAKI_DRAM_BYTES_PER_FLOP = None
 
 
 def run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier, steps=None, warmup=None):
@@ -351,6 +353,11 @@ def run_gpu(args, rank, world, local_rank):
     if rank != 0:
         return
 
+    # measured FMA-pipe peaks (the bound of the SIMT FP64 / FP32 stages)
+    fma_peaks = {"fp64_tflops": round(R["ctx"].fma_throughput(64) / 1e12, 4),
+                 "fp32_tflops": round(R["ctx"].fma_throughput(32) / 1e12, 3),
+                 "how": "fraclap_fma_throughput: independent FMA chains, 8 CTAs x 256 threads per SM, CUDA events"}
+    fp64_peak = fma_peaks["fp64_tflops"] or FP64_PEAK_TFLOPS
     stages = R["stages"]
     b = band[head]
     if head == "fp64":
@@ -359,21 +366,30 @@ def run_gpu(args, rank, world, local_rank):
         work = q2_flops(n, b)
         traffic = None
         roof = {"kernel": "q2t_apply_kernel (back-transformation by the bulge-chasing reflectors, FP64)",
-                "bound": "alu", "peak": round(FP64_PEAK_TFLOPS, 4),
-                "peak_source": "derived FP64 peak (152 SMs x 2.07 GHz x 2 DFMA/clk x 2); no FP64 figure in MEASURED_PEAKS.json"}
+                "bound": "alu", "peak": round(fp64_peak, 4),
+                "peak_source": "measured FP64 FMA throughput (fraclap_fma_throughput); no FP64 figure in "
+                               "MEASURED_PEAKS.json"}
     else:
         g_ms, g_cnt = stages["slice_products"]
         dur = g_ms / max(g_cnt, 1)
         # average over the launches (2 per iteration, fewer slices in the first two)
-        per_iter = refine_slice_counts(len(R.get("refine", [])) or 3, REFINE_ITERS)
+        digit_bits = R["ctx"].get_schedule("ozaki_bits")
+        per_iter = refine_slice_counts(len(R.get("refine", [])) or 3, REFINE_ITERS, digit_bits)
         total = sum(2 * ozaki_bf16_flops(n, sl) for sl in per_iter)
         work = total / max(2 * len(per_iter), 1)
-        traffic = OZAKI_DRAM_BYTES_PER_FLOP * work
-        peak = _measured_peak("bf16_tflops") or 1900.0
+        traffic = OZAKI_DRAM_BYTES_PER_FLOP * work if OZAKI_DRAM_BYTES_PER_FLOP else None
+        # the kernel runs inside a seconds-long step: the sustained BF16 figure is its peak
+        peak = _measured_peak("bf16_tflops_sustained") or _measured_peak("bf16_tflops") or 1700.0
         roof = {"kernel": "ozaki_tc_kernel (residual products of the refinement: tcgen05.mma on TMA-loaded BF16 slices)",
                 "bound": "tensor", "peak": round(peak, 1),
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if _measured_peak("bf16_tflops") else "fallback 1.9 PFLOP/s"}
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured; the kernel is timed inside a "
+                                "seconds-long step)") if _measured_peak("bf16_tflops_sustained") else
+                               ("MEASURED_PEAKS.json bf16_tflops (burst)" if _measured_peak("bf16_tflops")
+                                else "fallback 1.7 PFLOP/s sustained"),
+                "frac_of_burst": None}
     achieved = work / (dur * 1e-3) / 1e12
+    if "frac_of_burst" in roof:
+        roof["frac_of_burst"] = round(achieved / (_measured_peak("bf16_tflops") or 1900.0), 5)
     roof.update({"achieved": round(achieved, 4), "unit": "TFLOP/s", "frac": round(achieved / roof["peak"], 5),
                  "traffic": (round(traffic) if traffic else None), "flops_per_launch": work,
                  "ms_per_launch": round(dur, 3)})
@@ -400,6 +416,7 @@ def run_gpu(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int(U_h.numel() * 8), "ms_per_step": round(e2e_ms, 3)},
         "gpu_launches": int(R["launches"]),
         "clocks": R["clocks"],
+        "measured_fma_peaks": fma_peaks,
     }
     for pth, r in results.items():
         st = r["stages"]
@@ -409,7 +426,7 @@ def run_gpu(args, rank, world, local_rank):
             "steps_timed": r["steps"], "warmup": r["warmup"],
             "eig_s": round(eig_ms / 1e3, 4),
             "eig_tflops_credited_fp64": round(eig_flops(n) / (eig_ms * 1e-3) / 1e12, 4),
-            "eig_frac_of_fp64_peak": round(eig_flops(n) / (eig_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
+            "eig_frac_of_fp64_peak": round(eig_flops(n) / (eig_ms * 1e-3) / 1e12 / fp64_peak, 4),
             "apply_s": round(st["apply"][0] / r["steps"] / 1e3, 5),
             "stage_ms": {s: round(v[0] / r["steps"], 3) for s, v in st.items()},
             "gpu_launches": int(r["launches"]),

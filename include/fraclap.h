@@ -427,6 +427,16 @@ int fraclap_set_tensor_route(fraclap_ctx* ctx, int route);
  * `stream`; returns FRACLAP_ERR_INVALID_ARG for any other `which`. */
 int fraclap_wait_selftest(fraclap_ctx* ctx, int which, fraclap_stream_t stream);
 
+/* Sustained throughput of the FMA pipe (precision 64: DFMA, 32: FFMA) in
+ * flop/s, measured by independent FMA chains over 8 CTAs of 256 threads per
+ * SM (iters steps each: 2^16 FP64 or 2^20 FP32 steps take a few tenths of a
+ * second on a GB300), one untimed launch
+ * then one timed with CUDA events; synchronises `stream`.  The peaks the
+ * SIMT FP64 and FP32 kernels are measured against (no counterpart in the
+ * paper). */
+int fraclap_fma_throughput(fraclap_ctx* ctx, int precision, int64_t iters, double* flops_per_s,
+                           fraclap_stream_t stream);
+
 /* C = alpha op(A) op(B) + beta C with FP64-accurate products formed on the
  * BF16 tensor cores by Ozaki's error-free splitting into `slices` 8-bit slices
  * per row/column (7 slices: full FP64 accuracy; fewer: about 8*slices bits

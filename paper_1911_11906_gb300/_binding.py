@@ -71,6 +71,7 @@ SIGNATURES = {
     "fraclap_bisect": (_i32, [_p, _p, _p, _i64, _i64, _i64, _p, _p]),
     "fraclap_partition_spectrum": (_i32, [_p, _i64, _p, _p, _p, _p, _i64, _dbl, _i32, _i32, _i32, _i32, _dbl, _p,
                                           _p, _p, _i32, _p, _sz, _p]),
+    "fraclap_fma_throughput": (_i32, [_p, _i32, _i64, _p, _p]),
     "fraclap_set_schedule": (_i32, [_p, _i32, _i32]),
     "fraclap_get_schedule": (_i32, [_p, _i32]),
     "fraclap_sgemm": (_i32, [_p, _i32, _i32, _i32, _i64, _i64, _i64, ctypes.c_float, _p, _i64, _p, _i64,
@@ -197,6 +198,15 @@ class Context:
         """Drives one bounded device wait (0: grid barrier, 1: mbarrier) into
         its time limit; the next sync raises FraclapError(-4)."""
         self.check(self.lib.fraclap_wait_selftest(self.handle, int(which), ctypes.c_void_p(_stream(stream))))
+
+    def fma_throughput(self, precision: int, iters: int | None = None, stream=None) -> float:
+        """Measured FMA-pipe throughput in flop/s (precision 64 or 32)."""
+        if iters is None:
+            iters = (1 << 16) if precision == 64 else (1 << 20)
+        out = ctypes.c_double(0.0)
+        self.check(self.lib.fraclap_fma_throughput(self.handle, int(precision), int(iters), ctypes.byref(out),
+                                                   ctypes.c_void_p(_stream(stream))))
+        return float(out.value)
 
     def launch_count(self) -> int:
         return int(self.lib.fraclap_launch_count(self.handle))

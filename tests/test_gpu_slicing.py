@@ -176,11 +176,14 @@ def test_bisection_of_the_gpu_tridiagonal_form():
     assert np.max(np.abs(lam - lam_o[k0:k1 + 1]) / lam_o[k0:k1 + 1]) <= 1e-11
 
 
-@pytest.mark.parametrize("grid,P,n_b", [("square48", 8, 0), ("ellipse64", 12, 2), ("square48", 1, 0)])
+@pytest.mark.parametrize("grid,P,n_b", [("square48", 7, 0), ("ellipse64", 11, 2), ("square48", 1, 0)])
 def test_partition_spectrum_matches_oracle(grid, P, n_b):
     """The greedy partitioning of Sec. III-D on GPU counts reproduces the
     oracle's partitioner on the oracle's counts exactly (split points, loads,
-    history), and balances the loads."""
+    history), and balances the loads.  (With rho = 8 / h^2, an even P puts
+    the first split of the middle at 4 / h^2, the diagonal value, where the
+    first pivot of the factorisation without pivoting is exactly zero; both
+    sides then report the shift instead of a count.)"""
     F = _F()
     p = I.square_problem(48) if grid == "square48" else I.ellipse_problem(64, n_ellipses=6, seed=1000)
     _, A = O.assemble(p.mask, p.h)
@@ -194,3 +197,20 @@ def test_partition_spectrum_matches_oracle(grid, P, n_b):
     assert l_g.sum() == A.n
     if P > 1:
         assert l_g.max() <= 1.3 * A.n / P
+
+
+def test_partition_reports_a_zero_pivot_shift():
+    """A split on the diagonal value (rho = 8 / h^2, P = 2: the split 4 / h^2)
+    makes the first pivot exactly zero: the partitioner reports it as an
+    error, as the oracle's count does, and the context stays usable."""
+    F = _F()
+    p = I.square_problem(12)
+    _, A = O.assemble(p.mask, p.h)
+    rp, cl, vl = _csr_cuda(A)
+    with pytest.raises(F.FraclapError) as ei:
+        F.partition_spectrum(rp, cl, vl, 8.0 / p.h ** 2, 2, n_a=1)
+    assert ei.value.code == -2
+    with pytest.raises(RuntimeError):
+        O.count_below(A, 4.0 / p.h ** 2)
+    s, l, _ = F.partition_spectrum(rp, cl, vl, 8.0 / p.h ** 2, 3, n_a=2)
+    assert l.sum() == A.n
