@@ -576,8 +576,11 @@ int fraclap_partition_spectrum(fraclap_ctx* ctx, int64_t n, const int64_t* rowpt
  *    reduction and first back-transformation: 0 on the FP32 FMA kernel, 1 on
  *    the tensor cores as three TF32 products (FP32-level accuracy, a few
  *    2^-22 per product instead of 2^-24) [0].
+ *  FRACLAP_SCHED_OZAKI_TILE_N: columns of the slice-product kernel's output
+ *    tile, 128 or 256 (rows are 128) [128].
  * ---------------------------------------------------------------------- */
-enum { FRACLAP_SCHED_OZAKI_GROUP = 0, FRACLAP_SCHED_OZAKI_BITS = 1, FRACLAP_SCHED_FP32_STAGES = 2 };
+enum { FRACLAP_SCHED_OZAKI_GROUP = 0, FRACLAP_SCHED_OZAKI_BITS = 1, FRACLAP_SCHED_FP32_STAGES = 2,
+       FRACLAP_SCHED_OZAKI_TILE_N = 3 };
 int fraclap_set_schedule(fraclap_ctx* ctx, int knob, int value);
 int fraclap_get_schedule(const fraclap_ctx* ctx, int knob);
 

@@ -162,20 +162,20 @@ def best_workers(problems: list, candidates=(4, 8, 16, 32), tuner: Autotuner | N
                         lambda w: _event_seconds(lambda: B.solve_batched(problems, workers=int(w), ctx=ctx)), reps)
 
 
-def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7,),
+def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7,), tiles=(128, 256),
                         tuner: Autotuner | None = None, reps: int = 2) -> dict:
-    """Tile order (raster group of tile rows) and digit width of the
-    slice-product kernel for the refinement's residual product X^T X of an
+    """Tile order (raster group of tile rows), tile width and digit width of
+    the slice-product kernel for the refinement's residual product X^T X of an
     n x n X with `slices` BF16 slices, measured on a seeded matrix of that
     size through fraclap_dgemm_ozaki.  Returns {"ozaki_group": G,
-    "ozaki_bits": w}; apply it with apply_schedule(ctx, ...).  The digit
+    "ozaki_bits": w, "ozaki_tile_n": t}; apply it with apply_schedule(ctx, ...).  The digit
     widths tried default to 7 alone: 8-bit digits (28 instead of 36 slice
     pairs for 7 slices) measured the same kernel time on a GB300 at n = 4096
     and 8810, their four times more chunk sums taking what the pairs save."""
     import torch
     from . import _binding as B
     tuner = tuner or Autotuner()
-    cands = [f"{g}/{w}" for w in bits for g in groups]
+    cands = [f"{g}/{w}/{t}" for t in tiles for w in bits for g in groups]
     fields = {"device": _device_name(), "n_bucket": size_bucket(n), "slices": int(slices)}
     hit = tuner.lookup("ozaki_schedule", fields, cands)
     if hit is None:
@@ -187,9 +187,10 @@ def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7,)
                          device="cuda")
 
         def measure(c):
-            g, w = (int(x) for x in c.split("/"))
+            g, w, t = (int(x) for x in c.split("/"))
             ctx.set_schedule("ozaki_group", g)
             ctx.set_schedule("ozaki_bits", w)
+            ctx.set_schedule("ozaki_tile_n", t)
 
             def run():
                 import ctypes
@@ -199,8 +200,8 @@ def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7,)
             return _event_seconds(run)
 
         hit = tuner.choose("ozaki_schedule", fields, cands, measure, reps)
-    g, w = (int(x) for x in hit.split("/"))
-    return {"ozaki_group": g, "ozaki_bits": w}
+    g, w, t = (int(x) for x in hit.split("/"))
+    return {"ozaki_group": g, "ozaki_bits": w, "ozaki_tile_n": t}
 
 
 def apply_schedule(ctx, schedule: dict) -> None:

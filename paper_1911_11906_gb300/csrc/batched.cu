@@ -62,6 +62,8 @@ int ensure_workers(fraclap_ctx* ctx, int W) {
     w->refine_tau = ctx->refine_tau;
     w->oz_group = ctx->oz_group;
     w->oz_bits = ctx->oz_bits;
+    w->oz_tile_n = ctx->oz_tile_n;
+    w->fp32_stages_tc = ctx->fp32_stages_tc;
   }
   return 0;
 }

@@ -209,16 +209,26 @@ ozaki_kernel(const __nv_bfloat16* __restrict__ SA, const __nv_bfloat16* __restri
 // thread one output row and 64 of the 128 columns.  Six 32 KB stages keep
 // enough bytes in flight to cover the L2 latency.
 // ----------------------------------------------------------------------------
-constexpr int TC_M = 128, TC_N = 128, TC_KB = 64, TC_STAGES = 6;
-constexpr int TC_A_BYTES = TC_M * TC_KB * 2, TC_B_BYTES = TC_N * TC_KB * 2;
-constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
-constexpr int TC_EPI_WARPS = 8, TC_EPI_COLS = TC_N * 4 / TC_EPI_WARPS;
+// The tile width TCN (128 or 256 columns of op(B)) is a schedule choice: a
+// 128 x 256 tile moves 48 KB of slices per 4.2 MFLOP k-block instead of
+// 32 KB per 2.1 MFLOP (1.33x fewer L2 bytes per flop), with four stages
+// instead of six and the two accumulators filling all 512 TMEM columns.
+constexpr int TC_M = 128, TC_KB = 64;
+constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
-constexpr uint32_t TC_TMEM_COLS = 2 * TC_N;  // two FP32 accumulators
+constexpr int TC_A_BYTES = TC_M * TC_KB * 2;
+template <int TCN>
+struct OzTile {
+  static constexpr int STAGES = (TCN == 256) ? 4 : 6;
+  static constexpr int B_BYTES = TCN * TC_KB * 2;
+  static constexpr int STAGE_BYTES = TC_A_BYTES + B_BYTES;
+  static constexpr int EPI_COLS = TCN * 4 / TC_EPI_WARPS;  // columns per epilogue thread
+  static constexpr uint32_t TMEM_COLS = 2 * TCN;           // two FP32 accumulators
+  // kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, M 128, N TCN.
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) |
+                                    ((uint32_t)(TC_M >> 4) << 24);
+};
 
-// kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, M 128, N 128.
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-                              ((uint32_t)(TC_M >> 4) << 24);
 // 2^e for e in [-1022, 1023], from its bit pattern.
 __device__ __forceinline__ double pow2i(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
@@ -229,20 +239,29 @@ __device__ __forceinline__ double pow2i(int e) { return __longlong_as_double((lo
 // block streams them (in the plain order a wave spans every tile row, so each
 // slice pair re-streams all of A).  With `lower`, a group only has the columns
 // up to its last row: tiles entirely above the diagonal are not enumerated.
-// The host sizes the grid with the same count (ozaki_tile_count).
-__host__ __device__ inline int64_t ozaki_tile_count(int TM, int TN, int G, bool lower) {
+// The host sizes the grid with the same count (ozaki_tile_count).  Tiles
+// are TCM rows by TCN columns; with `lower`, a group of tile rows ending at
+// tile row r needs the tile columns that start at or below row r TCM + TCM - 1.
+__host__ __device__ inline int ozaki_group_cols(int g0, int Gg, int TN, int TCM, int TCN, bool lower) {
+  if (!lower) return TN;
+  const int64_t last_row = (int64_t)(g0 + Gg - 1) * TCM + TCM - 1;
+  const int64_t c = last_row / TCN + 1;
+  return (int)(c < TN ? c : TN);
+}
+__host__ __device__ inline int64_t ozaki_tile_count(int TM, int TN, int G, bool lower, int TCM, int TCN) {
   int64_t tot = 0;
   for (int g0 = 0; g0 < TM; g0 += G) {
     const int Gg = (TM - g0 < G) ? TM - g0 : G;
-    tot += (int64_t)Gg * (lower ? ((g0 + Gg < TN) ? g0 + Gg : TN) : TN);
+    tot += (int64_t)Gg * ozaki_group_cols(g0, Gg, TN, TCM, TCN, lower);
   }
   return tot;
 }
-__device__ __forceinline__ void ozaki_tile_of(int64_t idx, int TM, int TN, int G, bool lower, int* tm, int* tn) {
+__device__ __forceinline__ void ozaki_tile_of(int64_t idx, int TM, int TN, int G, bool lower, int TCM, int TCN,
+                                              int* tm, int* tn) {
   int64_t base = 0;
   for (int g0 = 0; g0 < TM; g0 += G) {
     const int Gg = (TM - g0 < G) ? TM - g0 : G;
-    const int ncol = lower ? ((g0 + Gg < TN) ? g0 + Gg : TN) : TN;
+    const int ncol = ozaki_group_cols(g0, Gg, TN, TCM, TCN, lower);
     const int64_t cnt = (int64_t)Gg * ncol;
     if (idx < base + cnt) {
       const int r = (int)(idx - base);
@@ -256,12 +275,17 @@ __device__ __forceinline__ void ozaki_tile_of(int64_t idx, int TM, int TN, int G
   *tn = 0;
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <int TCN>
+__global__ void __maxnreg__(200)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const int* __restrict__ ea, const int* __restrict__ eb, int64_t M, int64_t N, int64_t Kp,
                 int s, int bits, int64_t chunk, double alpha, double beta, double* C, int64_t ldc,
                 int lower, int group, long long limit,
                 int32_t* status) {
+  constexpr int TC_N = TCN, TC_STAGES = OzTile<TCN>::STAGES, TC_B_BYTES = OzTile<TCN>::B_BYTES;
+  constexpr int TC_STAGE_BYTES = OzTile<TCN>::STAGE_BYTES, TC_EPI_COLS = OzTile<TCN>::EPI_COLS;
+  constexpr uint32_t TC_TMEM_COLS = OzTile<TCN>::TMEM_COLS, TC_IDESC = OzTile<TCN>::IDESC;
+  (void)TC_B_BYTES;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES];
@@ -271,7 +295,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int TM = (int)((M + TC_M - 1) / TC_M), TN = (int)((N + TC_N - 1) / TC_N);
   int tm, tn;
-  ozaki_tile_of((int64_t)blockIdx.x, TM, TN, group, lower != 0, &tm, &tn);
+  ozaki_tile_of((int64_t)blockIdx.x, TM, TN, group, lower != 0, TC_M, TC_N, &tm, &tn);
   if (tm >= TM || tn >= TN) return;
   const int64_t m0 = (int64_t)tm * TC_M, n0 = (int64_t)tn * TC_N;
   if (lower && m0 + TC_M - 1 < n0) return;  // whole CTA: tile above the diagonal
@@ -392,34 +416,6 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 #pragma unroll
     for (int j = 0; j < TC_EPI_COLS; ++j) acc[j] = 0;
     bool first = true;
-    auto fold = [&](int dg) {
-      const int sh = bits * (dg + 2);
-      if (row < M) {
-        // opaque copies of the base pointers: the per-column addresses are
-        // formed here, not hoisted out of the diagonal loop into registers
-        const int* ebp;
-        double* cb;
-        asm volatile("mov.b64 %0, %1;" : "=l"(ebp) : "l"(eb + n0 + cbase));
-        asm volatile("mov.b64 %0, %1;" : "=l"(cb) : "l"(C + row + (n0 + cbase) * ldc));
-#pragma unroll
-        for (int j = 0; j < TC_EPI_COLS; ++j) {
-          const int64_t col = n0 + cbase + j;
-          if (col < N && !(lower && row < col)) {
-            // acc 2^e in two exact power-of-two steps (each factor normal);
-            // beyond |e| = 2044 the result is 0 or infinite either way
-            int e = er + ebp[j] - sh;
-            e = (e < -2044) ? -2044 : (e > 2044 ? 2044 : e);
-            const int e1 = e / 2;
-            const double v = alpha * (((double)acc[j] * pow2i(e1)) * pow2i(e - e1));
-            double* cp = cb + j * ldc;
-            *cp = first ? ((beta == 0.0) ? v : v + beta * *cp) : *cp + v;
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < TC_EPI_COLS; ++j) acc[j] = 0;
-      first = false;
-    };
     int chunk_i = 0;
     bool ok = true;
     for (int dg = 0; dg < s && ok; ++dg) {
@@ -444,13 +440,40 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[buf]);
-          if (++pending == 127) {
-            fold(dg);
+          // one call site (the fold is inlined once): after 127 chunks, and
+          // after the last chunk of the diagonal
+          if (++pending == 127 || (p == dg && c == nchunk - 1)) {
+            // fold: acc 2^(e_i + f_j - bits (dg + 2)) into C in FP64, then restart the sums
+            const int sh = bits * (dg + 2);
+            if (row < M) {
+              // opaque copies of the base pointers: the per-column addresses are
+              // formed here, not hoisted out of the diagonal loop into registers
+              const int* ebp;
+              double* cb;
+              asm volatile("mov.b64 %0, %1;" : "=l"(ebp) : "l"(eb + n0 + cbase));
+              asm volatile("mov.b64 %0, %1;" : "=l"(cb) : "l"(C + row + (n0 + cbase) * ldc));
+#pragma unroll
+              for (int j = 0; j < TC_EPI_COLS; ++j) {
+                const int64_t col = n0 + cbase + j;
+                if (col < N && !(lower && row < col)) {
+                  // acc 2^e in two exact power-of-two steps (each factor normal);
+                  // beyond |e| = 2044 the result is 0 or infinite either way
+                  int e = er + ebp[j] - sh;
+                  e = (e < -2044) ? -2044 : (e > 2044 ? 2044 : e);
+                  const int e1 = e / 2;
+                  const double v = alpha * (((double)acc[j] * pow2i(e1)) * pow2i(e - e1));
+                  double* cp = cb + j * ldc;
+                  *cp = first ? ((beta == 0.0) ? v : v + beta * *cp) : *cp + v;
+                }
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < TC_EPI_COLS; ++j) acc[j] = 0;
+            first = false;
             pending = 0;
           }
         }
       }
-      if (ok) fold(dg);
     }
     if (!ok) {
       if (lane == 0) atomicCAS(status, 0, FRACLAP_ERR_TIMEOUT);
@@ -478,6 +501,25 @@ bool slice_map(CUtensorMap* map, const __nv_bfloat16* S, int64_t rows, int64_t K
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+template <int TCN>
+int launch_tc(fraclap_ctx* ctx, const __nv_bfloat16* SA, const __nv_bfloat16* SB, const int* ea, const int* eb,
+              int64_t M, int64_t N, int64_t Kp, int sl, int bits, int64_t chunk, double alpha, double beta,
+              double* C, int64_t ldc, bool lower, cudaStream_t st) {
+  CUtensorMap ma, mb;
+  FL_CHECK(ctx, slice_map(&ma, SA, M, Kp, sl, TC_M) && slice_map(&mb, SB, N, Kp, sl, TCN), FRACLAP_ERR_CUDA,
+           "ozaki_gemm: tensor map encoding failed");
+  const size_t smem = (size_t)OzTile<TCN>::STAGES * OzTile<TCN>::STAGE_BYTES + 1024;
+  FL_CUDA(ctx, cudaFuncSetAttribute(ozaki_tc_kernel<TCN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int TM = (int)cdiv(M, TC_M), TN = (int)cdiv(N, TCN);
+  const int G = std::max(1, std::min(ctx->oz_group > 0 ? ctx->oz_group : TM, TM));
+  const int64_t tiles = ozaki_tile_count(TM, TN, G, lower, TC_M, TCN);
+  FL_CHECK(ctx, tiles <= INT32_MAX, FRACLAP_ERR_UNSUPPORTED, "ozaki_gemm: too many tiles");
+  ozaki_tc_kernel<TCN><<<(unsigned)tiles, TC_THREADS, smem, st>>>(ma, mb, ea, eb, M, N, Kp, sl, bits, chunk, alpha,
+                                                                  beta, C, ldc, lower ? 1 : 0, G, ctx->wait_cycles,
+                                                                  ctx->d_status);
+  return 0;
+}
+
 }  // namespace
 
 size_t ozaki_ws(int64_t M, int64_t N, int64_t K, int s) {
@@ -526,18 +568,11 @@ int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t
   count_launch(ctx);
   StageTimer tm(ctx, kStageSliceProducts, st);
   if (ctx->tensor_route == 1) {
-    CUtensorMap ma, mb;
-    FL_CHECK(ctx, slice_map(&ma, SA, M, Kp, sl, TC_M) && slice_map(&mb, SB, N, Kp, sl, TC_N),
-             FRACLAP_ERR_CUDA, "ozaki_gemm: tensor map encoding failed");
-    const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
-    FL_CUDA(ctx, cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int TM = (int)cdiv(M, TC_M), TN = (int)cdiv(N, TC_N);
-    const int G = std::max(1, std::min(ctx->oz_group > 0 ? ctx->oz_group : TM, TM));
-    const int64_t tiles = ozaki_tile_count(TM, TN, G, lower);
-    FL_CHECK(ctx, tiles <= INT32_MAX, FRACLAP_ERR_UNSUPPORTED, "ozaki_gemm: too many tiles");
-    ozaki_tc_kernel<<<(unsigned)tiles, TC_THREADS, smem, st>>>(ma, mb, ea, eb, M, N, Kp, sl, bits, chunk, alpha,
-                                                               beta, C, ldc, lower ? 1 : 0, G, ctx->wait_cycles,
-                                                               ctx->d_status);
+    if (ctx->oz_tile_n == 256) {
+      FL_TRY(launch_tc<256>(ctx, SA, SB, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc, lower, st));
+    } else {
+      FL_TRY(launch_tc<128>(ctx, SA, SB, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc, lower, st));
+    }
   } else {
     dim3 grid((unsigned)cdiv(M, OZ_BM), (unsigned)cdiv(N, OZ_BN));
     ozaki_kernel<<<grid, OZ_NT, 0, st>>>(SA, SB, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc, lower);
@@ -588,6 +623,10 @@ extern "C" int fraclap_set_schedule(fraclap_ctx* ctx, int knob, int value) {
       FL_CHECK(ctx, value == 0 || value == 1, FRACLAP_ERR_INVALID_ARG, "set_schedule: FP32 stage route must be 0 or 1");
       ctx->fp32_stages_tc = value;
       return 0;
+    case FRACLAP_SCHED_OZAKI_TILE_N:
+      FL_CHECK(ctx, value == 128 || value == 256, FRACLAP_ERR_INVALID_ARG, "set_schedule: tile width must be 128 or 256");
+      ctx->oz_tile_n = value;
+      return 0;
     default:
       return set_error(ctx, FRACLAP_ERR_INVALID_ARG, "set_schedule: unknown knob %d", knob);
   }
@@ -599,6 +638,7 @@ extern "C" int fraclap_get_schedule(const fraclap_ctx* ctx, int knob) {
     case FRACLAP_SCHED_OZAKI_GROUP: return ctx->oz_group;
     case FRACLAP_SCHED_OZAKI_BITS: return ctx->oz_bits;
     case FRACLAP_SCHED_FP32_STAGES: return ctx->fp32_stages_tc;
+    case FRACLAP_SCHED_OZAKI_TILE_N: return ctx->oz_tile_n;
     default: return FRACLAP_ERR_INVALID_ARG;
   }
 }

@@ -41,12 +41,13 @@ def test_ozaki_schedule_is_tuned_cached_and_applied(tmp_path):
     from paper_1911_11906_gb300 import autotune as A
     import paper_1911_11906_gb300 as F
     path = str(tmp_path / "tune.json")
-    sched = A.best_ozaki_schedule(640, groups=(0, 2), bits=(7, 8), tuner=A.Autotuner(path), reps=1)
-    assert sched["ozaki_group"] in (0, 2) and sched["ozaki_bits"] in (7, 8)
+    sched = A.best_ozaki_schedule(640, groups=(0, 2), bits=(7, 8), tiles=(128, 256), tuner=A.Autotuner(path),
+                                  reps=1)
+    assert sched["ozaki_group"] in (0, 2) and sched["ozaki_bits"] in (7, 8) and sched["ozaki_tile_n"] in (128, 256)
     entries = json.load(open(path))["entries"]
     (val,) = [v for k, v in entries.items() if k.startswith("ozaki_schedule:")]
-    assert set(val["seconds"]) == {"0/7", "2/7", "0/8", "2/8"}
-    assert A.best_ozaki_schedule(700, groups=(0, 2), bits=(7, 8), tuner=A.Autotuner(path)) == sched
+    assert set(val["seconds"]) == {f"{g}/{w}/{t}" for g in (0, 2) for w in (7, 8) for t in (128, 256)}
+    assert A.best_ozaki_schedule(700, groups=(0, 2), bits=(7, 8), tiles=(128, 256), tuner=A.Autotuner(path)) == sched
     ctx = F.Context()
     A.apply_schedule(ctx, sched)
     assert ctx.get_schedule("ozaki_group") == sched["ozaki_group"]

@@ -139,13 +139,16 @@ def test_dgemm_ozaki_is_fp64_accurate(ta, tb, m, n, k):
     assert np.max(np.abs(got - ref) / (rowmax + 1e-300)) <= 1e-15
 
 
-@pytest.mark.parametrize("group,bits", [(0, 7), (1, 7), (3, 8), (8, 8), (8, 7)])
-@pytest.mark.parametrize("ta,m,n,k", [(True, 300, 260, 1000), (False, 520, 130, 2000), (True, 129, 385, 257)])
-def test_dgemm_ozaki_schedules_agree(group, bits, ta, m, n, k):
-    """Every tile order (raster group) and digit width gives an FP64-accurate
-    product (against math.fsum at sampled entries and the FP64 product
-    everywhere), and tile orders with the same digit width give the same
-    bits: only the order of the tiles over the CTAs differs."""
+@pytest.mark.parametrize("group,bits,tile_n", [(0, 7, 128), (1, 7, 128), (3, 8, 128), (8, 8, 128), (8, 7, 128),
+                                               (0, 7, 256), (4, 7, 256), (2, 8, 256)])
+@pytest.mark.parametrize("ta,m,n,k", [(True, 300, 260, 1000), (False, 520, 130, 2000), (True, 129, 385, 257),
+                                      (True, 640, 600, 300)])
+def test_dgemm_ozaki_schedules_agree(group, bits, tile_n, ta, m, n, k):
+    """Every tile order (raster group), tile width and digit width gives an
+    FP64-accurate product (against math.fsum at sampled entries and the FP64
+    product everywhere), and schedules with the same digit width give the
+    same bits: only the tiling and the order of the tiles over the CTAs
+    differ, not the sums of any output element."""
     import math
     F = _F()
     rng = np.random.default_rng(m + 3 * n + k + group)
@@ -155,7 +158,9 @@ def test_dgemm_ozaki_schedules_agree(group, bits, ta, m, n, k):
     ctx = F.Context(wait_timeout_s=2.0)
     ctx.set_schedule("ozaki_group", group)
     ctx.set_schedule("ozaki_bits", bits)
+    ctx.set_schedule("ozaki_tile_n", tile_n)
     assert ctx.get_schedule("ozaki_group") == group and ctx.get_schedule("ozaki_bits") == bits
+    assert ctx.get_schedule("ozaki_tile_n") == tile_n
     got = F.dgemm_ozaki(_colmajor(A), _colmajor(B), trans_a=ta, ctx=ctx).cpu().numpy()
     scale = np.abs(opA).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * k
     assert np.max(np.abs(got - opA @ B) / scale) <= 1e-15
@@ -171,7 +176,8 @@ def test_dgemm_ozaki_schedules_agree(group, bits, ta, m, n, k):
 def test_schedule_knobs_reject_bad_values():
     F = _F()
     ctx = F.Context()
-    for knob, bad in (("ozaki_group", -1), ("ozaki_bits", 6), ("ozaki_bits", 9)):
+    for knob, bad in (("ozaki_group", -1), ("ozaki_bits", 6), ("ozaki_bits", 9), ("ozaki_tile_n", 192),
+                      ("fp32_stages_tc", 2)):
         with pytest.raises(F.FraclapError):
             ctx.set_schedule(knob, bad)
     assert ctx.lib.fraclap_set_schedule(ctx.handle, 99, 1) == -1

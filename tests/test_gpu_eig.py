@@ -126,13 +126,14 @@ def _csr_cuda(A):
     return (torch.from_numpy(A.rowptr).cuda(), torch.from_numpy(A.col).cuda(), torch.from_numpy(A.val).cuda())
 
 
-@pytest.mark.parametrize("tc", [0, 1])
+@pytest.mark.parametrize("tc,tile_n", [(0, 128), (1, 128), (0, 256)])
 @pytest.mark.parametrize("which,b,iters", [("square23", 32, 6), ("ellipse36", 32, 6), ("ellipse36", 64, 6),
                                             ("ellipse64", 32, 6), ("ellipse48", 16, 6), ("square9", 8, 6),
                                             ("cube6", 32, 6)])
-def test_eig_full_mixed_refined_vs_oracle(which, b, iters, tc):
+def test_eig_full_mixed_refined_vs_oracle(which, b, iters, tc, tile_n):
     """FP32 stages (FMA kernel, or three TF32 products on the tensor cores
-    with tc = 1) + Ogita-Aishima refinement reach the FP64 tolerances."""
+    with tc = 1) + Ogita-Aishima refinement (slice products on 128- or
+    256-column tiles) reach the FP64 tolerances."""
     F = _F()
     if which.startswith("square"):
         p = I.square_problem(int(which[6:]))
@@ -146,6 +147,7 @@ def test_eig_full_mixed_refined_vs_oracle(which, b, iters, tc):
     lam_o, V_o = O.eig_full(D)
     ctx = F.Context(band_width=b)
     ctx.set_schedule("fp32_stages_tc", tc)
+    ctx.set_schedule("ozaki_tile_n", tile_n)
     lam, V = F.eig_full_mixed(_colmajor(D), *_csr_cuda(A), refine_iters=iters, ctx=ctx)
     lam, V = lam.cpu().numpy(), V.cpu().numpy()
     _check_decomposition(D, lam_o, lam, V)
