@@ -100,56 +100,70 @@ __global__ void frob_norms(const double* S, int64_t lds, const double* R, int64_
   }
 }
 
-// y += M x for a symmetric M stored in its lower triangle: one 32 x 32 tile
-// (I >= J) per block; the tile contributes L_IJ x_J to y_I and, off the
-// diagonal, L_IJ^T x_I to y_J (atomic adds).  y must be zeroed (or hold the
-// diagonal shift term) beforehand.
-__global__ void symv_lower_tiles(const double* M, int64_t ldm, int64_t n, const double* x, double* y) {
-  __shared__ double t[32][33];
-  // tile index -> (I, J) with I >= J over the lower tile triangle
-  const int64_t q = blockIdx.x;
-  int64_t I = (int64_t)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
-  while (I * (I + 1) / 2 > q) --I;
-  while ((I + 1) * (I + 2) / 2 <= q) ++I;
-  const int64_t J = q - I * (I + 1) / 2;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  for (int r = ty; r < 32; r += 8) {
-    const int64_t gi = I * 32 + tx, gj = J * 32 + r;
-    double v = 0.0;
-    if (gi < n && gj < n && (I != J || tx >= r)) v = M[gi + gj * ldm];
-    t[tx][r] = v;  // t[i][j] = L(I*32+i, J*32+j)
-  }
-  __syncthreads();
-  if (ty == 0) {  // y_I += L_IJ x_J
+
+// y = M x for the symmetric M stored in its lower triangle, in two strip
+// passes of one launch (no atomics): CTA b < nt sums row block b over its
+// lower part, y_row(i) = sum_{j <= i} M(i, j) x_j; CTA nt + b sums column
+// block b over its strictly lower part, y_col(j) = sum_{i > j} M(i, j) x_i.
+// Thread (row lane, column group w) keeps its partial sums across the
+// 32 x 32 tiles of its strip (coalesced 256-byte column segments) and
+// reduces once at the end.  Block 256 = 32 x 8, grid 2 nt.
+__global__ void __launch_bounds__(256) symv_strips(const double* M, int64_t ldm, int64_t n, const double* x,
+                                                   double* yrow, double* ycol) {
+  __shared__ double red[8][33];
+  const int64_t nt = (n + 31) / 32;
+  const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if ((int64_t)blockIdx.x < nt) {
+    const int64_t I = blockIdx.x, gi = I * 32 + tx;
     double s = 0.0;
-    for (int j = 0; j < 32; ++j) {
-      const int64_t gj = J * 32 + j;
-      if (gj < n) s = fma(t[tx][j], x[gj], s);
+    if (gi < n)
+      for (int64_t J = 0; J <= I; ++J)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t gj = J * 32 + w * 4 + q;
+          if (gj <= gi) s = fma(M[gi + gj * ldm], x[gj], s);
+        }
+    red[w][tx] = s;
+    __syncthreads();
+    if (w == 0 && gi < n) {
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t += red[q][tx];
+      yrow[gi] = t;
     }
-    const int64_t gi = I * 32 + tx;
-    if (gi < n) atomicAdd(y + gi, s);
-  } else if (ty == 1) {  // y_J += L_IJ^T x_I (strictly lower part)
-    double s = 0.0;
-    for (int i = 0; i < 32; ++i) {
-      const int64_t gi = I * 32 + i;
-      if (gi < n && (I != J || i > tx)) s = fma(t[i][tx], x[gi], s);
+  } else {
+    const int64_t J = (int64_t)blockIdx.x - nt;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t I = J; I < nt; ++I) {
+      const int64_t gi = I * 32 + tx;
+      if (gi >= n) continue;
+      const double xi = x[gi];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t gj = J * 32 + w * 4 + q;
+        if (gi > gj) acc[q] = fma(M[gi + gj * ldm], xi, acc[q]);
+      }
     }
-    const int64_t gj = J * 32 + tx;
-    if (gj < n) atomicAdd(y + gj, s);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double v = warp_sum(acc[q]);
+      const int64_t gj = J * 32 + w * 4 + q;
+      if (tx == 0 && gj < n) ycol[gj] = v;
+    }
   }
 }
 
-// y = -shift .* x (or 0).
-__global__ void symv_init(const double* shift, const double* x, int64_t n, double* y) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = shift ? -shift[i] * x[i] : 0.0;
-}
-
-// x = y / ||y||, est = ||y|| (one block).
-__global__ void normalize_vec(const double* y, int64_t n, double* x, double* est) {
+// y = y_row + y_col - shift .* x, then x = y / ||y||, est = ||y|| (one block;
+// y is formed in y_row before x is overwritten).
+__global__ void combine_normalize(double* yrow, const double* ycol, const double* shift, int64_t n, double* x,
+                                  double* est) {
   __shared__ double red[32];
   double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += y[i] * y[i];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double y = yrow[i] + ycol[i] - (shift ? shift[i] * x[i] : 0.0);
+    yrow[i] = y;
+    s += y * y;
+  }
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -161,9 +175,10 @@ __global__ void normalize_vec(const double* y, int64_t n, double* x, double* est
   __syncthreads();
   const double nrm = sqrt(red[0]);
   const double inv = (nrm > 0.0) ? 1.0 / nrm : 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = y[i] * inv;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = yrow[i] * inv;
   if (threadIdx.x == 0) *est = nrm;
 }
+
 
 __global__ void start_vec(double* x, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -827,11 +842,10 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
         start_vec<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(xv, n);
         count_launch(ctx);
         const int64_t nt = cdiv(n, 32);
+        double* yc = AX + n;  // second n doubles of the same scratch
         for (int pit = 0; pit < 12; ++pit) {
-          symv_init<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(shift, xv, n, yv);
-          symv_lower_tiles<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(M, n, n, xv, yv);
-          normalize_vec<<<1, 1024, 0, st>>>(yv, n, xv, scal + 4 + which);
-          count_launch(ctx);
+          symv_strips<<<(unsigned)(2 * nt), 256, 0, st>>>(M, n, n, xv, yv, yc);
+          combine_normalize<<<1, 1024, 0, st>>>(yv, yc, shift, n, xv, scal + 4 + which);
           count_launch(ctx);
           count_launch(ctx);
         }
