@@ -40,23 +40,31 @@ constexpr int OZ_KPAD = 64;  // slice rows padded to a multiple of 64 (one TMA b
 constexpr int OZ_LDS = OZ_BK / 2 + 4;  // shared row stride in 32-bit words (padded)
 
 // Exponent of the largest |entry| of each row of op(A) (rows = M, length K).
-// One block per row.
+// One block per row.  The magnitudes are compared as the integers of their
+// IEEE bit patterns with the sign cleared (the same order as the values), so
+// the FP64 pipe is not used.
 __global__ void row_exponents(const double* A, int64_t lda, bool trans, int64_t K, int* ex) {
   const int64_t i = blockIdx.x;
-  double m = 0.0;
+  unsigned long long m = 0;
   for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
     const double v = trans ? A[k + i * lda] : A[i + k * lda];
-    m = fmax(m, fabs(v));
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    m = u > m ? u : m;
   }
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ unsigned long long red[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (unsigned w = 0; w < blockDim.x / 32; ++w) t = fmax(t, red[w]);
+    unsigned long long t = 0;
+    for (unsigned w = 0; w < blockDim.x / 32; ++w) t = red[w] > t ? red[w] : t;
     int e = 0;
-    if (t > 0.0) frexp(t, &e);  // t = f 2^e, f in [0.5, 1): every |entry| < 2^e
+    const int E = (int)(t >> 52);
+    if (E > 0) e = E - 1022;  // t = f 2^e, f in [0.5, 1): every |entry| < 2^e
+    else if (t != 0) frexp(__longlong_as_double((long long)t), &e);  // subnormal maximum
     ex[i] = e;
   }
 }
@@ -80,7 +88,14 @@ __global__ void make_slices(const double* A, int64_t lda, bool trans, int64_t M,
     if (trans) { k = t % Kp; i = t / Kp; } else { i = t % M; k = t / M; }
     const double a = (k < K) ? (trans ? A[k + i * lda] : A[i + k * lda]) : 0.0;
     if (tb <= 64) {
-      const unsigned long long u = __double2ull_rz(ldexp(fabs(a), tb - ex[i]));
+      // floor(|a| 2^(tb - e)) from the bits: |a| = m 2^(E - 1075) (m with
+      // its hidden bit; subnormals take E = 1), shifted exactly; below 2^tb
+      // because |a| < 2^e
+      const unsigned long long bitsA = (unsigned long long)__double_as_longlong(a);
+      const int E = (int)((bitsA >> 52) & 0x7FF);
+      const unsigned long long mant = (bitsA & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+      const int sh = (E ? E : 1) - 1075 + tb - ex[i];
+      const unsigned long long u = (sh >= 64 || sh <= -64) ? 0ull : (sh >= 0 ? (mant << sh) : (mant >> -sh));
       const float sg = (a < 0.0) ? -1.0f : 1.0f;
       for (int p = 0; p < s; ++p) {
         const unsigned long long dgt = (u >> (bits * (s - 1 - p))) & mask;
