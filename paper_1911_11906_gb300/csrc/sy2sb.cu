@@ -201,18 +201,32 @@ panel_qr_cluster_kernel(T* P, int64_t ldp, int64_t m, int bw, T* Vout, int64_t l
   for (int c = 0; c < nref; ++c) {
     double* mine = part[c & 1];
     const int64_t r0 = (c > rb) ? c - rb : 0;  // first local row with global row >= c
-    for (int j = c + warp; j < bw; j += nwarp) {
+    {
       // per-CTA partial dots in the working precision (FP64 work on ~m/16 rows
-      // would occupy GB300's narrow FP64 pipe); the cluster sum is FP64
-      T sum = T(0);
+      // would occupy GB300's narrow FP64 pipe); the cluster sum is FP64.  A
+      // warp takes columns j = c + warp + 8 q, all in one pass over its rows
+      // (the pivot column read once, eight independent sums).
+      constexpr int QMAX = 64 / 8;
+      T sum[QMAX];
+#pragma unroll
+      for (int q = 0; q < QMAX; ++q) sum[q] = T(0);
       for (int64_t r = r0 + lane; r < nr; r += 32) {
         const int64_t gr = rb + r;
-        if (j == c && gr == c) continue;  // g_c is the tail sum of squares (rows > c)
-        sum += S[r + c * ld] * S[r + j * ld];
+        const T pc = S[r + c * ld];
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+          const int j = c + warp + nwarp * q;
+          if (j < bw && !(j == c && gr == c)) sum[q] += pc * S[r + j * ld];  // g_c: rows > c only
+        }
       }
 #pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      if (lane == 0) mine[j] = (double)sum;
+      for (int q = 0; q < QMAX; ++q) {
+        T v = sum[q];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int j = c + warp + nwarp * q;
+        if (lane == 0 && j < bw) mine[j] = (double)v;
+      }
     }
     for (int j = c + tid; j < bw; j += PQR_NT) mine[bw + j] = (c >= rb && c < re) ? (double)S[(c - rb) + j * ld] : 0.0;
     cluster.sync();
