@@ -185,6 +185,7 @@ panel_qr_cluster_kernel(T* P, int64_t ldp, int64_t m, int bw, T* Vout, int64_t l
   __shared__ double part[2][2 * 64];
   __shared__ double red[2 * 64 + 4];
   __shared__ double sw[64];
+  __shared__ T swt[64];  // sw in the working precision (converted once per column, not once per row)
   __shared__ double s_coef[4];
   const unsigned rank = cluster.block_rank(), CS = cluster.num_blocks();
   const int64_t rb = (int64_t)rank * rows_per_cta;
@@ -261,6 +262,7 @@ panel_qr_cluster_kernel(T* P, int64_t ldp, int64_t m, int bw, T* Vout, int64_t l
     for (int j = c + 1 + tid; j < bw; j += PQR_NT) {
       const double g = red[j - c], pc = red[64 + (j - c)];
       sw[j] = (tu == 0.0) ? 0.0 : tu * (g - beta * pc) * inv_v0;
+      swt[j] = (T)sw[j];
     }
     __syncthreads();
     for (int64_t r = r0 + tid; r < nr; r += PQR_NT) {
@@ -275,7 +277,7 @@ panel_qr_cluster_kernel(T* P, int64_t ldp, int64_t m, int bw, T* Vout, int64_t l
       }
       if (tu != 0.0) {
         const T vt = (T)vr;
-        for (int j = c + 1; j < bw; ++j) S[r + j * ld] -= vt * (T)sw[j];
+        for (int j = c + 1; j < bw; ++j) S[r + j * ld] -= vt * swt[j];
       }
     }
     __syncthreads();
