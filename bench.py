@@ -739,12 +739,16 @@ def run_apply_bench(args, diffusion=False, steps=None, warmup=None):
     import oracle as O
     import paper_1911_11906_gb300 as F
     from paper_1911_11906_gb300 import inputs as I
+    from paper_1911_11906_gb300 import autotune
     p = I.apply_at_scale_problem()
     ctx = F.Context(band_width=64)
     mask = torch.from_numpy(p.mask).cuda()
     asm = F.fd_assemble(mask, p.h, ctx=ctx)
     lam, V = F.eig_full_mixed(asm["A"], asm["rowptr"], asm["col"], asm["val"], refine_iters=6, ctx=ctx)
     del asm
+    # tile order and width of the sliced products from the autotuner (V^T F shape, 6 slices)
+    sched = {} if args.no_autotune else autotune.best_ozaki_schedule(p.n, slices=6, cols=p.F.shape[1])
+    autotune.apply_schedule(ctx, sched)
     Fd = torch.from_numpy(np.ascontiguousarray(p.F.T)).cuda().t()
     pf = torch.from_numpy(p.pair_f.astype(np.int32)).cuda()
     pa = torch.from_numpy(p.pair_alpha.astype(np.float64)).cuda()
@@ -819,7 +823,8 @@ def run_apply_bench(args, diffusion=False, steps=None, warmup=None):
                  "config": {"workload": workload, "n": p.n, "pairs": k, "products": "6 BF16 slices on tcgen05",
                             "l2_policy": "inputs larger than L2 (V is %.1f GB)" % (8 * p.n * p.n / 1e9)},
                  "fp64_products": {"value": lines[0]["value"], "ms_per_step": lines[0]["ms_per_step"]},
-                 "cuda_graph": graph, "accuracy": acc})
+                 "cuda_graph": graph, "accuracy": acc,
+                 "slice_product_schedule": dict(sched, source="autotuner") if sched else "defaults"})
     return head
 
 

@@ -163,11 +163,12 @@ def best_workers(problems: list, candidates=(4, 8, 16, 32), tuner: Autotuner | N
 
 
 def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7,), tiles=(128, 256),
-                        tuner: Autotuner | None = None, reps: int = 2) -> dict:
+                        tuner: Autotuner | None = None, reps: int = 2, cols: int | None = None) -> dict:
     """Tile order (raster group of tile rows), tile width and digit width of
     the slice-product kernel for the refinement's residual product X^T X of an
-    n x n X with `slices` BF16 slices, measured on a seeded matrix of that
-    size through fraclap_dgemm_ozaki.  Returns {"ozaki_group": G,
+    n x n X with `slices` BF16 slices (or, with cols, the apply's product
+    V^T F of an n x n V and an n x cols F), measured on seeded matrices of
+    that size through fraclap_dgemm_ozaki.  Returns {"ozaki_group": G,
     "ozaki_bits": w, "ozaki_tile_n": t}; apply it with apply_schedule(ctx, ...).  The digit
     widths tried default to 7 alone: 8-bit digits (28 instead of 36 slice
     pairs for 7 slices) measured the same kernel time on a GB300 at n = 4096
@@ -177,13 +178,17 @@ def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7,)
     tuner = tuner or Autotuner()
     cands = [f"{g}/{w}/{t}" for t in tiles for w in bits for g in groups]
     fields = {"device": _device_name(), "n_bucket": size_bucket(n), "slices": int(slices)}
+    if cols is not None:
+        fields["cols_bucket"] = size_bucket(cols)
+    nc = n if cols is None else int(cols)
     hit = tuner.lookup("ozaki_schedule", fields, cands)
     if hit is None:
         gen = torch.Generator(device="cpu").manual_seed(n)
         X = (torch.randn(n, n, generator=gen, dtype=torch.float64) / n ** 0.5).cuda()
-        C = torch.empty(n, n, dtype=torch.float64, device="cuda").t()
+        Y = X if cols is None else (torch.randn(nc, n, generator=gen, dtype=torch.float64) / n ** 0.5).cuda().t()
+        C = torch.empty(nc, n, dtype=torch.float64, device="cuda").t()
         ctx = B.Context()
-        ws = torch.empty(ctx.lib.fraclap_dgemm_ozaki_workspace_bytes(n, n, n, slices), dtype=torch.uint8,
+        ws = torch.empty(ctx.lib.fraclap_dgemm_ozaki_workspace_bytes(n, nc, n, slices), dtype=torch.uint8,
                          device="cuda")
 
         def measure(c):
@@ -195,7 +200,7 @@ def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7,)
             def run():
                 import ctypes
                 st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-                ctx.check(ctx.lib.fraclap_dgemm_ozaki(ctx.handle, 1, 0, n, n, n, 1.0, B._ptr(X), n, B._ptr(X), n,
+                ctx.check(ctx.lib.fraclap_dgemm_ozaki(ctx.handle, 1, 0, n, nc, n, 1.0, B._ptr(X), n, B._ptr(Y), n,
                                                       0.0, B._ptr(C), n, int(slices), B._ptr(ws), ws.numel(), st))
             return _event_seconds(run)
 
