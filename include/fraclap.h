@@ -429,8 +429,8 @@ int fraclap_wait_selftest(fraclap_ctx* ctx, int which, fraclap_stream_t stream);
 
 /* Sustained throughput of the FMA pipe (precision 64: DFMA, 32: FFMA) in
  * flop/s, measured by independent FMA chains over 8 CTAs of 256 threads per
- * SM (iters steps each: 2^16 FP64 or 2^20 FP32 steps take a few tenths of a
- * second on a GB300), one untimed launch
+ * SM (iters steps each: 2^14 FP64 or 2^18 FP32 steps take under a tenth
+ * of a second on a GB300), one untimed launch
  * then one timed with CUDA events; synchronises `stream`.  The peaks the
  * SIMT FP64 and FP32 kernels are measured against (no counterpart in the
  * paper). */
@@ -578,9 +578,13 @@ int fraclap_partition_spectrum(fraclap_ctx* ctx, int64_t n, const int64_t* rowpt
  *    2^-22 per product instead of 2^-24) [0].
  *  FRACLAP_SCHED_OZAKI_TILE_N: columns of the slice-product kernel's output
  *    tile, 128 or 256 (rows are 128) [128].
+ *  FRACLAP_SCHED_Q2_PARTS: at half-bandwidth 64, the lanes that share one
+ *    column's window of the stage-2 back-transformation: 4, 8 or 16 (16, 8 or
+ *    4 rows per lane; more parts give more warps over the same columns), or 0
+ *    for the default (4 in FP32, 8 in FP64) [0].
  * ---------------------------------------------------------------------- */
 enum { FRACLAP_SCHED_OZAKI_GROUP = 0, FRACLAP_SCHED_OZAKI_BITS = 1, FRACLAP_SCHED_FP32_STAGES = 2,
-       FRACLAP_SCHED_OZAKI_TILE_N = 3 };
+       FRACLAP_SCHED_OZAKI_TILE_N = 3, FRACLAP_SCHED_Q2_PARTS = 4 };
 int fraclap_set_schedule(fraclap_ctx* ctx, int knob, int value);
 int fraclap_get_schedule(const fraclap_ctx* ctx, int knob);
 

@@ -181,7 +181,7 @@ class Context:
         """frac_apply products: 0 = FP64 engine; s = 1..8 BF16 slices on the tensor cores."""
         self.check(self.lib.fraclap_set_apply_slices(self.handle, int(slices)))
 
-    SCHEDULE_KNOBS = {"ozaki_group": 0, "ozaki_bits": 1, "fp32_stages_tc": 2, "ozaki_tile_n": 3}
+    SCHEDULE_KNOBS = {"ozaki_group": 0, "ozaki_bits": 1, "fp32_stages_tc": 2, "ozaki_tile_n": 3, "q2_parts": 4}
 
     def set_schedule(self, knob: str, value: int):
         """Sets a schedule knob of the context (see SCHEDULE_KNOBS)."""
@@ -202,7 +202,7 @@ class Context:
     def fma_throughput(self, precision: int, iters: int | None = None, stream=None) -> float:
         """Measured FMA-pipe throughput in flop/s (precision 64 or 32)."""
         if iters is None:
-            iters = (1 << 16) if precision == 64 else (1 << 20)
+            iters = (1 << 14) if precision == 64 else (1 << 18)
         out = ctypes.c_double(0.0)
         self.check(self.lib.fraclap_fma_throughput(self.handle, int(precision), int(iters), ctypes.byref(out),
                                                    ctypes.c_void_p(_stream(stream))))

@@ -427,6 +427,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     const int cbase = ((warp - 2) >> 2) * TC_EPI_COLS;  // this warp's columns of the tile
     const int64_t row = m0 + lg * 32 + lane;          // output row of this thread
     const int er = (row < M) ? ea[row] : 0;
+    const bool alpha_one = alpha == 1.0, alpha_neg_one = alpha == -1.0;
     int acc[TC_EPI_COLS];
 #pragma unroll
     for (int j = 0; j < TC_EPI_COLS; ++j) acc[j] = 0;
@@ -471,12 +472,27 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
               for (int j = 0; j < TC_EPI_COLS; ++j) {
                 const int64_t col = n0 + cbase + j;
                 if (col < N && !(lower && row < col)) {
-                  // acc 2^e in two exact power-of-two steps (each factor normal);
-                  // beyond |e| = 2044 the result is 0 or infinite either way
+                  // acc 2^e: the exponent field of the exactly converted sum is
+                  // shifted by e (an exact scaling, one FP64 operation fewer
+                  // than multiplying); near the ends of the range, two exact
+                  // power-of-two steps (beyond |e| = 2044 the result is 0 or
+                  // infinite either way); alpha = +-1 is a sign
                   int e = er + ebp[j] - sh;
-                  e = (e < -2044) ? -2044 : (e > 2044 ? 2044 : e);
-                  const int e1 = e / 2;
-                  const double v = alpha * (((double)acc[j] * pow2i(e1)) * pow2i(e - e1));
+                  const int a = acc[j];
+                  double v = 0.0;
+                  if (a != 0) {
+                    const double d = (double)a;
+                    const long long db = __double_as_longlong(d);
+                    const int E = (int)((db >> 52) & 0x7FF);
+                    if (E + e >= 1 && E + e <= 2046) {
+                      v = __longlong_as_double(db + ((long long)e << 52));
+                    } else {
+                      e = (e < -2044) ? -2044 : (e > 2044 ? 2044 : e);
+                      const int e1 = e / 2;
+                      v = (d * pow2i(e1)) * pow2i(e - e1);
+                    }
+                  }
+                  v = alpha_one ? v : (alpha_neg_one ? -v : alpha * v);
                   double* cp = cb + j * ldc;
                   *cp = first ? ((beta == 0.0) ? v : v + beta * *cp) : *cp + v;
                 }
@@ -642,6 +658,11 @@ extern "C" int fraclap_set_schedule(fraclap_ctx* ctx, int knob, int value) {
       FL_CHECK(ctx, value == 128 || value == 256, FRACLAP_ERR_INVALID_ARG, "set_schedule: tile width must be 128 or 256");
       ctx->oz_tile_n = value;
       return 0;
+    case FRACLAP_SCHED_Q2_PARTS:
+      FL_CHECK(ctx, value == 0 || value == 4 || value == 8 || value == 16, FRACLAP_ERR_INVALID_ARG,
+               "set_schedule: Q2 parts must be 0, 4, 8 or 16");
+      ctx->q2_parts = value;
+      return 0;
     default:
       return set_error(ctx, FRACLAP_ERR_INVALID_ARG, "set_schedule: unknown knob %d", knob);
   }
@@ -654,6 +675,7 @@ extern "C" int fraclap_get_schedule(const fraclap_ctx* ctx, int knob) {
     case FRACLAP_SCHED_OZAKI_BITS: return ctx->oz_bits;
     case FRACLAP_SCHED_FP32_STAGES: return ctx->fp32_stages_tc;
     case FRACLAP_SCHED_OZAKI_TILE_N: return ctx->oz_tile_n;
+    case FRACLAP_SCHED_Q2_PARTS: return ctx->q2_parts;
     default: return FRACLAP_ERR_INVALID_ARG;
   }
 }

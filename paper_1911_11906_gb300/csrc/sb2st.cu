@@ -502,8 +502,12 @@ int q2_apply_run(fraclap_ctx* ctx, const Stage2T<T>* s, int64_t n, int b, T* Z, 
   if (n < 2 || ncols <= 0) return 0;
   FL_TRY(transpose_run<T>(ctx, Z, ldz, Yt, ldy, n, ncols, st));
   int cpw = 0;
+  // parts per window at b = 64: 4 (16 rows per lane, 8 columns per warp),
+  // 8 or 16 (fewer rows per lane, more warps over the same columns: the
+  // kernel has ncols / (32 / P) warps in all, so small P leaves SMs idle)
+  const int parts64 = (ctx->q2_parts == 8 || ctx->q2_parts == 16) ? ctx->q2_parts : (sizeof(T) == 4 ? 4 : 8);
 #define FL_Q2T(BB, PP)                                                                        \
-  if (b == BB) {                                                                              \
+  if (b == BB && cpw == 0) {                                                                  \
     cpw = 32 / PP;                                                                            \
     const int64_t grid = cdiv(ncols, (int64_t)cpw * Q2T_WARPS);                                \
     q2t_apply_kernel<T, BB, PP><<<(unsigned)grid, Q2T_WARPS * 32, 0, st>>>(s->refl, s->rtau, n, \
@@ -514,10 +518,13 @@ int q2_apply_run(fraclap_ctx* ctx, const Stage2T<T>* s, int64_t n, int b, T* Z, 
   FL_Q2T(8, 2)
   FL_Q2T(16, 4)
   FL_Q2T(32, 8)
-  if constexpr (sizeof(T) == 4) {  // FP64 windows of 16 rows would not fit the registers
-    FL_Q2T(64, 4)
-  } else {
-    FL_Q2T(64, 8)
+  if (b == 64) {
+    if constexpr (sizeof(T) == 4) {  // FP64 windows of 16 rows would not fit the registers
+      if (parts64 == 4) FL_Q2T(64, 4)
+    }
+    if (parts64 == 8) FL_Q2T(64, 8)
+    if (parts64 == 16) FL_Q2T(64, 16)
+    if (parts64 == 4) FL_Q2T(64, 8)  // FP64 with the default
   }
 #undef FL_Q2T
   FL_CHECK(ctx, cpw != 0, FRACLAP_ERR_UNSUPPORTED, "q2 back-transformation: band width %d not in {4, 8, 16, 32, 64}", b);

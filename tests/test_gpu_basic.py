@@ -177,7 +177,7 @@ def test_schedule_knobs_reject_bad_values():
     F = _F()
     ctx = F.Context()
     for knob, bad in (("ozaki_group", -1), ("ozaki_bits", 6), ("ozaki_bits", 9), ("ozaki_tile_n", 192),
-                      ("fp32_stages_tc", 2)):
+                      ("fp32_stages_tc", 2), ("q2_parts", 5)):
         with pytest.raises(F.FraclapError):
             ctx.set_schedule(knob, bad)
     assert ctx.lib.fraclap_set_schedule(ctx.handle, 99, 1) == -1

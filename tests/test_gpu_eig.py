@@ -105,14 +105,16 @@ def test_eig_full_small_squares(m):
     assert np.max(np.abs(lam - ref) / ref) <= 1e-11
 
 
-@pytest.mark.parametrize("seed,b", [(3, 32), (4, 8), (5, 64)])
-def test_eig_full_masked_vs_oracle(seed, b):
+@pytest.mark.parametrize("seed,b,q2", [(3, 32, 0), (4, 8, 0), (5, 64, 0), (5, 64, 16), (6, 64, 4)])
+def test_eig_full_masked_vs_oracle(seed, b, q2):
     F = _F()
     p = I.ellipse_problem(36, seed=seed)
     _, A = O.assemble(p.mask, p.h)
     D = A.dense()
     lam_o, V_o = O.eig_full(D)
-    lam, V = F.eig_full(_colmajor(D), ctx=F.Context(band_width=b))
+    ctx = F.Context(band_width=b)
+    ctx.set_schedule("q2_parts", q2)  # FP64 stage-2 back-transformation with 8 (default, and for 4) or 16 parts
+    lam, V = F.eig_full(_colmajor(D), ctx=ctx)
     lam, V = lam.cpu().numpy(), V.cpu().numpy()
     _check_decomposition(D, lam_o, lam, V)
     # solutions agree (eigenvectors are not compared column by column)
@@ -126,11 +128,11 @@ def _csr_cuda(A):
     return (torch.from_numpy(A.rowptr).cuda(), torch.from_numpy(A.col).cuda(), torch.from_numpy(A.val).cuda())
 
 
-@pytest.mark.parametrize("tc,tile_n", [(0, 128), (1, 128), (0, 256)])
+@pytest.mark.parametrize("tc,tile_n,q2", [(0, 128, 0), (1, 128, 0), (0, 256, 8), (0, 128, 16)])
 @pytest.mark.parametrize("which,b,iters", [("square23", 32, 6), ("ellipse36", 32, 6), ("ellipse36", 64, 6),
                                             ("ellipse64", 32, 6), ("ellipse48", 16, 6), ("square9", 8, 6),
                                             ("cube6", 32, 6)])
-def test_eig_full_mixed_refined_vs_oracle(which, b, iters, tc, tile_n):
+def test_eig_full_mixed_refined_vs_oracle(which, b, iters, tc, tile_n, q2):
     """FP32 stages (FMA kernel, or three TF32 products on the tensor cores
     with tc = 1) + Ogita-Aishima refinement (slice products on 128- or
     256-column tiles) reach the FP64 tolerances."""
@@ -148,6 +150,7 @@ def test_eig_full_mixed_refined_vs_oracle(which, b, iters, tc, tile_n):
     ctx = F.Context(band_width=b)
     ctx.set_schedule("fp32_stages_tc", tc)
     ctx.set_schedule("ozaki_tile_n", tile_n)
+    ctx.set_schedule("q2_parts", q2)
     lam, V = F.eig_full_mixed(_colmajor(D), *_csr_cuda(A), refine_iters=iters, ctx=ctx)
     lam, V = lam.cpu().numpy(), V.cpu().numpy()
     _check_decomposition(D, lam_o, lam, V)
