@@ -291,7 +291,7 @@ __device__ __forceinline__ void ozaki_tile_of(int64_t idx, int TM, int TN, int G
 }
 
 template <int TCN>
-__global__ void __maxnreg__(200)
+__global__ void __launch_bounds__(TC_THREADS, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const int* __restrict__ ea, const int* __restrict__ eb, int64_t M, int64_t N, int64_t Kp,
                 int s, int bits, int64_t chunk, double alpha, double beta, double* C, int64_t ldc,
@@ -427,7 +427,6 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     const int cbase = ((warp - 2) >> 2) * TC_EPI_COLS;  // this warp's columns of the tile
     const int64_t row = m0 + lg * 32 + lane;          // output row of this thread
     const int er = (row < M) ? ea[row] : 0;
-    const bool alpha_one = alpha == 1.0, alpha_neg_one = alpha == -1.0;
     int acc[TC_EPI_COLS];
 #pragma unroll
     for (int j = 0; j < TC_EPI_COLS; ++j) acc[j] = 0;
@@ -472,27 +471,12 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
               for (int j = 0; j < TC_EPI_COLS; ++j) {
                 const int64_t col = n0 + cbase + j;
                 if (col < N && !(lower && row < col)) {
-                  // acc 2^e: the exponent field of the exactly converted sum is
-                  // shifted by e (an exact scaling, one FP64 operation fewer
-                  // than multiplying); near the ends of the range, two exact
-                  // power-of-two steps (beyond |e| = 2044 the result is 0 or
-                  // infinite either way); alpha = +-1 is a sign
+                  // acc 2^e in two exact power-of-two steps (each factor normal);
+                  // beyond |e| = 2044 the result is 0 or infinite either way
                   int e = er + ebp[j] - sh;
-                  const int a = acc[j];
-                  double v = 0.0;
-                  if (a != 0) {
-                    const double d = (double)a;
-                    const long long db = __double_as_longlong(d);
-                    const int E = (int)((db >> 52) & 0x7FF);
-                    if (E + e >= 1 && E + e <= 2046) {
-                      v = __longlong_as_double(db + ((long long)e << 52));
-                    } else {
-                      e = (e < -2044) ? -2044 : (e > 2044 ? 2044 : e);
-                      const int e1 = e / 2;
-                      v = (d * pow2i(e1)) * pow2i(e - e1);
-                    }
-                  }
-                  v = alpha_one ? v : (alpha_neg_one ? -v : alpha * v);
+                  e = (e < -2044) ? -2044 : (e > 2044 ? 2044 : e);
+                  const int e1 = e / 2;
+                  const double v = alpha * (((double)acc[j] * pow2i(e1)) * pow2i(e - e1));
                   double* cp = cb + j * ldc;
                   *cp = first ? ((beta == 0.0) ? v : v + beta * *cp) : *cp + v;
                 }
