@@ -19,9 +19,10 @@
 // Two tensor-core kernels compute the slice products: the sm_103a one uses
 // tcgen05.mma with operands brought into shared memory by TMA
 // (cp.async.bulk.tensor, 128-byte swizzle) and the FP32 chunk accumulators in
-// tensor memory, double-buffered so that the FP64 folding of one chunk
-// overlaps the products of the next; a plain mma.sync m16n8k16 kernel is kept
-// as the reference route for checking it.
+// tensor memory (four buffers at 128 columns, two at 256), so that the
+// draining and FP64 folding of finished chunks overlap the products of the
+// next ones; a plain mma.sync m16n8k16 kernel is kept as the reference route
+// for checking it.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -238,7 +239,11 @@ struct OzTile {
   static constexpr int B_BYTES = TCN * TC_KB * 2;
   static constexpr int STAGE_BYTES = TC_A_BYTES + B_BYTES;
   static constexpr int EPI_COLS = TCN * 4 / TC_EPI_WARPS;  // columns per epilogue thread
-  static constexpr uint32_t TMEM_COLS = 2 * TCN;           // two FP32 accumulators
+  // FP32 chunk accumulators filling the 512 TMEM columns: four at 128 columns
+  // (the MMA warp runs up to three chunks ahead of an epilogue that is
+  // folding a finished diagonal into C), two at 256
+  static constexpr int NBUF = 512 / TCN;
+  static constexpr uint32_t TMEM_COLS = NBUF * TCN;
   // kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, M 128, N TCN.
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) |
                                     ((uint32_t)(TC_M >> 4) << 24);
@@ -300,11 +305,12 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   constexpr int TC_N = TCN, TC_STAGES = OzTile<TCN>::STAGES, TC_B_BYTES = OzTile<TCN>::B_BYTES;
   constexpr int TC_STAGE_BYTES = OzTile<TCN>::STAGE_BYTES, TC_EPI_COLS = OzTile<TCN>::EPI_COLS;
   constexpr uint32_t TC_TMEM_COLS = OzTile<TCN>::TMEM_COLS, TC_IDESC = OzTile<TCN>::IDESC;
+  constexpr int NBUF = OzTile<TCN>::NBUF;
   (void)TC_B_BYTES;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES];
-  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], done_bar;
+  __shared__ __align__(8) uint64_t acc_full[OzTile<TCN>::NBUF], acc_empty[OzTile<TCN>::NBUF], done_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -321,7 +327,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       mbar_init(&full_bar[i], 1);
       mbar_init(&empty_bar[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NBUF; ++i) {
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], TC_EPI_WARPS);
     }
@@ -383,8 +389,8 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       for (int dg = 0; dg < s && ok; ++dg)
         for (int p = 0; p <= dg && ok; ++p)
           for (int c = 0; c < nchunk && ok; ++c, ++chunk_i) {
-            const int buf = chunk_i & 1;
-            if (!mbar_wait(&acc_empty[buf], ((chunk_i >> 1) & 1) ^ 1, limit) || *(volatile int*)&abort_sh) {
+            const int buf = chunk_i % NBUF;
+            if (!mbar_wait(&acc_empty[buf], ((chunk_i / NBUF) & 1) ^ 1, limit) || *(volatile int*)&abort_sh) {
               ok = false;
               break;
             }
@@ -437,8 +443,8 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       int pending = 0;
       for (int p = 0; p <= dg && ok; ++p) {
         for (int c = 0; c < nchunk; ++c, ++chunk_i) {
-          const int buf = chunk_i & 1;
-          if (!mbar_wait(&acc_full[buf], (chunk_i >> 1) & 1, limit) || *(volatile int*)&abort_sh) {
+          const int buf = chunk_i % NBUF;
+          if (!mbar_wait(&acc_full[buf], (chunk_i / NBUF) & 1, limit) || *(volatile int*)&abort_sh) {
             ok = false;
             break;
           }
