@@ -128,7 +128,7 @@ def _csr_cuda(A):
     return (torch.from_numpy(A.rowptr).cuda(), torch.from_numpy(A.col).cuda(), torch.from_numpy(A.val).cuda())
 
 
-@pytest.mark.parametrize("tc,tile_n,q2", [(0, 128, 0), (1, 128, 0), (0, 256, 8), (0, 128, 16)])
+@pytest.mark.parametrize("tc,tile_n,q2", [(0, 256, 0), (1, 128, 0), (0, 128, 8), (0, 128, 16), (0, 256, 4)])
 @pytest.mark.parametrize("which,b,iters", [("square23", 32, 6), ("ellipse36", 32, 6), ("ellipse36", 64, 6),
                                             ("ellipse64", 32, 6), ("ellipse48", 16, 6), ("square9", 8, 6),
                                             ("cube6", 32, 6)])
