@@ -94,3 +94,23 @@ def test_graph_needs_a_caller_workspace(decomposition):
     assert ctx.lib.fraclap_graph_launch(None, None) == -1
     assert ctx.lib.fraclap_graph_kernels(None) == -1
     ctx.lib.fraclap_graph_destroy(None)
+
+
+def test_stage_times_stay_readable_after_a_capture_with_profiling(decomposition):
+    """With profiling on, capturing the apply into a graph records no stage
+    events inside the capture: stage_times() afterwards reads only the
+    events of direct calls, and the graph's replays give the direct result."""
+    import paper_1911_11906_gb300 as F
+    p, V, lam = decomposition
+    ctx = F.Context()
+    ctx.set_profiling(True)
+    Fd = _colmajor(p.F)
+    direct = F.frac_apply(V, lam, Fd, p.pair_f, p.pair_alpha, ctx=ctx)
+    g = F.ApplyGraph(V, lam, Fd, p.pair_f, p.pair_alpha, ctx=ctx)
+    out = g.launch()
+    times = ctx.stage_times()  # raised on captured events before
+    assert times["apply"][1] == 1 and times["apply"][0] > 0.0
+    assert _close(out, direct, 1e-15)
+    F.frac_apply(V, lam, Fd, p.pair_f, p.pair_alpha, ctx=ctx)
+    assert ctx.stage_times()["apply"][1] == 1
+    g.close()
