@@ -190,6 +190,10 @@ def whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
 FP32_PEAK_TFLOPS = 152 * 2.070e9 * 128 * 2 / 1e12
 REFINE_ITERS = 6
 BAND = {"fp64": 64, "mixed": 64}
+# the mixed route's apply takes its two products as 6 BF16 slices per operand
+# on the tensor cores (FP64-accurate to a few 1e-12, checked on every solve
+# against the FP64 route); the FP64 route keeps FP64 products
+APPLY_SLICES = {"fp64": 0, "mixed": 6}
 # wall-clock budget of the oracle arm: whole steps are timed until one ends past it
 REFERENCE_BUDGET_S = 60.0
 
@@ -200,6 +204,14 @@ def ozaki_bf16_flops(n: int, slices: int = 8) -> float:
     p + q < slices, each 2 n flops per lower-triangle entry."""
     pairs = slices * (slices + 1) // 2
     return 2.0 * pairs * n * (n * (n + 1) // 2)
+
+
+def apply_slice_flops(n: int, m: int, k: int, slices: int, digit_bits: int = 7) -> float:
+    """BF16 flops of the apply's two sliced products, V^T F (n x m) and
+    V C (n x k), both with inner dimension n: every digit pair p + q < d,
+    d = ceil(8 s / 7) digits of 7 bits (or the s slices themselves)."""
+    d = slices if digit_bits == 8 else (8 * slices + 6) // 7
+    return 2.0 * (d * (d + 1) // 2) * n * n * (m + k)
 
 
 def refine_slice_counts(iterations: int, cap: int, digit_bits: int = 7) -> list:
@@ -305,7 +317,9 @@ def run_gpu(args, rank, world, local_rank):
         ctx = F.Context(band_width=band[path])
         if path == "mixed" and sched:
             autotune.apply_schedule(ctx, sched)
-        app_ws = torch.empty(ctx.lib.fraclap_apply_workspace_bytes(n, Fd.shape[1], k), dtype=torch.uint8, device=dev)
+        ctx.set_apply_slices(APPLY_SLICES[path])
+        app_ws = torch.empty(ctx.lib.fraclap_apply_workspace_bytes_ctx(ctx.handle, n, Fd.shape[1], k),
+                             dtype=torch.uint8, device=dev)
         # the FP64 route is the comparison when both run: fewer timed steps (it is 6x slower)
         short = path == "fp64" and len(paths) > 1
         r = run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier,
@@ -372,15 +386,21 @@ def run_gpu(args, rank, world, local_rank):
     else:
         g_ms, g_cnt = stages["slice_products"]
         dur = g_ms / max(g_cnt, 1)
-        # average over the launches (2 per iteration, fewer slices in the first two)
+        # average over the launches of one step: 2 per refinement iteration
+        # (fewer slices in the first two) and the apply's 2
         digit_bits = R["ctx"].get_schedule("ozaki_bits")
         per_iter = refine_slice_counts(len(R.get("refine", [])) or 3, REFINE_ITERS, digit_bits)
         total = sum(2 * ozaki_bf16_flops(n, sl) for sl in per_iter)
-        work = total / max(2 * len(per_iter), 1)
+        launches_per_step = 2 * len(per_iter)
+        if APPLY_SLICES[head]:
+            total += apply_slice_flops(n, Fd.shape[1], k, APPLY_SLICES[head], digit_bits)
+            launches_per_step += 2
+        work = total / max(launches_per_step, 1)
         traffic = OZAKI_DRAM_BYTES_PER_FLOP * work if OZAKI_DRAM_BYTES_PER_FLOP else None
         # the kernel runs inside a seconds-long step: the sustained BF16 figure is its peak
         peak = _measured_peak("bf16_tflops_sustained") or _measured_peak("bf16_tflops") or 1700.0
-        roof = {"kernel": "ozaki_tc_kernel (residual products of the refinement: tcgen05.mma on TMA-loaded BF16 slices)",
+        roof = {"kernel": "ozaki_tc_kernel (residual products of the refinement and the apply's two products: "
+                          "tcgen05.mma on TMA-loaded BF16 slices)",
                 "bound": "tensor", "peak": round(peak, 1),
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured; the kernel is timed inside a "
                                 "seconds-long step)") if _measured_peak("bf16_tflops_sustained") else
@@ -428,6 +448,8 @@ def run_gpu(args, rank, world, local_rank):
             "eig_tflops_credited_fp64": round(eig_flops(n) / (eig_ms * 1e-3) / 1e12, 4),
             "eig_frac_of_fp64_peak": round(eig_flops(n) / (eig_ms * 1e-3) / 1e12 / fp64_peak, 4),
             "apply_s": round(st["apply"][0] / r["steps"] / 1e3, 5),
+            "apply_products": (f"{APPLY_SLICES[pth]} BF16 slices per operand on tcgen05" if APPLY_SLICES[pth]
+                               else "FP64"),
             "stage_ms": {s: round(v[0] / r["steps"], 3) for s, v in st.items()},
             "gpu_launches": int(r["launches"]),
             "accuracy": r["acc"],
