@@ -577,14 +577,19 @@ int fraclap_partition_spectrum(fraclap_ctx* ctx, int64_t n, const int64_t* rowpt
  *    the tensor cores as three TF32 products (FP32-level accuracy, a few
  *    2^-22 per product instead of 2^-24) [0].
  *  FRACLAP_SCHED_OZAKI_TILE_N: columns of the slice-product kernel's output
- *    tile, 128 or 256 (rows are 128) [256].
+ *    tile, 128, 192 or 256 (rows are 128; outputs of at most 128 columns
+ *    always take 128) [192].
  *  FRACLAP_SCHED_Q2_PARTS: at half-bandwidth 64, the lanes that share one
  *    column's window of the stage-2 back-transformation: 4, 8 or 16 (16, 8 or
  *    4 rows per lane; more parts give more warps over the same columns; FP64
  *    takes 8 when asked for 4), or 0 for the default 8 [0].
+ *  FRACLAP_SCHED_OZAKI_CLUSTER: CTAs of the slice-product kernel per thread-
+ *    block cluster, 1, 2 or 4: the cluster's CTAs take consecutive tile rows
+ *    of one tile column and share its B tile through TMA multicast, each
+ *    loading 1/CS of it (fewer L2-to-SM bytes per flop) [1].
  * ---------------------------------------------------------------------- */
 enum { FRACLAP_SCHED_OZAKI_GROUP = 0, FRACLAP_SCHED_OZAKI_BITS = 1, FRACLAP_SCHED_FP32_STAGES = 2,
-       FRACLAP_SCHED_OZAKI_TILE_N = 3, FRACLAP_SCHED_Q2_PARTS = 4 };
+       FRACLAP_SCHED_OZAKI_TILE_N = 3, FRACLAP_SCHED_Q2_PARTS = 4, FRACLAP_SCHED_OZAKI_CLUSTER = 5 };
 int fraclap_set_schedule(fraclap_ctx* ctx, int knob, int value);
 int fraclap_get_schedule(const fraclap_ctx* ctx, int knob);
 

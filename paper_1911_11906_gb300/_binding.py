@@ -181,7 +181,8 @@ class Context:
         """frac_apply products: 0 = FP64 engine; s = 1..8 BF16 slices on the tensor cores."""
         self.check(self.lib.fraclap_set_apply_slices(self.handle, int(slices)))
 
-    SCHEDULE_KNOBS = {"ozaki_group": 0, "ozaki_bits": 1, "fp32_stages_tc": 2, "ozaki_tile_n": 3, "q2_parts": 4}
+    SCHEDULE_KNOBS = {"ozaki_group": 0, "ozaki_bits": 1, "fp32_stages_tc": 2, "ozaki_tile_n": 3, "q2_parts": 4,
+                      "ozaki_cluster": 5}
 
     def set_schedule(self, knob: str, value: int):
         """Sets a schedule knob of the context (see SCHEDULE_KNOBS)."""

@@ -162,21 +162,24 @@ def best_workers(problems: list, candidates=(4, 8, 16, 32), tuner: Autotuner | N
                         lambda w: _event_seconds(lambda: B.solve_batched(problems, workers=int(w), ctx=ctx)), reps)
 
 
-def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7,), tiles=(128, 256),
-                        tuner: Autotuner | None = None, reps: int = 2, cols: int | None = None) -> dict:
-    """Tile order (raster group of tile rows), tile width and digit width of
-    the slice-product kernel for the refinement's residual product X^T X of an
-    n x n X with `slices` BF16 slices (or, with cols, the apply's product
-    V^T F of an n x n V and an n x cols F), measured on seeded matrices of
-    that size through fraclap_dgemm_ozaki.  Returns {"ozaki_group": G,
-    "ozaki_bits": w, "ozaki_tile_n": t}; apply it with apply_schedule(ctx, ...).  The digit
-    widths tried default to 7 alone: 8-bit digits (28 instead of 36 slice
-    pairs for 7 slices) measured the same kernel time on a GB300 at n = 4096
-    and 8810, their four times more chunk sums taking what the pairs save."""
+def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7,), tiles=(128, 192, 256),
+                        clusters=(1, 2), tuner: Autotuner | None = None, reps: int = 2,
+                        cols: int | None = None) -> dict:
+    """Tile order (raster group of tile rows), tile width, cluster size (CTAs
+    sharing a B tile by TMA multicast) and digit width of the slice-product
+    kernel for the refinement's residual product X^T X of an n x n X with
+    `slices` BF16 slices (or, with cols, the apply's product V^T F of an
+    n x n V and an n x cols F), measured on seeded matrices of that size
+    through fraclap_dgemm_ozaki.  Returns {"ozaki_group": G, "ozaki_bits": w,
+    "ozaki_tile_n": t, "ozaki_cluster": c}; apply it with
+    apply_schedule(ctx, ...).  The digit widths tried default to 7 alone:
+    8-bit digits (28 instead of 36 slice pairs for 7 slices) measured the same
+    kernel time on a GB300 at n = 4096 and 8810, their four times more chunk
+    sums taking what the pairs save."""
     import torch
     from . import _binding as B
     tuner = tuner or Autotuner()
-    cands = [f"{g}/{w}/{t}" for t in tiles for w in bits for g in groups]
+    cands = [f"{g}/{w}/{t}/{c}" for c in clusters for t in tiles for w in bits for g in groups]
     fields = {"device": _device_name(), "n_bucket": size_bucket(n), "slices": int(slices)}
     if cols is not None:
         fields["cols_bucket"] = size_bucket(cols)
@@ -192,10 +195,11 @@ def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7,)
                          device="cuda")
 
         def measure(c):
-            g, w, t = (int(x) for x in c.split("/"))
+            g, w, t, cl = (int(x) for x in c.split("/"))
             ctx.set_schedule("ozaki_group", g)
             ctx.set_schedule("ozaki_bits", w)
             ctx.set_schedule("ozaki_tile_n", t)
+            ctx.set_schedule("ozaki_cluster", cl)
 
             def run():
                 import ctypes
@@ -205,8 +209,8 @@ def best_ozaki_schedule(n: int, slices: int = 7, groups=(0, 4, 8, 16), bits=(7,)
             return _event_seconds(run)
 
         hit = tuner.choose("ozaki_schedule", fields, cands, measure, reps)
-    g, w, t = (int(x) for x in hit.split("/"))
-    return {"ozaki_group": g, "ozaki_bits": w, "ozaki_tile_n": t}
+    g, w, t, cl = (int(x) for x in hit.split("/"))
+    return {"ozaki_group": g, "ozaki_bits": w, "ozaki_tile_n": t, "ozaki_cluster": cl}
 
 
 def apply_schedule(ctx, schedule: dict) -> None:

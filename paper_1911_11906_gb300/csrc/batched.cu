@@ -63,6 +63,7 @@ int ensure_workers(fraclap_ctx* ctx, int W) {
     w->oz_group = ctx->oz_group;
     w->oz_bits = ctx->oz_bits;
     w->oz_tile_n = ctx->oz_tile_n;
+    w->oz_cluster = ctx->oz_cluster;
     w->q2_parts = ctx->q2_parts;
     w->fp32_stages_tc = ctx->fp32_stages_tc;
   }

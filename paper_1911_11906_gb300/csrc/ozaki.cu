@@ -40,6 +40,16 @@ constexpr int OZ_BM = 64, OZ_BN = 64, OZ_BK = 32, OZ_NT = 128;
 constexpr int OZ_KPAD = 64;  // slice rows padded to a multiple of 64 (one TMA box)
 constexpr int OZ_LDS = OZ_BK / 2 + 4;  // shared row stride in 32-bit words (padded)
 
+// e with every |entry| < 2^e, from the largest |entry| t given as the bits
+// of its IEEE pattern with the sign cleared.
+__device__ __forceinline__ int exponent_above(unsigned long long t) {
+  int e = 0;
+  const int E = (int)(t >> 52);
+  if (E > 0) e = E - 1022;  // t = f 2^e, f in [0.5, 1): every |entry| < 2^e
+  else if (t != 0) frexp(__longlong_as_double((long long)t), &e);  // subnormal maximum
+  return e;
+}
+
 // Exponent of the largest |entry| of each row of op(A) (rows = M, length K).
 // One block per row.  The magnitudes are compared as the integers of their
 // IEEE bit patterns with the sign cleared (the same order as the values), so
@@ -62,12 +72,31 @@ __global__ void row_exponents(const double* A, int64_t lda, bool trans, int64_t 
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
     for (unsigned w = 0; w < blockDim.x / 32; ++w) t = red[w] > t ? red[w] : t;
-    int e = 0;
-    const int E = (int)(t >> 52);
-    if (E > 0) e = E - 1022;  // t = f 2^e, f in [0.5, 1): every |entry| < 2^e
-    else if (t != 0) frexp(__longlong_as_double((long long)t), &e);  // subnormal maximum
-    ex[i] = e;
+    ex[i] = exponent_above(t);
   }
+}
+
+// The same for the rows of an untransposed column-major M x K operand, whose
+// rows are strided: a thread per row over a chunk of kch columns (the reads
+// of a warp are contiguous), the chunks' maxima merged by an integer
+// atomicMax on the bit patterns (order-free, so the same maximum), then
+// exponents_of_max.
+constexpr int OZ_MAX_KCH = 64;
+__global__ void row_absmax_strided(const double* A, int64_t lda, int64_t M, int64_t K, unsigned long long* mx) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const int64_t k0 = (int64_t)blockIdx.y * OZ_MAX_KCH;
+  const int64_t k1 = (k0 + OZ_MAX_KCH < K) ? k0 + OZ_MAX_KCH : K;
+  unsigned long long m = 0;
+  for (int64_t k = k0; k < k1; ++k) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(A[i + k * lda]) & 0x7FFFFFFFFFFFFFFFull;
+    m = u > m ? u : m;
+  }
+  if (m != 0) atomicMax(&mx[i], m);
+}
+__global__ void exponents_of_max(const unsigned long long* mx, int64_t M, int* ex) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) ex[i] = exponent_above(mx[i]);
 }
 
 // Slices of op(A) (M x K): S[p][i][k] (k contiguous, Kp >= K, zero padded).
@@ -78,39 +107,63 @@ __global__ void row_exponents(const double* A, int64_t lda, bool trans, int64_t 
 // integer (exact: a power-of-two scaling, then a truncating conversion) and
 // the digits are read off with shifts; otherwise the digits are peeled in
 // FP64, which gives the same digits.
+// The s digits of one entry a of row i (exponent e = ex[i]) into S[p * pstride].
+__device__ __forceinline__ void write_digits(double a, int e, int s, int bits, __nv_bfloat16* S, int64_t pstride) {
+  const int tb = bits * s;
+  if (tb <= 64) {
+    // floor(|a| 2^(tb - e)) from the bits: |a| = m 2^(E - 1075) (m with
+    // its hidden bit; subnormals take E = 1), shifted exactly; below 2^tb
+    // because |a| < 2^e
+    const unsigned long long mask = (1ull << bits) - 1ull;
+    const unsigned long long bitsA = (unsigned long long)__double_as_longlong(a);
+    const int E = (int)((bitsA >> 52) & 0x7FF);
+    const unsigned long long mant = (bitsA & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+    const int sh = (E ? E : 1) - 1075 + tb - e;
+    const unsigned long long u = (sh >= 64 || sh <= -64) ? 0ull : (sh >= 0 ? (mant << sh) : (mant >> -sh));
+    const float sg = (a < 0.0) ? -1.0f : 1.0f;
+    for (int p = 0; p < s; ++p) {
+      const unsigned long long dgt = (u >> (bits * (s - 1 - p))) & mask;
+      S[p * pstride] = __float2bfloat16_rn(sg * (float)dgt);
+    }
+  } else {
+    double x = ldexp(a, -e);
+    for (int p = 0; p < s; ++p) {
+      const double y = ldexp(x, bits);
+      const double q = trunc(y);
+      S[p * pstride] = __float2bfloat16_rn((float)q);
+      x = y - q;
+    }
+  }
+}
+
 __global__ void make_slices(const double* A, int64_t lda, bool trans, int64_t M, int64_t K,
                             int64_t Kp, const int* ex, int s, int bits, __nv_bfloat16* S) {
   const int64_t total = M * Kp;
-  const int tb = bits * s;
-  const unsigned long long mask = (1ull << bits) - 1ull;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     int64_t i, k;
     if (trans) { k = t % Kp; i = t / Kp; } else { i = t % M; k = t / M; }
     const double a = (k < K) ? (trans ? A[k + i * lda] : A[i + k * lda]) : 0.0;
-    if (tb <= 64) {
-      // floor(|a| 2^(tb - e)) from the bits: |a| = m 2^(E - 1075) (m with
-      // its hidden bit; subnormals take E = 1), shifted exactly; below 2^tb
-      // because |a| < 2^e
-      const unsigned long long bitsA = (unsigned long long)__double_as_longlong(a);
-      const int E = (int)((bitsA >> 52) & 0x7FF);
-      const unsigned long long mant = (bitsA & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
-      const int sh = (E ? E : 1) - 1075 + tb - ex[i];
-      const unsigned long long u = (sh >= 64 || sh <= -64) ? 0ull : (sh >= 0 ? (mant << sh) : (mant >> -sh));
-      const float sg = (a < 0.0) ? -1.0f : 1.0f;
-      for (int p = 0; p < s; ++p) {
-        const unsigned long long dgt = (u >> (bits * (s - 1 - p))) & mask;
-        S[((int64_t)p * M + i) * Kp + k] = __float2bfloat16_rn(sg * (float)dgt);
-      }
-    } else {
-      double x = ldexp(a, -ex[i]);
-      for (int p = 0; p < s; ++p) {
-        const double y = ldexp(x, bits);
-        const double q = trunc(y);
-        S[((int64_t)p * M + i) * Kp + k] = __float2bfloat16_rn((float)q);
-        x = y - q;
-      }
-    }
+    write_digits(a, ex[i], s, bits, S + i * Kp + k, M * Kp);
+  }
+}
+
+// The same slices of an untransposed column-major operand (rows strided):
+// 32 x 32 tiles of (i, k) staged in shared memory, read along i and written
+// along k, so that both the FP64 reads and the BF16 writes are contiguous
+// within a warp.  Block 32 x 8 threads; grid (ceil(M / 32), Kp / 32).
+__global__ void make_slices_strided(const double* A, int64_t lda, int64_t M, int64_t K, int64_t Kp,
+                                    const int* ex, int s, int bits, __nv_bfloat16* S) {
+  __shared__ double tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t i = i0 + threadIdx.x, k = k0 + r;
+    tile[r][threadIdx.x] = (i < M && k < K) ? A[i + k * lda] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t i = i0 + r, k = k0 + threadIdx.x;
+    if (i < M) write_digits(tile[threadIdx.x][r], ex[i], s, bits, S + i * Kp + k, M * Kp);
   }
 }
 
@@ -225,25 +278,30 @@ ozaki_kernel(const __nv_bfloat16* __restrict__ SA, const __nv_bfloat16* __restri
 // thread one output row and 64 of the 128 columns.  Six 32 KB stages keep
 // enough bytes in flight to cover the L2 latency.
 // ----------------------------------------------------------------------------
-// The tile width TCN (128 or 256 columns of op(B)) is a schedule choice: a
-// 128 x 256 tile moves 48 KB of slices per 4.2 MFLOP k-block instead of
-// 32 KB per 2.1 MFLOP (1.33x fewer L2 bytes per flop), with four stages
-// instead of six and the two accumulators filling all 512 TMEM columns.
+// The tile width TCN (128, 192 or 256 columns of op(B)) is a schedule
+// choice: a 128 x 256 tile moves 48 KB of slices per 4.2 MFLOP k-block
+// instead of 32 KB per 2.1 MFLOP (1.33x fewer L2 bytes per flop), with four
+// stages instead of six and the two accumulators filling all 512 TMEM
+// columns, but its epilogue threads keep 128 integer sums each, more than
+// their registers hold; 128 x 192 (40 KB per 3.1 MFLOP, five stages) keeps
+// 96 per thread.
 constexpr int TC_M = 128, TC_KB = 64;
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 constexpr int TC_A_BYTES = TC_M * TC_KB * 2;
 template <int TCN>
 struct OzTile {
-  static constexpr int STAGES = (TCN == 256) ? 4 : 6;
+  static_assert(TCN == 128 || TCN == 192 || TCN == 256, "tile width 128, 192 or 256");
+  static constexpr int STAGES = (TCN == 256) ? 4 : (TCN == 192) ? 5 : 6;
   static constexpr int B_BYTES = TCN * TC_KB * 2;
   static constexpr int STAGE_BYTES = TC_A_BYTES + B_BYTES;
   static constexpr int EPI_COLS = TCN * 4 / TC_EPI_WARPS;  // columns per epilogue thread
-  // FP32 chunk accumulators filling the 512 TMEM columns: four at 128 columns
+  // FP32 chunk accumulators in the 512 TMEM columns: four at 128 columns
   // (the MMA warp runs up to three chunks ahead of an epilogue that is
-  // folding a finished diagonal into C), two at 256
+  // folding a finished diagonal into C), two at 192 or 256; the allocation
+  // is the whole (power-of-two) 512 columns
   static constexpr int NBUF = 512 / TCN;
-  static constexpr uint32_t TMEM_COLS = NBUF * TCN;
+  static constexpr uint32_t TMEM_COLS = 512;
   // kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, M 128, N TCN.
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) |
                                     ((uint32_t)(TC_M >> 4) << 24);
@@ -295,7 +353,17 @@ __device__ __forceinline__ void ozaki_tile_of(int64_t idx, int TM, int TN, int G
   *tn = 0;
 }
 
-template <int TCN>
+// CS > 1: a cluster of CS CTAs takes CS consecutive tile rows of one tile
+// column.  They need the same B tile, so each CTA loads 1/CS of it (TCN / CS
+// rows of op(B)) with one TMA multicast into the same stage of every CTA of
+// the cluster: the L2-to-SM bytes per k-block drop from A + B to A + B / CS.
+// A stage may then be refilled only once all CS CTAs have consumed it, so
+// every MMA warp's stage-release commit is multicast to the empty barriers of
+// the whole cluster, which count CS arrivals.  Every CTA of a cluster runs
+// the whole pipeline (its peers need its share of B), also when its tile
+// lies past the last row or above the diagonal; its epilogue then writes
+// nothing.
+template <int TCN, int CS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const int* __restrict__ ea, const int* __restrict__ eb, int64_t M, int64_t N, int64_t Kp,
@@ -306,6 +374,9 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   constexpr int TC_STAGE_BYTES = OzTile<TCN>::STAGE_BYTES, TC_EPI_COLS = OzTile<TCN>::EPI_COLS;
   constexpr uint32_t TC_TMEM_COLS = OzTile<TCN>::TMEM_COLS, TC_IDESC = OzTile<TCN>::IDESC;
   constexpr int NBUF = OzTile<TCN>::NBUF;
+  constexpr int B_ROWS = TCN / CS;  // rows of the B tile this CTA loads (and multicasts)
+  static_assert(CS == 1 || CS == 2 || CS == 4, "cluster of 1, 2 or 4 CTAs");
+  static_assert((B_ROWS * 128) % 1024 == 0, "a B share starts on a 128-byte-swizzle atom");
   (void)TC_B_BYTES;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -315,17 +386,25 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int TM = (int)((M + TC_M - 1) / TC_M), TN = (int)((N + TC_N - 1) / TC_N);
+  const int rank = (CS > 1) ? (int)cluster_ctarank() : 0;
   int tm, tn;
-  ozaki_tile_of((int64_t)blockIdx.x, TM, TN, group, lower != 0, TC_M, TC_N, &tm, &tn);
-  if (tm >= TM || tn >= TN) return;
+  if (CS == 1) {
+    ozaki_tile_of((int64_t)blockIdx.x, TM, TN, group, lower != 0, TC_M, TC_N, &tm, &tn);
+    if (tm >= TM || tn >= TN) return;
+    if (lower && (int64_t)tm * TC_M + TC_M - 1 < (int64_t)tn * TC_N) return;  // tile above the diagonal
+  } else {
+    // the grid holds whole clusters of CS tile rows: no CTA leaves early
+    int tc;
+    ozaki_tile_of((int64_t)(blockIdx.x / CS), (TM + CS - 1) / CS, TN, group, lower != 0, CS * TC_M, TC_N, &tc, &tn);
+    tm = tc * CS + rank;
+  }
   const int64_t m0 = (int64_t)tm * TC_M, n0 = (int64_t)tn * TC_N;
-  if (lower && m0 + TC_M - 1 < n0) return;  // whole CTA: tile above the diagonal
   const int nchunk = (int)((Kp + chunk - 1) / chunk);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < TC_STAGES; ++i) {
       mbar_init(&full_bar[i], 1);
-      mbar_init(&empty_bar[i], 1);
+      mbar_init(&empty_bar[i], CS);
     }
     for (int i = 0; i < NBUF; ++i) {
       mbar_init(&acc_full[i], 1);
@@ -345,6 +424,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   }
   tc_fence_before();
   __syncthreads();
+  if (CS > 1) cluster_sync_all();  // every CTA's barriers exist before any multicast reaches them
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
 
@@ -367,12 +447,22 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
               }
               unsigned char* a = smem + st * TC_STAGE_BYTES;
               unsigned char* b = a + TC_A_BYTES;
-              mbar_expect_tx(&full_bar[st], TC_STAGE_BYTES);
+              mbar_expect_tx(&full_bar[st], TC_STAGE_BYTES);  // A and the whole B tile (all CS shares)
               const int kc = (int)(c0 + kb * TC_KB);
               tma_load_3d(a, &mapA, &full_bar[st], kc, (int)m0, p);
-              tma_load_3d(b, &mapB, &full_bar[st], kc, (int)n0, q);
+              if (CS == 1)
+                tma_load_3d(b, &mapB, &full_bar[st], kc, (int)n0, q);
+              else
+                tma_load_3d_multicast(b + rank * (B_ROWS * 128), &mapB, &full_bar[st], kc,
+                                      (int)(n0 + rank * B_ROWS), q, (uint16_t)((1u << CS) - 1u));
             }
           }
+      if (CS > 1 && ok) {
+        // every peer's last releases of this CTA's stages have arrived: no
+        // remote arrive can reach this CTA's barriers after it exits
+        for (int j = (it > TC_STAGES ? it - TC_STAGES : 0); j < it && ok; ++j)
+          ok = mbar_wait(&empty_bar[j % TC_STAGES], ((j / TC_STAGES) & 1), limit);
+      }
       if (!ok) {
         atomicCAS(status, 0, FRACLAP_ERR_TIMEOUT);
         abort_sh = 1;
@@ -410,7 +500,10 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 #pragma unroll
               for (int kk = 0; kk < TC_KB / 16; ++kk)  // K = 16 per instruction: 32 bytes
                 umma<false>(d, sdesc_k128(a + kk * 32), sdesc_k128(b + kk * 32), TC_IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
-              umma_commit(&empty_bar[st]);  // frees the stage once these MMAs have read it
+              if (CS == 1)
+                umma_commit(&empty_bar[st]);  // frees the stage once these MMAs have read it
+              else
+                umma_commit_multicast(&empty_bar[st], (uint16_t)((1u << CS) - 1u));  // in every CTA of the cluster
             }
             if (!ok) break;
             umma_commit(&acc_full[buf]);  // the chunk's accumulator is complete
@@ -508,6 +601,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
                  : "memory");
   }
+  if (CS > 1) cluster_sync_all();  // no CTA leaves while a peer may still signal it
 }
 
 // 3-D map over the slices S[s][rows][Kp] (bf16), box 64 (K) x box_rows x 1.
@@ -522,22 +616,41 @@ bool slice_map(CUtensorMap* map, const __nv_bfloat16* S, int64_t rows, int64_t K
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-template <int TCN>
+template <int TCN, int CS>
 int launch_tc(fraclap_ctx* ctx, const __nv_bfloat16* SA, const __nv_bfloat16* SB, const int* ea, const int* eb,
               int64_t M, int64_t N, int64_t Kp, int sl, int bits, int64_t chunk, double alpha, double beta,
               double* C, int64_t ldc, bool lower, cudaStream_t st) {
   CUtensorMap ma, mb;
-  FL_CHECK(ctx, slice_map(&ma, SA, M, Kp, sl, TC_M) && slice_map(&mb, SB, N, Kp, sl, TCN), FRACLAP_ERR_CUDA,
+  FL_CHECK(ctx, slice_map(&ma, SA, M, Kp, sl, TC_M) && slice_map(&mb, SB, N, Kp, sl, TCN / CS), FRACLAP_ERR_CUDA,
            "ozaki_gemm: tensor map encoding failed");
   const size_t smem = (size_t)OzTile<TCN>::STAGES * OzTile<TCN>::STAGE_BYTES + 1024;
-  FL_CUDA(ctx, cudaFuncSetAttribute(ozaki_tc_kernel<TCN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int TM = (int)cdiv(M, TC_M), TN = (int)cdiv(N, TCN);
+  auto kern = ozaki_tc_kernel<TCN, CS>;
+  FL_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the raster counts clusters of CS tile rows (a tile of CS * 128 rows)
+  const int TM = (int)cdiv(cdiv(M, TC_M), CS), TN = (int)cdiv(N, TCN);
   const int G = std::max(1, std::min(ctx->oz_group > 0 ? ctx->oz_group : TM, TM));
-  const int64_t tiles = ozaki_tile_count(TM, TN, G, lower, TC_M, TCN);
-  FL_CHECK(ctx, tiles <= INT32_MAX, FRACLAP_ERR_UNSUPPORTED, "ozaki_gemm: too many tiles");
-  ozaki_tc_kernel<TCN><<<(unsigned)tiles, TC_THREADS, smem, st>>>(ma, mb, ea, eb, M, N, Kp, sl, bits, chunk, alpha,
-                                                                  beta, C, ldc, lower ? 1 : 0, G, ctx->wait_cycles,
-                                                                  ctx->d_status);
+  const int64_t tiles = ozaki_tile_count(TM, TN, G, lower, CS * TC_M, TCN);
+  FL_CHECK(ctx, tiles * CS <= INT32_MAX, FRACLAP_ERR_UNSUPPORTED, "ozaki_gemm: too many tiles");
+  int lw = lower ? 1 : 0;
+  if (CS == 1) {
+    kern<<<(unsigned)tiles, TC_THREADS, smem, st>>>(ma, mb, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc,
+                                                    lw, G, ctx->wait_cycles, ctx->d_status);
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(tiles * CS));
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  FL_CUDA(ctx, cudaLaunchKernelEx(&cfg, kern, ma, mb, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc, lw, G,
+                                  ctx->wait_cycles, ctx->d_status));
   return 0;
 }
 
@@ -551,7 +664,34 @@ size_t ozaki_ws(int64_t M, int64_t N, int64_t K, int s) {
   ar.take<__nv_bfloat16>((int64_t)s * N * Kp);
   ar.take<int>(M);
   ar.take<int>(N);
+  ar.take<unsigned long long>(std::max(M, N));
   return ar.off;
+}
+
+// Exponents and digit slices of the rows of op(X) (R rows of length K):
+// contiguous rows (trans) one block per row; strided rows through the
+// column-parallel maximum and the tiled slicing.
+int slice_operand(fraclap_ctx* ctx, const double* X, int64_t ldx, bool trans, int64_t R, int64_t K, int64_t Kp,
+                  int sl, int bits, int* ex, __nv_bfloat16* S, unsigned long long* mx, cudaStream_t st) {
+  if (trans || Kp / 32 > 65535 || cdiv(K, OZ_MAX_KCH) > 65535) {
+    row_exponents<<<(unsigned)R, 256, 0, st>>>(X, ldx, trans, K, ex);
+    count_launch(ctx);
+    const unsigned gs = (unsigned)std::min<int64_t>(cdiv(R * Kp, 256), 152 * 32);
+    make_slices<<<gs, 256, 0, st>>>(X, ldx, trans, R, K, Kp, ex, sl, bits, S);
+    count_launch(ctx);
+  } else {
+    FL_CUDA(ctx, cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * (size_t)R, st));
+    row_absmax_strided<<<dim3((unsigned)cdiv(R, 256), (unsigned)std::max<int64_t>(cdiv(K, OZ_MAX_KCH), 1)), 256, 0,
+                         st>>>(X, ldx, R, K, mx);
+    count_launch(ctx);
+    exponents_of_max<<<(unsigned)cdiv(R, 256), 256, 0, st>>>(mx, R, ex);
+    count_launch(ctx);
+    make_slices_strided<<<dim3((unsigned)cdiv(R, 32), (unsigned)(Kp / 32)), dim3(32, 8), 0, st>>>(
+        X, ldx, R, K, Kp, ex, sl, bits, S);
+    count_launch(ctx);
+  }
+  FL_CUDA(ctx, cudaGetLastError());
+  return 0;
 }
 
 // C = alpha op(A) op(B) + beta C, FP64-accurate through s BF16 slices
@@ -568,7 +708,8 @@ int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t
   __nv_bfloat16* SB = ar->take<__nv_bfloat16>((int64_t)smax * N * Kp);
   int* ea = ar->take<int>(M);
   int* eb = ar->take<int>(N);
-  FL_CHECK(ctx, eb != nullptr, FRACLAP_ERR_ALLOC, "ozaki_gemm: workspace too small");
+  unsigned long long* mx = ar->take<unsigned long long>(std::max(M, N));
+  FL_CHECK(ctx, mx != nullptr, FRACLAP_ERR_ALLOC, "ozaki_gemm: workspace too small");
   // op(A) rows: trans -> A stored K x M; op(B) columns = rows of op(B)^T
   // slice width: 8 bits (exact chunks of 256) for short K, else 7 bits (exact
   // chunks of 1024) with one more slice for the same 8s bits: 3x fewer folds.
@@ -578,22 +719,23 @@ int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t
     sl = (8 * s + 6) / 7;
   }
   const int64_t chunk = (int64_t)1 << (24 - 2 * bits);
-  row_exponents<<<(unsigned)M, 256, 0, st>>>(A, lda, ta, K, ea);
-  count_launch(ctx);
-  row_exponents<<<(unsigned)N, 256, 0, st>>>(B, ldb, !tb, K, eb);
-  count_launch(ctx);
-  const unsigned gs = (unsigned)std::min<int64_t>(cdiv(std::max(M, N) * Kp, 256), 152 * 32);
-  make_slices<<<gs, 256, 0, st>>>(A, lda, ta, M, K, Kp, ea, sl, bits, SA);
-  count_launch(ctx);
-  make_slices<<<gs, 256, 0, st>>>(B, ldb, !tb, N, K, Kp, eb, sl, bits, SB);
-  count_launch(ctx);
+  // rows of op(A) and columns of op(B): contiguous when trans, else strided
+  FL_TRY(slice_operand(ctx, A, lda, ta, M, K, Kp, sl, bits, ea, SA, mx, st));
+  FL_TRY(slice_operand(ctx, B, ldb, !tb, N, K, Kp, sl, bits, eb, SB, mx, st));
   StageTimer tm(ctx, kStageSliceProducts, st);
   if (ctx->tensor_route == 1) {
-    if (ctx->oz_tile_n == 256) {
-      FL_TRY(launch_tc<256>(ctx, SA, SB, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc, lower, st));
+    const int tw = (N <= 128) ? 128 : ctx->oz_tile_n;  // a narrow output takes the 128-column tile
+    const int cs = ctx->oz_cluster;
+#define FL_OZ_LAUNCH(W, K) \
+  launch_tc<W, K>(ctx, SA, SB, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc, lower, st)
+    if (cs == 4) {
+      FL_TRY(tw == 256 ? FL_OZ_LAUNCH(256, 4) : tw == 192 ? FL_OZ_LAUNCH(192, 4) : FL_OZ_LAUNCH(128, 4));
+    } else if (cs == 2) {
+      FL_TRY(tw == 256 ? FL_OZ_LAUNCH(256, 2) : tw == 192 ? FL_OZ_LAUNCH(192, 2) : FL_OZ_LAUNCH(128, 2));
     } else {
-      FL_TRY(launch_tc<128>(ctx, SA, SB, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc, lower, st));
+      FL_TRY(tw == 256 ? FL_OZ_LAUNCH(256, 1) : tw == 192 ? FL_OZ_LAUNCH(192, 1) : FL_OZ_LAUNCH(128, 1));
     }
+#undef FL_OZ_LAUNCH
   } else {
     dim3 grid((unsigned)cdiv(M, OZ_BM), (unsigned)cdiv(N, OZ_BN));
     ozaki_kernel<<<grid, OZ_NT, 0, st>>>(SA, SB, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc, lower);
@@ -645,13 +787,19 @@ extern "C" int fraclap_set_schedule(fraclap_ctx* ctx, int knob, int value) {
       ctx->fp32_stages_tc = value;
       return 0;
     case FRACLAP_SCHED_OZAKI_TILE_N:
-      FL_CHECK(ctx, value == 128 || value == 256, FRACLAP_ERR_INVALID_ARG, "set_schedule: tile width must be 128 or 256");
+      FL_CHECK(ctx, value == 128 || value == 192 || value == 256, FRACLAP_ERR_INVALID_ARG,
+               "set_schedule: tile width must be 128, 192 or 256");
       ctx->oz_tile_n = value;
       return 0;
     case FRACLAP_SCHED_Q2_PARTS:
       FL_CHECK(ctx, value == 0 || value == 4 || value == 8 || value == 16, FRACLAP_ERR_INVALID_ARG,
                "set_schedule: Q2 parts must be 0, 4, 8 or 16");
       ctx->q2_parts = value;
+      return 0;
+    case FRACLAP_SCHED_OZAKI_CLUSTER:
+      FL_CHECK(ctx, value == 1 || value == 2 || value == 4, FRACLAP_ERR_INVALID_ARG,
+               "set_schedule: slice-product cluster must be 1, 2 or 4 CTAs");
+      ctx->oz_cluster = value;
       return 0;
     default:
       return set_error(ctx, FRACLAP_ERR_INVALID_ARG, "set_schedule: unknown knob %d", knob);
@@ -666,6 +814,7 @@ extern "C" int fraclap_get_schedule(const fraclap_ctx* ctx, int knob) {
     case FRACLAP_SCHED_FP32_STAGES: return ctx->fp32_stages_tc;
     case FRACLAP_SCHED_OZAKI_TILE_N: return ctx->oz_tile_n;
     case FRACLAP_SCHED_Q2_PARTS: return ctx->q2_parts;
+    case FRACLAP_SCHED_OZAKI_CLUSTER: return ctx->oz_cluster;
     default: return FRACLAP_ERR_INVALID_ARG;
   }
 }

@@ -35,22 +35,27 @@ def test_band_width_and_workers_are_tuned_and_cached(tmp_path):
 
 
 def test_ozaki_schedule_is_tuned_cached_and_applied(tmp_path):
-    """The slice-product schedule (raster group, digit width) is measured
-    over the candidates, cached, answered from the cache by a second tuner,
+    """The slice-product schedule (raster group, digit width, tile width,
+    cluster size) is measured over the candidates, cached, answered from the
+    cache by a second tuner,
     and set on a context, whose products stay FP64-accurate."""
     from paper_1911_11906_gb300 import autotune as A
     import paper_1911_11906_gb300 as F
     path = str(tmp_path / "tune.json")
-    sched = A.best_ozaki_schedule(640, groups=(0, 2), bits=(7, 8), tiles=(128, 256), tuner=A.Autotuner(path),
-                                  reps=1)
+    sched = A.best_ozaki_schedule(640, groups=(0, 2), bits=(7, 8), tiles=(128, 256), clusters=(1, 2),
+                                  tuner=A.Autotuner(path), reps=1)
     assert sched["ozaki_group"] in (0, 2) and sched["ozaki_bits"] in (7, 8) and sched["ozaki_tile_n"] in (128, 256)
+    assert sched["ozaki_cluster"] in (1, 2)
     entries = json.load(open(path))["entries"]
     (val,) = [v for k, v in entries.items() if k.startswith("ozaki_schedule:")]
-    assert set(val["seconds"]) == {f"{g}/{w}/{t}" for g in (0, 2) for w in (7, 8) for t in (128, 256)}
-    assert A.best_ozaki_schedule(700, groups=(0, 2), bits=(7, 8), tiles=(128, 256), tuner=A.Autotuner(path)) == sched
+    assert set(val["seconds"]) == {f"{g}/{w}/{t}/{c}" for g in (0, 2) for w in (7, 8) for t in (128, 256)
+                                   for c in (1, 2)}
+    assert A.best_ozaki_schedule(700, groups=(0, 2), bits=(7, 8), tiles=(128, 256), clusters=(1, 2),
+                                 tuner=A.Autotuner(path)) == sched
     ctx = F.Context()
     A.apply_schedule(ctx, sched)
     assert ctx.get_schedule("ozaki_group") == sched["ozaki_group"]
+    assert ctx.get_schedule("ozaki_cluster") == sched["ozaki_cluster"]
     rng = np.random.default_rng(640)
     X = rng.standard_normal((640, 300))
     got = F.dgemm_ozaki(torch.from_numpy(X.T.copy()).cuda().t(), torch.from_numpy(X.T.copy()).cuda().t(),

@@ -139,16 +139,19 @@ def test_dgemm_ozaki_is_fp64_accurate(ta, tb, m, n, k):
     assert np.max(np.abs(got - ref) / (rowmax + 1e-300)) <= 1e-15
 
 
-@pytest.mark.parametrize("group,bits,tile_n", [(0, 7, 128), (1, 7, 128), (3, 8, 128), (8, 8, 128), (8, 7, 128),
-                                               (0, 7, 256), (4, 7, 256), (2, 8, 256)])
+@pytest.mark.parametrize("group,bits,tile_n,cluster", [
+    (0, 7, 128, 1), (1, 7, 128, 1), (3, 8, 128, 1), (8, 8, 128, 1), (8, 7, 128, 1), (0, 7, 256, 1), (4, 7, 256, 1),
+    (2, 8, 256, 1), (0, 7, 128, 2), (0, 7, 256, 2), (3, 8, 256, 2), (0, 7, 128, 4), (4, 7, 256, 4), (1, 8, 128, 4),
+    (0, 7, 192, 1), (3, 8, 192, 1), (0, 7, 192, 2), (2, 7, 192, 4)])
 @pytest.mark.parametrize("ta,m,n,k", [(True, 300, 260, 1000), (False, 520, 130, 2000), (True, 129, 385, 257),
                                       (True, 640, 600, 300)])
-def test_dgemm_ozaki_schedules_agree(group, bits, tile_n, ta, m, n, k):
-    """Every tile order (raster group), tile width and digit width gives an
-    FP64-accurate product (against math.fsum at sampled entries and the FP64
-    product everywhere), and schedules with the same digit width give the
-    same bits: only the tiling and the order of the tiles over the CTAs
-    differ, not the sums of any output element."""
+def test_dgemm_ozaki_schedules_agree(group, bits, tile_n, cluster, ta, m, n, k):
+    """Every tile order (raster group), tile width, cluster size (B tile
+    shared by TMA multicast; clusters that run past the last tile row) and
+    digit width gives an FP64-accurate product (against math.fsum at sampled
+    entries and the FP64 product everywhere), and schedules with the same
+    digit width give the same bits: only the tiling and the order of the
+    tiles over the CTAs differ, not the sums of any output element."""
     import math
     F = _F()
     rng = np.random.default_rng(m + 3 * n + k + group)
@@ -159,8 +162,9 @@ def test_dgemm_ozaki_schedules_agree(group, bits, tile_n, ta, m, n, k):
     ctx.set_schedule("ozaki_group", group)
     ctx.set_schedule("ozaki_bits", bits)
     ctx.set_schedule("ozaki_tile_n", tile_n)
+    ctx.set_schedule("ozaki_cluster", cluster)
     assert ctx.get_schedule("ozaki_group") == group and ctx.get_schedule("ozaki_bits") == bits
-    assert ctx.get_schedule("ozaki_tile_n") == tile_n
+    assert ctx.get_schedule("ozaki_tile_n") == tile_n and ctx.get_schedule("ozaki_cluster") == cluster
     got = F.dgemm_ozaki(_colmajor(A), _colmajor(B), trans_a=ta, ctx=ctx).cpu().numpy()
     scale = np.abs(opA).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * k
     assert np.max(np.abs(got - opA @ B) / scale) <= 1e-15
@@ -176,8 +180,8 @@ def test_dgemm_ozaki_schedules_agree(group, bits, tile_n, ta, m, n, k):
 def test_schedule_knobs_reject_bad_values():
     F = _F()
     ctx = F.Context()
-    for knob, bad in (("ozaki_group", -1), ("ozaki_bits", 6), ("ozaki_bits", 9), ("ozaki_tile_n", 192),
-                      ("fp32_stages_tc", 2), ("q2_parts", 5)):
+    for knob, bad in (("ozaki_group", -1), ("ozaki_bits", 6), ("ozaki_bits", 9), ("ozaki_tile_n", 160),
+                      ("fp32_stages_tc", 2), ("q2_parts", 5), ("ozaki_cluster", 3), ("ozaki_cluster", 8)):
         with pytest.raises(F.FraclapError):
             ctx.set_schedule(knob, bad)
     assert ctx.lib.fraclap_set_schedule(ctx.handle, 99, 1) == -1

@@ -128,14 +128,16 @@ def _csr_cuda(A):
     return (torch.from_numpy(A.rowptr).cuda(), torch.from_numpy(A.col).cuda(), torch.from_numpy(A.val).cuda())
 
 
-@pytest.mark.parametrize("tc,tile_n,q2", [(0, 256, 0), (1, 128, 0), (0, 128, 8), (0, 128, 16), (0, 256, 4)])
+@pytest.mark.parametrize("tc,tile_n,q2,cluster", [(0, 256, 0, 1), (1, 128, 0, 1), (0, 128, 8, 1), (0, 128, 16, 1),
+                                                  (0, 256, 4, 1), (0, 256, 0, 2), (0, 128, 0, 4), (0, 192, 8, 1)])
 @pytest.mark.parametrize("which,b,iters", [("square23", 32, 6), ("ellipse36", 32, 6), ("ellipse36", 64, 6),
                                             ("ellipse64", 32, 6), ("ellipse48", 16, 6), ("square9", 8, 6),
                                             ("cube6", 32, 6)])
-def test_eig_full_mixed_refined_vs_oracle(which, b, iters, tc, tile_n, q2):
+def test_eig_full_mixed_refined_vs_oracle(which, b, iters, tc, tile_n, q2, cluster):
     """FP32 stages (FMA kernel, or three TF32 products on the tensor cores
     with tc = 1) + Ogita-Aishima refinement (slice products on 128- or
-    256-column tiles) reach the FP64 tolerances."""
+    256-column tiles, alone or in clusters sharing the B tile, lower
+    triangle only) reach the FP64 tolerances."""
     F = _F()
     if which.startswith("square"):
         p = I.square_problem(int(which[6:]))
@@ -151,6 +153,7 @@ def test_eig_full_mixed_refined_vs_oracle(which, b, iters, tc, tile_n, q2):
     ctx.set_schedule("fp32_stages_tc", tc)
     ctx.set_schedule("ozaki_tile_n", tile_n)
     ctx.set_schedule("q2_parts", q2)
+    ctx.set_schedule("ozaki_cluster", cluster)
     lam, V = F.eig_full_mixed(_colmajor(D), *_csr_cuda(A), refine_iters=iters, ctx=ctx)
     lam, V = lam.cpu().numpy(), V.cpu().numpy()
     _check_decomposition(D, lam_o, lam, V)
