@@ -226,11 +226,11 @@ def refine_slice_counts(iterations: int, cap: int, digit_bits: int = 7) -> list:
     return out
 
 
-# DRAM bytes per BF16 flop of ozaki_tc_kernel from one ncu capture of the
-# 4096^3 product with the current kernel (None until captured: the tile order
-# changed since the last capture); its tile re-streaming grows in proportion
-# to the flops.
-OZAKI_DRAM_BYTES_PER_FLOP = None
+# DRAM bytes per BF16 flop of ozaki_tc_kernel (128 x 192 tiles) from one ncu
+# capture of the 4096^3 product with the current kernel: (9.98 + 1.32) GB
+# over 4.95e12 flop; its tile re-streaming grows in proportion to the flops.
+# None whenever the kernel changes until it is captured again.
+OZAKI_DRAM_BYTES_PER_FLOP = 2.285e-3
 
 
 def run_path(F, ctx, p, path, args, mask, Fd, pf, pa, U, app_ws, barrier, steps=None, warmup=None):
@@ -396,7 +396,9 @@ def run_gpu(args, rank, world, local_rank):
             total += apply_slice_flops(n, Fd.shape[1], k, APPLY_SLICES[head], digit_bits)
             launches_per_step += 2
         work = total / max(launches_per_step, 1)
-        traffic = OZAKI_DRAM_BYTES_PER_FLOP * work if OZAKI_DRAM_BYTES_PER_FLOP else None
+        # the captured figure holds for the captured tile width and no cluster
+        captured = R["ctx"].get_schedule("ozaki_tile_n") == 192 and R["ctx"].get_schedule("ozaki_cluster") == 1
+        traffic = OZAKI_DRAM_BYTES_PER_FLOP * work if (OZAKI_DRAM_BYTES_PER_FLOP and captured) else None
         # the kernel runs inside a seconds-long step: the sustained BF16 figure is its peak
         peak = _measured_peak("bf16_tflops_sustained") or _measured_peak("bf16_tflops") or 1700.0
         roof = {"kernel": "ozaki_tc_kernel (residual products of the refinement and the apply's two products: "

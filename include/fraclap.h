@@ -584,9 +584,9 @@ int fraclap_partition_spectrum(fraclap_ctx* ctx, int64_t n, const int64_t* rowpt
  *    4 rows per lane; more parts give more warps over the same columns; FP64
  *    takes 8 when asked for 4), or 0 for the default 8 [0].
  *  FRACLAP_SCHED_OZAKI_CLUSTER: CTAs of the slice-product kernel per thread-
- *    block cluster, 1, 2 or 4: the cluster's CTAs take consecutive tile rows
- *    of one tile column and share its B tile through TMA multicast, each
- *    loading 1/CS of it (fewer L2-to-SM bytes per flop) [1].
+ *    block cluster, 1 or 2: the two CTAs of a cluster take consecutive tile
+ *    rows of one tile column and share its B tile through TMA multicast,
+ *    each loading half of it (fewer L2-to-SM bytes per flop) [1].
  * ---------------------------------------------------------------------- */
 enum { FRACLAP_SCHED_OZAKI_GROUP = 0, FRACLAP_SCHED_OZAKI_BITS = 1, FRACLAP_SCHED_FP32_STAGES = 2,
        FRACLAP_SCHED_OZAKI_TILE_N = 3, FRACLAP_SCHED_Q2_PARTS = 4, FRACLAP_SCHED_OZAKI_CLUSTER = 5 };

@@ -24,7 +24,7 @@ struct fraclap_ctx {
   int oz_group = 8;              // slice-product kernel: tile rows per raster group (0 = all rows)
   int oz_bits = 7;               // slice-product kernel: digit width for K > 256 (7 or 8)
   int oz_tile_n = 192;           // slice-product kernel: tile columns (128, 192 or 256)
-  int oz_cluster = 1;            // slice-product kernel: CTAs per cluster sharing a B tile (1, 2, 4)
+  int oz_cluster = 1;            // slice-product kernel: CTAs per cluster sharing a B tile (1 or 2)
   int q2_parts = 0;              // stage-2 back-transformation at b = 64: lane parts per window (0: default 8)
   int fp32_stages_tc = 0;        // mixed route: FP32 band reduction and Q1 products on the tensor cores (TF32 x 3)
   void* tc_scratch = nullptr;    // split operands of the TF32 tensor-core route of FP32 GEMMs

@@ -353,7 +353,7 @@ __device__ __forceinline__ void ozaki_tile_of(int64_t idx, int TM, int TN, int G
   *tn = 0;
 }
 
-// CS > 1: a cluster of CS CTAs takes CS consecutive tile rows of one tile
+// CS = 2: a cluster of CS CTAs takes CS consecutive tile rows of one tile
 // column.  They need the same B tile, so each CTA loads 1/CS of it (TCN / CS
 // rows of op(B)) with one TMA multicast into the same stage of every CTA of
 // the cluster: the L2-to-SM bytes per k-block drop from A + B to A + B / CS.
@@ -728,9 +728,7 @@ int ozaki_gemm(fraclap_ctx* ctx, bool ta, bool tb, int64_t M, int64_t N, int64_t
     const int cs = ctx->oz_cluster;
 #define FL_OZ_LAUNCH(W, K) \
   launch_tc<W, K>(ctx, SA, SB, ea, eb, M, N, Kp, sl, bits, chunk, alpha, beta, C, ldc, lower, st)
-    if (cs == 4) {
-      FL_TRY(tw == 256 ? FL_OZ_LAUNCH(256, 4) : tw == 192 ? FL_OZ_LAUNCH(192, 4) : FL_OZ_LAUNCH(128, 4));
-    } else if (cs == 2) {
+    if (cs == 2) {
       FL_TRY(tw == 256 ? FL_OZ_LAUNCH(256, 2) : tw == 192 ? FL_OZ_LAUNCH(192, 2) : FL_OZ_LAUNCH(128, 2));
     } else {
       FL_TRY(tw == 256 ? FL_OZ_LAUNCH(256, 1) : tw == 192 ? FL_OZ_LAUNCH(192, 1) : FL_OZ_LAUNCH(128, 1));
@@ -797,8 +795,8 @@ extern "C" int fraclap_set_schedule(fraclap_ctx* ctx, int knob, int value) {
       ctx->q2_parts = value;
       return 0;
     case FRACLAP_SCHED_OZAKI_CLUSTER:
-      FL_CHECK(ctx, value == 1 || value == 2 || value == 4, FRACLAP_ERR_INVALID_ARG,
-               "set_schedule: slice-product cluster must be 1, 2 or 4 CTAs");
+      FL_CHECK(ctx, value == 1 || value == 2, FRACLAP_ERR_INVALID_ARG,
+               "set_schedule: slice-product cluster must be 1 or 2 CTAs");
       ctx->oz_cluster = value;
       return 0;
     default:

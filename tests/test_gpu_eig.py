@@ -129,7 +129,7 @@ def _csr_cuda(A):
 
 
 @pytest.mark.parametrize("tc,tile_n,q2,cluster", [(0, 256, 0, 1), (1, 128, 0, 1), (0, 128, 8, 1), (0, 128, 16, 1),
-                                                  (0, 256, 4, 1), (0, 256, 0, 2), (0, 128, 0, 4), (0, 192, 8, 1)])
+                                                  (0, 256, 4, 1), (0, 256, 0, 2), (0, 128, 0, 2), (0, 192, 8, 1)])
 @pytest.mark.parametrize("which,b,iters", [("square23", 32, 6), ("ellipse36", 32, 6), ("ellipse36", 64, 6),
                                             ("ellipse64", 32, 6), ("ellipse48", 16, 6), ("square9", 8, 6),
                                             ("cube6", 32, 6)])
