@@ -148,6 +148,47 @@ __global__ void make_slices(const double* A, int64_t lda, bool trans, int64_t M,
   }
 }
 
+// The slices of an operand whose rows are contiguous (trans), for s * bits
+// <= 64: a thread takes eight consecutive entries of a row and writes each
+// digit's eight BF16 values as one 16-byte store (Kp is a multiple of 64, so
+// every store is aligned); the digits are those of write_digits.
+__global__ void make_slices_rows(const double* A, int64_t lda, int64_t M, int64_t K, int64_t Kp,
+                                 const int* ex, int s, int bits, __nv_bfloat16* S) {
+  const int64_t per_row = Kp / 8, total = M * per_row;
+  const int tb = bits * s;
+  const unsigned long long mask = (1ull << bits) - 1ull;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / per_row, k0 = (t % per_row) * 8;
+    const int e = ex[i];
+    unsigned long long u[8];
+    float sg[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double a = (k0 + q < K) ? A[k0 + q + i * lda] : 0.0;
+      const unsigned long long bitsA = (unsigned long long)__double_as_longlong(a);
+      const int E = (int)((bitsA >> 52) & 0x7FF);
+      const unsigned long long mant = (bitsA & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+      const int sh = (E ? E : 1) - 1075 + tb - e;
+      u[q] = (sh >= 64 || sh <= -64) ? 0ull : (sh >= 0 ? (mant << sh) : (mant >> -sh));
+      sg[q] = (a < 0.0) ? -1.0f : 1.0f;
+    }
+    for (int p = 0; p < s; ++p) {
+      const int rs = bits * (s - 1 - p);
+      uint32_t w[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const unsigned short lo =
+            __bfloat16_as_ushort(__float2bfloat16_rn(sg[2 * h] * (float)((u[2 * h] >> rs) & mask)));
+        const unsigned short hi =
+            __bfloat16_as_ushort(__float2bfloat16_rn(sg[2 * h + 1] * (float)((u[2 * h + 1] >> rs) & mask)));
+        w[h] = (uint32_t)lo | ((uint32_t)hi << 16);
+      }
+      *reinterpret_cast<uint4*>(S + ((int64_t)p * M + i) * Kp + k0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
 // The same slices of an untransposed column-major operand (rows strided):
 // 32 x 32 tiles of (i, k) staged in shared memory, read along i and written
 // along k, so that both the FP64 reads and the BF16 writes are contiguous
@@ -676,8 +717,13 @@ int slice_operand(fraclap_ctx* ctx, const double* X, int64_t ldx, bool trans, in
   if (trans || Kp / 32 > 65535 || cdiv(K, OZ_MAX_KCH) > 65535) {
     row_exponents<<<(unsigned)R, 256, 0, st>>>(X, ldx, trans, K, ex);
     count_launch(ctx);
-    const unsigned gs = (unsigned)std::min<int64_t>(cdiv(R * Kp, 256), 152 * 32);
-    make_slices<<<gs, 256, 0, st>>>(X, ldx, trans, R, K, Kp, ex, sl, bits, S);
+    if (trans && sl * bits <= 64) {
+      const unsigned gs = (unsigned)std::min<int64_t>(cdiv(R * (Kp / 8), 256), 152 * 16);
+      make_slices_rows<<<gs, 256, 0, st>>>(X, ldx, R, K, Kp, ex, sl, bits, S);
+    } else {
+      const unsigned gs = (unsigned)std::min<int64_t>(cdiv(R * Kp, 256), 152 * 32);
+      make_slices<<<gs, 256, 0, st>>>(X, ldx, trans, R, K, Kp, ex, sl, bits, S);
+    }
     count_launch(ctx);
   } else {
     FL_CUDA(ctx, cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * (size_t)R, st));

@@ -261,54 +261,147 @@ __global__ void mark_big(const int* cid, const int* list, int64_t n, int* big) {
 }
 
 // Merges the spans (sorted positions) into clusters: cid[pos] = cluster
-// index or -1; list = (start, size) pairs; *count.  One thread.  A second
-// pass (flag != nullptr) runs only if *flag is set.
-__global__ void merge_spans(const int* reach, int64_t n, int* cid, int* list, int* count, const int* flag) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (flag && !*flag) return;
-  int c = 0;
-  int64_t i = 0;
-  while (i < n) {
-    int64_t j = reach[i], k = i;
-    while (k <= j) {
-      if (reach[k] > j) j = reach[k];
-      ++k;
-    }
-    if (j > i) {
-      list[2 * c] = (int)i;
-      list[2 * c + 1] = (int)(j - i + 1);
-      for (int64_t q = i; q <= j; ++q) cid[q] = c;
-      ++c;
-    } else {
-      cid[i] = -1;
-    }
-    i = j + 1;
+// index or -1; list = (start, size) pairs, clusters in position order;
+// *count.  A second pass (flag != nullptr) runs only if *flag is set.
+// reach[k] >= k, so with the prefix maximum M[k] = max(reach[0..k]) a
+// cluster (or a lone position) ends at k exactly when M[k] = k: nothing at
+// or before k reaches past it.  One CTA of kMergeThreads threads, each over
+// a run of consecutive positions: a block scan of the runs' maxima gives
+// M, a block scan of the counts of cluster starts gives the indices
+// (n <= 65535).
+constexpr int kMergeThreads = 1024;
+__device__ __forceinline__ int block_scan_exclusive(int v, bool is_max, int* sh) {
+  // exclusive scan (max or sum) over the CTA's threads in thread order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = is_max ? max(x, y) : x + y;
   }
-  *count = c;
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : (is_max ? INT_MIN : 0);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w = is_max ? max(w, y) : w + y;
+    }
+    sh[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  const int before_warp = (warp == 0) ? (is_max ? INT_MIN : 0) : sh[warp - 1];
+  const int excl_in_warp = __shfl_up_sync(0xffffffffu, x, 1);
+  const int mine = (lane == 0) ? (is_max ? INT_MIN : 0) : excl_in_warp;
+  const int r = is_max ? max(before_warp, mine) : before_warp + mine;
+  __syncthreads();  // sh is reused by the next scan
+  return r;
+}
+__global__ void __launch_bounds__(kMergeThreads) merge_spans(const int* reach, int64_t n, int* cid, int* list,
+                                                             int* count, const int* flag) {
+  if (flag && !*flag) return;
+  __shared__ int sh[32];
+  const int nn = (int)n;
+  const int run = (nn + kMergeThreads - 1) / kMergeThreads;
+  const int k0 = min(nn, (int)threadIdx.x * run), k1 = min(nn, k0 + run);
+  // M[k] for the run: the maximum reach before it, then the running maximum
+  int m = INT_MIN;
+  for (int k = k0; k < k1; ++k) m = max(m, reach[k]);
+  const int before = block_scan_exclusive(m, true, sh);
+  // starts of clusters (segments of more than one position) in the run
+  int cnt = 0;
+  {
+    int M = before;  // M[k0 - 1] (INT_MIN for the first run)
+    for (int k = k0; k < k1; ++k) {
+      const bool start = (k == 0) || (M == k - 1);
+      M = max(M, reach[k]);
+      if (start && M != k) ++cnt;
+    }
+  }
+  const int first = block_scan_exclusive(cnt, false, sh);
+  // cluster of each position and the clusters' starts; a run that does not
+  // begin at a start continues the last cluster started before it
+  {
+    int M = before, c = first;
+    bool in_cl = false;
+    for (int k = k0; k < k1; ++k) {
+      const bool start = (k == 0) || (M == k - 1);
+      M = max(M, reach[k]);
+      if (start) {
+        in_cl = (M != k);
+        if (in_cl) list[2 * c++] = k;
+      } else if (k == k0) {
+        in_cl = true;
+      }
+      cid[k] = in_cl ? c - 1 : -1;
+    }
+  }
+  __syncthreads();  // every start is in list before the sizes are formed
+  {
+    int M = before, c = first;
+    bool in_cl = false;
+    for (int k = k0; k < k1; ++k) {
+      const bool start = (k == 0) || (M == k - 1);
+      M = max(M, reach[k]);
+      if (start) {
+        in_cl = (M != k);
+        if (in_cl) ++c;
+      } else if (k == k0) {
+        in_cl = true;
+      }
+      if (in_cl && M == k) list[2 * (c - 1) + 1] = k - list[2 * (c - 1)] + 1;  // the cluster ends at k
+    }
+  }
+  if (threadIdx.x == kMergeThreads - 1) *count = first + cnt;
 }
 
 // E (FP32) and X32 (FP32 copy of X); pairs inside one cluster get r_ij / 2.
-__global__ void correction(const double* S, int64_t lds, const double* R, int64_t ldr,
-                           const double* lt, const int* rank, const int* cid, int64_t n, float* E,
-                           int64_t lde, const double* X, int64_t ldx, float* X32) {
-  const int64_t total = n * n;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = p % n, j = p / n;
-    const int64_t a = (i >= j) ? i : j, b = (i >= j) ? j : i;  // lower-triangle element
-    const double r = R[a + b * ldr], s = S[a + b * lds];
+// Tile by tile, every global access coalesced: a tile at
+// or below the diagonal stages its own entries of R and S (the diagonal tile
+// takes the mirror of its upper half from the staged lower half), a tile
+// above it stages the tile below the diagonal that holds its entries, read
+// transposed from shared memory.  Block 32 x 8, grid (nt, nt).
+__global__ void __launch_bounds__(256) correction_tiles(const double* S, int64_t lds, const double* R,
+                                                        int64_t ldr, const double* lt, const int* rank,
+                                                        const int* cid, int64_t n, float* E, int64_t lde,
+                                                        const double* X, int64_t ldx, float* X32) {
+  __shared__ double rs[32][33], ss[32][33];  // [column offset][row offset] of the staged lower tile
+  __shared__ double li[32], lj[32];
+  __shared__ int ci[32], cj[32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  const bool below = blockIdx.x >= blockIdx.y;
+  const int64_t a0 = below ? i0 : j0, b0 = below ? j0 : i0;  // staged tile: rows a0.., columns b0..
+  for (int c = ty; c < 32; c += 8) {
+    const int64_t a = a0 + tx, b = b0 + c;
+    const bool in = a < n && b < n;
+    rs[c][tx] = in ? R[a + b * ldr] : 0.0;
+    ss[c][tx] = in ? S[a + b * lds] : 0.0;
+  }
+  if (ty == 0) {
+    const int64_t i = i0 + tx, j = j0 + tx;
+    li[tx] = (i < n) ? lt[i] : 0.0;
+    ci[tx] = (i < n) ? cid[rank[i]] : -1;
+    lj[tx] = (j < n) ? lt[j] : 0.0;
+    cj[tx] = (j < n) ? cid[rank[j]] : -1;
+  }
+  __syncthreads();
+  for (int c = ty; c < 32; c += 8) {
+    const int64_t i = i0 + tx, j = j0 + c;
+    if (i >= n || j >= n) continue;
+    // the lower-triangle element (max(i, j), min(i, j)) in the staged tile
+    const bool mine = below && (blockIdx.x != blockIdx.y || tx >= c);
+    const double r = mine ? rs[c][tx] : rs[tx][c];
+    const double sv = mine ? ss[c][tx] : ss[tx][c];
     double e;
-    const int ci = cid[rank[i]], cj = cid[rank[j]];
-    if (i == j || (ci >= 0 && ci == cj)) {
+    if (i == j || (ci[tx] >= 0 && ci[tx] == cj[c])) {
       e = 0.5 * r;
     } else {
-      e = (s + lt[j] * r) / (lt[j] - lt[i]);
+      e = (sv + lj[c] * r) / (lj[c] - li[tx]);
     }
     E[i + j * lde] = (float)e;
     X32[i + j * n] = (float)X[i + j * ldx];
   }
 }
-
 __global__ void add_correction(double* X, int64_t ldx, const float* P, int64_t n) {
   const int64_t total = n * n;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
@@ -319,16 +412,27 @@ __global__ void add_correction(double* X, int64_t ldx, const float* P, int64_t n
 }
 
 // rank of l_i in ascending order (ties by index); O(n^2) comparisons, one thread per i
-__global__ void ranks(const double* lt, int64_t n, int* rank) {
+// rank[i] = #{j : lt[j] < lt[i] or (lt[j] == lt[i] and j < i)}, a permutation.
+// Thread per i, the j range split over blockIdx.y in chunks staged in shared
+// memory, the chunk counts added into rank (zeroed before; integer sums, so
+// the order of the additions does not matter).  Block 256, grid
+// (ceil(n / 256), ceil(n / kRankChunk)).
+constexpr int kRankChunk = 1024;
+__global__ void __launch_bounds__(256) ranks(const double* lt, int64_t n, int* rank) {
+  __shared__ double sl[kRankChunk];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j0 = (int64_t)blockIdx.y * kRankChunk;
+  const int64_t j1 = (j0 + kRankChunk < n) ? j0 + kRankChunk : n;
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) sl[j - j0] = lt[j];
+  __syncthreads();
   if (i >= n) return;
   const double v = lt[i];
-  int64_t r = 0;
-  for (int64_t j = 0; j < n; ++j) {
-    const double u = lt[j];
+  int r = 0;
+  for (int64_t j = j0; j < j1; ++j) {
+    const double u = sl[j - j0];
     r += (u < v) || (u == v && j < i);
   }
-  rank[i] = (int)r;
+  if (r) atomicAdd(rank + i, r);
 }
 
 // Xs(:, rank[j]) = X(:, j); ls(rank[j]) = l_j.  grid (rows / 256, n)
@@ -855,22 +959,24 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
     count_launch(ctx);
     span.start(kStageRefineUpdate);
     // clusters from unsafe pairs, in sorted order
-    ranks<<<(unsigned)cdiv(n, 128), 128, 0, st>>>(lt, n, rank);
+    FL_CUDA(ctx, cudaMemsetAsync(rank, 0, sizeof(int) * n, st));
+    ranks<<<dim3((unsigned)cdiv(n, 256), (unsigned)cdiv(n, kRankChunk)), 256, 0, st>>>(lt, n, rank);
     count_launch(ctx);
     init_reach<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(reach, n, nullptr);
     count_launch(ctx);
     unsafe_spans<<<flat, 256, 0, st>>>(S, n, R, n, lt, rank, delta, ctx->refine_tau, n, nullptr, reach);
     count_launch(ctx);
-    merge_spans<<<1, 1, 0, st>>>(reach, n, cid, clist + 1, clist, nullptr);
+    merge_spans<<<1, kMergeThreads, 0, st>>>(reach, n, cid, clist + 1, clist, nullptr);
     count_launch(ctx);
     // second pass inside clusters above kMaxCluster (device-side no-op without one)
     FL_CUDA(ctx, cudaMemsetAsync(bigm + n, 0, sizeof(int), st));
     mark_big<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(cid, clist + 1, n, bigm);
     init_reach<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(reach, n, bigm + n);
     unsafe_spans<<<flat, 256, 0, st>>>(S, n, R, n, lt, rank, delta, ctx->refine_tau, n, bigm, reach);
-    merge_spans<<<1, 1, 0, st>>>(reach, n, cid, clist + 1, clist, bigm + n);
+    merge_spans<<<1, kMergeThreads, 0, st>>>(reach, n, cid, clist + 1, clist, bigm + n);
     for (int q = 0; q < 4; ++q) count_launch(ctx);
-    correction<<<flat, 256, 0, st>>>(S, n, R, n, lt, rank, cid, n, E, n, X, ldx, X32);
+    correction_tiles<<<dim3((unsigned)cdiv(n, 32), (unsigned)cdiv(n, 32)), dim3(32, 8), 0, st>>>(
+        S, n, R, n, lt, rank, cid, n, E, n, X, ldx, X32);
     count_launch(ctx);
     // X += X E  (product in FP32)
     FL_TRY(gemm<float>(ctx, false, false, kGemmPlain, D32{n, n, n, X32, n, E, n, P, n, nullptr, 0, nullptr, 0, 0, 1.0, 0.0}, 1, st));
@@ -995,7 +1101,8 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
     count_launch(ctx);
     rayleigh<<<(unsigned)n, 256, 0, st>>>(X, ldx, AX, n, n, lt);
     count_launch(ctx);
-    ranks<<<(unsigned)cdiv(n, 128), 128, 0, st>>>(lt, n, rank);
+    FL_CUDA(ctx, cudaMemsetAsync(rank, 0, sizeof(int) * n, st));
+    ranks<<<dim3((unsigned)cdiv(n, 256), (unsigned)cdiv(n, kRankChunk)), 256, 0, st>>>(lt, n, rank);
     count_launch(ctx);
     permute_columns<<<dim3((unsigned)cdiv(n, 256), (unsigned)n), 256, 0, st>>>(X, ldx, rank, n, AX, lt, ls);
     count_launch(ctx);

@@ -274,32 +274,74 @@ __global__ void dc_merge_prep(DcBuf<T> B, const double* e, const double* lambda,
   int* flag = B.outsrc + lo;  // scratch
   for (int64_t i = tid; i < nm; i += nt) flag[i] = (rho * fabs(zp[i]) <= tol) ? 1 : 0;
   __syncthreads();
-  // close poles: Givens rotations between consecutive survivors (sequential)
-  if (tid == 0) {
-    int64_t nrot = 0, prev = -1;
-    for (int64_t i = 0; i < nm; ++i) {
-      if (flag[i]) continue;
-      if (prev >= 0) {
-        const double zp_ = zp[prev], zj = zp[i];
-        const double r = hypot(zp_, zj);
-        const double c = zj / r, s = -zp_ / r;
-        if (fabs((Dp[i] - Dp[prev]) * c * s) <= tol) {
-          zp[i] = r;
-          zp[prev] = 0.0;
-          const double dp = Dp[prev], dj = Dp[i];
-          Dp[prev] = dp * c * c + dj * s * s;
-          Dp[i] = dp * s * s + dj * c * c;
-          B.rot_i[lo + nrot] = (int)prev;
-          B.rot_j[lo + nrot] = (int)i;
-          B.rot_c[lo + nrot] = c;
-          B.rot_s[lo + nrot] = s;
-          ++nrot;
-          flag[prev] = 1;
-        }
+  // close poles: Givens rotations between consecutive survivors, in order.
+  // Each survivor i is tested against the survivor before it; a rotation
+  // deflates that one and changes z_i and D_i, so every later test depends
+  // on the earlier ones.  Warp 0 takes 32 positions at a time, tests all
+  // their pairs at once with the values as they stand, accepts the pairs
+  // before the first rotation, applies that rotation (the same arithmetic
+  // as a sequential pass) and restarts after it.
+  if (tid < 32) {
+    const int lane = tid;
+    int64_t nrot = 0, cur = -1;  // cur: the last survivor so far
+    double zc = 0.0, dc = 0.0;   // its current z and D
+    int64_t base = 0;
+    while (base < nm) {
+      const int64_t pos = base + lane;
+      const bool valid = pos < nm && !flag[pos];
+      const double z = valid ? zp[pos] : 0.0, d = valid ? Dp[pos] : 0.0;
+      const unsigned mask = __ballot_sync(0xffffffffu, valid);
+      // the survivor before this lane's position: a lower lane, or cur
+      const unsigned below = mask & ((1u << lane) - 1u);
+      const int pl = below ? 31 - __clz(below) : -1;
+      const double zq = __shfl_sync(0xffffffffu, z, pl < 0 ? 0 : pl);
+      const double dq = __shfl_sync(0xffffffffu, d, pl < 0 ? 0 : pl);
+      const bool has_pred = valid && (pl >= 0 || cur >= 0);
+      const double zpr = (pl >= 0) ? zq : zc, dpr = (pl >= 0) ? dq : dc;
+      bool rot = false;
+      double r = 0.0, c = 0.0, sn = 0.0;
+      if (has_pred) {
+        r = hypot(zpr, z);
+        c = z / r;
+        sn = -zpr / r;
+        rot = fabs((d - dpr) * c * sn) <= tol;
       }
-      prev = i;
+      const unsigned rmask = __ballot_sync(0xffffffffu, rot);
+      if (rmask == 0u) {  // no rotation among these pairs
+        if (mask) {
+          const int hl = 31 - __clz(mask);
+          cur = base + hl;
+          zc = __shfl_sync(0xffffffffu, z, hl);
+          dc = __shfl_sync(0xffffffffu, d, hl);
+        }
+        base += 32;
+        continue;
+      }
+      const int fl = __ffs(rmask) - 1;  // the first rotation: pair (its predecessor, base + fl)
+      if (lane == fl) {
+        const int64_t pv = (pl >= 0) ? base + pl : cur;
+        zp[pos] = r;
+        zp[pv] = 0.0;
+        const double dp = dpr, dj = d;
+        Dp[pv] = dp * c * c + dj * sn * sn;
+        const double dnew = dp * sn * sn + dj * c * c;
+        Dp[pos] = dnew;
+        B.rot_i[lo + nrot] = (int)pv;
+        B.rot_j[lo + nrot] = (int)pos;
+        B.rot_c[lo + nrot] = c;
+        B.rot_s[lo + nrot] = sn;
+        flag[pv] = 1;
+        zc = r;
+        dc = dnew;
+      }
+      __syncwarp();
+      zc = __shfl_sync(0xffffffffu, zc, fl);
+      dc = __shfl_sync(0xffffffffu, dc, fl);
+      cur = base + fl;
+      ++nrot;
+      base = base + fl + 1;
     }
-    s_nrot = nrot;
+    if (lane == 0) s_nrot = nrot;
   }
   __syncthreads();
   const int64_t nrot = s_nrot;

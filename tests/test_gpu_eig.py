@@ -41,6 +41,11 @@ def _tridiag_cases():
     cases.append(("glued", np.ones(200), np.full(199, 1e-10)))
     cases.append(("zero_coupling", np.arange(150.0), np.zeros(149)))
     cases.append(("wilkinson", np.abs(np.arange(-60, 61)).astype(float), np.ones(120)))
+    # many close poles in every merge: rotations within and across the
+    # deflation pass's 32-position groups
+    cases.append(("wilkinson401", np.abs(np.arange(-200, 201)).astype(float), np.ones(400)))
+    cases.append(("clusters1000", np.floor(np.arange(1000) / 7.0) + 1e-13 * rng.standard_normal(1000),
+                  1e-9 * rng.standard_normal(999)))
     p = I.ellipse_problem(30, seed=9)
     _, A = O.assemble(p.mask, p.h)
     d, e, _ = O.tridiagonalize(A.dense(), want_q=False)
