@@ -276,7 +276,7 @@ template <class T>
 struct Stage2T {
   T* refl;        // (n-1) * kmax * b
   double* rtau;   // (n-1) * kmax
-  int* progress;  // n + 1
+  int* progress;  // 2 (n + 1): completed steps per sweep, then published subdiagonal values
   int64_t kmax;
 };
 using Stage2 = Stage2T<double>;

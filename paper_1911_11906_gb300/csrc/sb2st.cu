@@ -10,10 +10,13 @@
 // of the fill stays within 2b-1 diagonals of storage and is absorbed by the
 // later sweeps.  Step k of sweep s touches only entries in rows
 // [s+1+kb, s+(k+2)b]; step k' of sweep s-1 touches rows from s+k'b on, so
-// the two are disjoint once k' >= k+3 (at k' = k+2 they share the entry
-// (s+(k+2)b, s+(k+1)b)).  Sweep s may therefore run step k as soon as sweep
-// s-1 has finished its step k+2: sweeps run in a pipeline, one CTA per sweep
-// in flight, each CTA waiting (bounded in time) on a progress counter of its
+// the two are disjoint once k' >= k+3; at k' = k+2 they share only the
+// entry (s+(k+2)b, s+(k+1)b), which step k+2 of sweep s-1 sets to the new
+// subdiagonal value beta of its reflector before anything else.  Sweep s may
+// therefore run step k as soon as sweep s-1 has finished its step k+1 and
+// published the beta of its step k+2 (written to the band right after it is
+// computed, with a second counter): sweeps run in a pipeline, one CTA per
+// sweep in flight, each CTA waiting (bounded in time) on the counters of its
 // predecessor.
 //
 // The reflectors H(s,k) of one sweep act on disjoint rows; H(s,k) and
@@ -41,6 +44,7 @@ struct SbArgs {
   T* refl;        // (n-1) * kmax * b
   double* rtau;   // (n-1) * kmax
   int* progress;  // n, completed steps per sweep
+  int* beta_progress;  // n, steps per sweep whose subdiagonal value is in the band
   int32_t* status;
   long long limit;
 };
@@ -116,13 +120,15 @@ __global__ void __launch_bounds__(SbShape<B, NG>::NT) sb2st_kernel(SbArgs<T> a) 
     const int64_t ns = sb_nsteps(s, n, B);
     const int64_t ns_prev = (s > 0) ? sb_nsteps(s - 1, n, B) : 0;
     for (int64_t k = 0; k < ns; ++k) {
-      // ---- wait for sweep s-1 to have completed step k+2 ----
+      // ---- wait for sweep s-1 to have completed step k+1 and published
+      // the beta of step k+2 ----
       if (tid == 0) {
         int ok = 1;
         if (s > 0) {
-          const int64_t need = (k + 3 < ns_prev) ? k + 3 : ns_prev;
+          const int64_t need = (k + 2 < ns_prev) ? k + 2 : ns_prev;
+          const int64_t need_b = (k + 3 < ns_prev) ? k + 3 : ns_prev;
           const long long t0 = clock64();
-          while (ld_acquire_gpu(a.progress + (s - 1)) < need) {
+          while (ld_acquire_gpu(a.progress + (s - 1)) < need || ld_acquire_gpu(a.beta_progress + (s - 1)) < need_b) {
             if (*(volatile int32_t*)a.status != 0) { ok = 0; break; }
             if (clock64() - t0 > a.limit) {
               raise_status(a.status, FRACLAP_ERR_TIMEOUT);
@@ -181,6 +187,10 @@ __global__ void __launch_bounds__(SbShape<B, NG>::NT) sb2st_kernel(SbArgs<T> a) 
           s_hh[0] = beta;
           s_hh[1] = tu;
           s_hh[2] = (tu == 0.0) ? 0.0 : 1.0 / v0;
+          // the entry sweep s+1 reads at step k-2: published now, not at the
+          // end of the step (the store below writes the same value again)
+          __stcg(&BAND(r0, c), (T)beta);
+          st_release_gpu(a.beta_progress + s, (int)(k + 1));
         }
       }
 #pragma unroll
@@ -439,7 +449,7 @@ int stage2_take(Arena* ar, int64_t n, int b, Stage2T<T>* s) {
   const int64_t nsw = (n >= 2) ? n - 1 : 0;
   s->refl = ar->take<T>(nsw * s->kmax * b);
   s->rtau = ar->take<double>(nsw * s->kmax);
-  s->progress = ar->take<int>(n + 1);
+  s->progress = ar->take<int>(2 * (n + 1));  // completed steps, then published betas
   return 0;
 }
 
@@ -461,9 +471,10 @@ template <class T>
 int sb2st_run(fraclap_ctx* ctx, T* band, int64_t n, int b, double* d, double* e, Stage2T<T>* s,
               cudaStream_t st) {
   if (n >= 2) {
-    FL_CUDA(ctx, cudaMemsetAsync(s->progress, 0, sizeof(int) * (n + 1), st));
+    FL_CUDA(ctx, cudaMemsetAsync(s->progress, 0, sizeof(int) * 2 * (n + 1), st));
     FL_CUDA(ctx, cudaMemsetAsync(s->rtau, 0, sizeof(double) * (n - 1) * s->kmax, st));
-    SbArgs<T> a{band, n, b, s->kmax, s->refl, s->rtau, s->progress, ctx->d_status, ctx->wait_cycles};
+    SbArgs<T> a{band, n, b, s->kmax, s->refl, s->rtau, s->progress, s->progress + (n + 1), ctx->d_status,
+                ctx->wait_cycles};
     int rc = 0;
     switch (b) {
       case 4: rc = sb2st_launch<T, 4, 4>(ctx, a, st); break;
