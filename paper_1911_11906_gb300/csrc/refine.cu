@@ -101,40 +101,50 @@ __global__ void frob_norms(const double* S, int64_t lds, const double* R, int64_
 }
 
 
-// y = M x for the symmetric M stored in its lower triangle, in two strip
-// passes of one launch (no atomics): CTA b < nt sums row block b over its
-// lower part, y_row(i) = sum_{j <= i} M(i, j) x_j; CTA nt + b sums column
-// block b over its strictly lower part, y_col(j) = sum_{i > j} M(i, j) x_i.
-// Thread (row lane, column group w) keeps its partial sums across the
-// 32 x 32 tiles of its strip (coalesced 256-byte column segments) and
-// reduces once at the end.  Block 256 = 32 x 8, grid 2 nt.
-__global__ void __launch_bounds__(256) symv_strips(const double* M, int64_t ldm, int64_t n, const double* x,
-                                                   double* yrow, double* ycol) {
+// y = M x for the symmetric M stored in its lower triangle, in segments of
+// kSymvSeg 32 x 32 tiles (no atomics): CTA (row strip I, segment s) sums the
+// row part y_row(i) = sum_{j <= i} M(i, j) x_j over the tiles J in
+// [s G, s G + G) with J <= I into P[s n + i]; CTA (column strip J, segment s)
+// sums the strictly lower column part y_col(j) = sum_{i > j} M(i, j) x_i
+// over the tiles I in [J + s G, J + s G + G) into Q[s n + j]; segments
+// without tiles write zeros, and reduce_segments adds the segments of each
+// entry in a fixed order.  Thread (row lane, column group w) reads coalesced
+// 256-byte column segments.  Block 256 = 32 x 8, grid 2 nt S.
+constexpr int kSymvSeg = 16;
+__global__ void __launch_bounds__(256) symv_segments(const double* M, int64_t ldm, int64_t n, const double* x,
+                                                     double* P, double* Q, int S) {
   __shared__ double red[8][33];
   const int64_t nt = (n + 31) / 32;
   const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if ((int64_t)blockIdx.x < nt) {
-    const int64_t I = blockIdx.x, gi = I * 32 + tx;
-    double s = 0.0;
+  int64_t b = blockIdx.x;
+  const bool colpass = b >= nt * S;
+  if (colpass) b -= nt * S;
+  const int64_t strip = b / S;
+  const int seg = (int)(b % S);
+  if (!colpass) {
+    const int64_t I = strip, gi = I * 32 + tx;
+    const int64_t J0 = (int64_t)seg * kSymvSeg, J1 = (J0 + kSymvSeg - 1 < I) ? J0 + kSymvSeg - 1 : I;
+    double sum = 0.0;
     if (gi < n)
-      for (int64_t J = 0; J <= I; ++J)
+      for (int64_t J = J0; J <= J1; ++J)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int64_t gj = J * 32 + w * 4 + q;
-          if (gj <= gi) s = fma(M[gi + gj * ldm], x[gj], s);
+          if (gj <= gi) sum = fma(M[gi + gj * ldm], x[gj], sum);
         }
-    red[w][tx] = s;
+    red[w][tx] = sum;
     __syncthreads();
     if (w == 0 && gi < n) {
       double t = 0.0;
 #pragma unroll
       for (int q = 0; q < 8; ++q) t += red[q][tx];
-      yrow[gi] = t;
+      P[(int64_t)seg * n + gi] = t;
     }
   } else {
-    const int64_t J = (int64_t)blockIdx.x - nt;
+    const int64_t J = strip;
+    const int64_t I0 = J + (int64_t)seg * kSymvSeg, I1 = (I0 + kSymvSeg - 1 < nt - 1) ? I0 + kSymvSeg - 1 : nt - 1;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t I = J; I < nt; ++I) {
+    for (int64_t I = I0; I <= I1; ++I) {
       const int64_t gi = I * 32 + tx;
       if (gi >= n) continue;
       const double xi = x[gi];
@@ -148,34 +158,46 @@ __global__ void __launch_bounds__(256) symv_strips(const double* M, int64_t ldm,
     for (int q = 0; q < 4; ++q) {
       const double v = warp_sum(acc[q]);
       const int64_t gj = J * 32 + w * 4 + q;
-      if (tx == 0 && gj < n) ycol[gj] = v;
+      if (tx == 0 && gj < n) Q[(int64_t)seg * n + gj] = v;
     }
   }
 }
-
-// y = y_row + y_col - shift .* x, then x = y / ||y||, est = ||y|| (one block;
-// y is formed in y_row before x is overwritten).
-__global__ void combine_normalize(double* yrow, const double* ycol, const double* shift, int64_t n, double* x,
-                                  double* est) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double y = yrow[i] + ycol[i] - (shift ? shift[i] * x[i] : 0.0);
-    yrow[i] = y;
-    s += y * y;
+// y_i = sum_s P[s n + i] + sum_s Q[s n + i] - shift_i x_i (into P's first
+// segment), and each CTA's sum of y_i^2 into part[blockIdx.x].  Block 256.
+__global__ void reduce_segments(double* P, const double* Q, int S, const double* shift, const double* x,
+                                int64_t n, double* part) {
+  __shared__ double red[8];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double y2 = 0.0;
+  if (i < n) {
+    double y = 0.0;
+    for (int q = 0; q < S; ++q) y += P[(int64_t)q * n + i];
+    for (int q = 0; q < S; ++q) y += Q[(int64_t)q * n + i];
+    y -= shift ? shift[i] * x[i] : 0.0;
+    P[i] = y;
+    y2 = y * y;
   }
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  y2 = warp_sum(y2);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = y2;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0;
-    v = warp_sum(v);
-    if (threadIdx.x == 0) red[0] = v;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+// |y| from the CTAs' partial sums (added in order), x = y / |y|, *est = |y|.
+__global__ void normalize_parts(const double* y, const double* part, int nparts, int64_t n, double* x, double* est) {
+  __shared__ double nrm_sh;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < nparts; ++q) t += part[q];
+    nrm_sh = sqrt(t);
   }
   __syncthreads();
-  const double nrm = sqrt(red[0]);
+  const double nrm = nrm_sh;
   const double inv = (nrm > 0.0) ? 1.0 / nrm : 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = yrow[i] * inv;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = y[i] * inv;
   if (threadIdx.x == 0) *est = nrm;
 }
 
@@ -946,12 +968,15 @@ int refine_run(fraclap_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t
         start_vec<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(xv, n);
         count_launch(ctx);
         const int64_t nt = cdiv(n, 32);
-        double* yc = AX + n;  // second n doubles of the same scratch
+        const int S = (int)cdiv(nt, kSymvSeg);
+        const unsigned nb = (unsigned)cdiv(n, 256);
+        double* yc = AX + (int64_t)S * n;     // the segments' partial sums: 2 S n doubles of the n x n scratch
+        double* part = yc + (int64_t)S * n;  // nb CTA sums of y^2
         for (int pit = 0; pit < 12; ++pit) {
-          symv_strips<<<(unsigned)(2 * nt), 256, 0, st>>>(M, n, n, xv, yv, yc);
-          combine_normalize<<<1, 1024, 0, st>>>(yv, yc, shift, n, xv, scal + 4 + which);
-          count_launch(ctx);
-          count_launch(ctx);
+          symv_segments<<<(unsigned)(2 * nt * S), 256, 0, st>>>(M, n, n, xv, yv, yc, S);
+          reduce_segments<<<nb, 256, 0, st>>>(yv, yc, S, shift, xv, n, part);
+          normalize_parts<<<1, 1024, 0, st>>>(yv, part, (int)nb, n, xv, scal + 4 + which);
+          for (int q = 0; q < 3; ++q) count_launch(ctx);
         }
       }
     }
