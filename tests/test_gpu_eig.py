@@ -96,13 +96,19 @@ def _check_decomposition(A, lam_o, lam, V, tol_lam=1e-11):
     assert np.max(np.abs(V.T @ V - np.eye(n))) <= 1e-12
 
 
-@pytest.mark.parametrize("m", [1, 2, 5, 9, 23])
-def test_eig_full_small_squares(m):
+@pytest.mark.parametrize("route", ["fp64", "mixed"])
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 9, 23])
+def test_eig_full_small_squares(m, route):
+    """Both routes on the smallest grids (n = 1, 4, 9, ...): one-tile and
+    one-panel cases of every kernel, against the closed form and the oracle."""
     F = _F()
     p = I.square_problem(m, n_poly=0)
     _, A = O.assemble(p.mask, p.h)
     D = A.dense()
-    lam, V = F.eig_full(_colmajor(D))
+    if route == "fp64":
+        lam, V = F.eig_full(_colmajor(D))
+    else:
+        lam, V = F.eig_full_mixed(_colmajor(D), *_csr_cuda(A), refine_iters=6)
     lam, V = lam.cpu().numpy(), V.cpu().numpy()
     ref = square_closed_form(m, 2)
     lam_o, _ = O.eig_full(D)
