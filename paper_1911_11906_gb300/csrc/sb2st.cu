@@ -304,15 +304,19 @@ __global__ void band_diagonals(const T* band, int ldb, int64_t n, double* d, dou
 // CTA stages the reflectors of the next D steps in shared memory (double
 // buffered) while it applies the current D; the rows entering the window are
 // loaded one batch ahead.  Work: 4 L n flops per reflector of length L.
-constexpr int Q2T_WARPS = 8;
-
-template <class T, int B, int P>
-__global__ void __launch_bounds__(Q2T_WARPS * 32, 2)
+// Every CTA streams all the reflectors through its shared memory, so the
+// CTA's warp count W sets the L2 traffic per column: 16 warps per CTA (one
+// CTA per SM) halve it against 8 (two per SM), which matters once the
+// columns fill the SMs (at n = 8810 in FP32, 68 against 93 ms for the
+// kernel alone); with few columns, 8-warp CTAs spread over more SMs.
+template <class T, int B, int P, int W>
+__global__ void __launch_bounds__(W * 32, 16 / W)
 q2t_apply_kernel(const T* __restrict__ refl, const double* __restrict__ rtau, int64_t n,
                  int64_t kmax, T* Y, int64_t ldy, int64_t ncols) {
   // D = R: a batch of D reflectors slides the window by one full register
   // rotation, and the sweep is padded with zero reflectors (tau = 0) to whole
   // batches, so every slide is unconditional and compiles to renaming.
+  constexpr int Q2T_WARPS = W;
   constexpr int R = B / P, CPW = 32 / P, D = R, NT = Q2T_WARPS * 32;
   constexpr int PER = (D * B + NT - 1) / NT;  // staged doubles per thread
   __shared__ T vbuf[2][D][B];
@@ -519,13 +523,22 @@ int q2_apply_run(fraclap_ctx* ctx, const Stage2T<T>* s, int64_t n, int b, T* Z, 
   // Default 8: at n = 8810 in FP32, 123 ms against 140 (P = 4) and 247
   // (P = 16, a barrier every four reflectors).
   const int parts64 = (ctx->q2_parts == 4 || ctx->q2_parts == 16) ? ctx->q2_parts : 8;
-#define FL_Q2T(BB, PP)                                                                        \
-  if (b == BB && cpw == 0) {                                                                  \
-    cpw = 32 / PP;                                                                            \
-    const int64_t grid = cdiv(ncols, (int64_t)cpw * Q2T_WARPS);                                \
-    q2t_apply_kernel<T, BB, PP><<<(unsigned)grid, Q2T_WARPS * 32, 0, st>>>(s->refl, s->rtau, n, \
-                                                                          s->kmax, Yt, ldy, ncols); \
-    count_launch(ctx);                                                                        \
+  // 16-warp CTAs once 8-warp CTAs would already cover every SM
+  const auto wide = [&](int pp) { return cdiv(ncols, (int64_t)(32 / pp) * 8) >= ctx->sm_count; };
+#define FL_Q2T_W(BB, PP, WW)                                                                         \
+  {                                                                                                  \
+    cpw = 32 / PP;                                                                                   \
+    const int64_t grid = cdiv(ncols, (int64_t)cpw * WW);                                             \
+    q2t_apply_kernel<T, BB, PP, WW><<<(unsigned)grid, WW * 32, 0, st>>>(s->refl, s->rtau, n, s->kmax, \
+                                                                       Yt, ldy, ncols);              \
+    count_launch(ctx);                                                                               \
+  }
+#define FL_Q2T(BB, PP)                    \
+  if (b == BB && cpw == 0) {              \
+    if (BB == 64 && wide(PP))             \
+      FL_Q2T_W(BB, PP, 16)                \
+    else                                  \
+      FL_Q2T_W(BB, PP, 8)                 \
   }
   FL_Q2T(4, 1)
   FL_Q2T(8, 2)
@@ -540,6 +553,7 @@ int q2_apply_run(fraclap_ctx* ctx, const Stage2T<T>* s, int64_t n, int b, T* Z, 
     if (parts64 == 4) FL_Q2T(64, 8)  // FP64 asked for 4 parts: 8
   }
 #undef FL_Q2T
+#undef FL_Q2T_W
   FL_CHECK(ctx, cpw != 0, FRACLAP_ERR_UNSUPPORTED, "q2 back-transformation: band width %d not in {4, 8, 16, 32, 64}", b);
   FL_CUDA(ctx, cudaGetLastError());
   return transpose_run<T>(ctx, Yt, ldy, Z, ldz, ncols, n, st);
