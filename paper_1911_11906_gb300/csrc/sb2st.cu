@@ -520,8 +520,8 @@ int q2_apply_run(fraclap_ctx* ctx, const Stage2T<T>* s, int64_t n, int b, T* Z, 
   // parts per window at b = 64: 4 (16 rows per lane, 8 columns per warp),
   // 8 or 16 (fewer rows per lane, more warps over the same columns: the
   // kernel has ncols / (32 / P) warps in all, so small P leaves SMs idle).
-  // Default 8: at n = 8810 in FP32, 123 ms against 140 (P = 4) and 247
-  // (P = 16, a barrier every four reflectors).
+  // Default 8: at n = 8810 in FP32 (8-warp CTAs) 123 ms against 140 (P = 4)
+  // and 247 (P = 16, a barrier every four reflectors).
   const int parts64 = (ctx->q2_parts == 4 || ctx->q2_parts == 16) ? ctx->q2_parts : 8;
   // 16-warp CTAs once 8-warp CTAs would already cover every SM
   const auto wide = [&](int pp) { return cdiv(ncols, (int64_t)(32 / pp) * 8) >= ctx->sm_count; };
