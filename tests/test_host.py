@@ -149,6 +149,13 @@ def test_bench_work_counts():
     tot = sum(min(b, n - r0) for s in range(n - 1) for r0 in range(s + 1, n, b) if min(b, n - r0) > 1)
     assert bench.q2_flops(n, b) == 4.0 * tot * n
     assert bench.whole_job_rate(128, 4, 500.0) == 1024.0
+    # the apply's two sliced products V^T F (n x m) and V C (n x k), inner dimension n:
+    # 2 flops per digit pair p + q < d per output element per k; d = ceil(8 s / 7) 7-bit digits
+    n, m, k, s = 5, 3, 4, 6
+    d = -(-8 * s // 7)
+    pairs = sum(1 for p in range(d) for q in range(d) if p + q < d)
+    assert bench.apply_slice_flops(n, m, k, s) == 2.0 * pairs * n * n * (m + k)
+    assert bench.apply_slice_flops(n, m, k, s, digit_bits=8) == 2.0 * (s * (s + 1) // 2) * n * n * (m + k)
 
 
 def _free_port():
